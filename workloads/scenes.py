@@ -1,0 +1,239 @@
+"""Seeded synthetic sonar scenes and direction grids.
+
+This module feeds both the CUDA library and the oracle with the same inputs.
+It holds none of the beamforming arithmetic: it only synthesises microphone
+signals from point reflectors or sources (spherical propagation, one-way path
+length d, amplitude 1/d) and lists the direction grids to image.  Directions
+are returned either as (azimuth, elevation) pairs in radians or, for the
+Fibonacci grid, as unit vectors in the array frame (array in the z = 0 plane,
+broadside along +z, x horizontal, y vertical).
+
+The paper's recorded eRTIS dataset is not available; these scenes stand in
+for it with its array size (32 microphones), sample rate (450 kHz) and the
+frame lengths of the benchmark configurations.
+
+Recipes (all draws from numpy.random.default_rng(seed)):
+
+  small_2d   32 mics area-uniform in a 12 cm disc, fs 450 kHz, T 4096, three
+             reflectors (azimuth U(-60, 60) deg, elevation 0, range U(0.5, 3) m,
+             amplitude 1), Gaussian-windowed 40 kHz echo (sigma 50 us),
+             white noise at 20 dB SNR, 91 azimuths -90..90 deg, elevation 0.
+  hemi_3d    the same array, T 16384, 2048 directions on a frontal-hemisphere
+             Fibonacci grid, eight reflectors (area-uniform on the hemisphere,
+             range U(0.3, 6) m, amplitude log-uniform over 40 dB), 10 dB SNR.
+  passive    N in {64, 256} mics uniform in a 0.4 m square, fs 400 kHz,
+             T 32768, four broadband sources (white noise band-passed to
+             20-80 kHz, unit RMS, azimuth/elevation U(-60, 60) deg, range
+             U(1, 5) m, exact frequency-domain fractional delay, amplitude 1/d)
+             plus uncorrelated sensor noise at 0 dB SNR; 128 x 64 az/el grid
+             over [-60, 60] deg.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SOUND_SPEED = 343.0
+
+
+@dataclass
+class Scene:
+    """One synthetic frame with the geometry needed to image it."""
+    name: str
+    mic_xyz: np.ndarray            # [N][3] float64 metres
+    frame: np.ndarray              # [N][T] float32 samples
+    fs: float
+    c: float
+    dir_azel: np.ndarray | None    # [M][2] float64 radians, or None
+    dir_unit: np.ndarray | None    # [M][3] float64, or None
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def n_mics(self) -> int:
+        return int(self.frame.shape[0])
+
+    @property
+    def n_samples(self) -> int:
+        return int(self.frame.shape[1])
+
+    @property
+    def n_dirs(self) -> int:
+        if self.dir_unit is not None:
+            return int(self.dir_unit.shape[0])
+        return int(self.dir_azel.shape[0])
+
+
+# --------------------------------------------------------------------------
+# arrays
+# --------------------------------------------------------------------------
+def disc_array(rng: np.random.Generator, n: int, radius: float) -> np.ndarray:
+    """n positions area-uniform in a disc of the given radius, z = 0."""
+    rad = radius * np.sqrt(rng.random(n))
+    ang = 2.0 * np.pi * rng.random(n)
+    return np.stack([rad * np.cos(ang), rad * np.sin(ang), np.zeros(n)], axis=1)
+
+
+def square_array(rng: np.random.Generator, n: int, side: float) -> np.ndarray:
+    """n positions uniform in a side x side square centred on 0, z = 0."""
+    xy = (rng.random((n, 2)) - 0.5) * side
+    return np.concatenate([xy, np.zeros((n, 1))], axis=1)
+
+
+# --------------------------------------------------------------------------
+# direction grids
+# --------------------------------------------------------------------------
+def azimuth_fan(start_deg: float = -90.0, stop_deg: float = 90.0,
+                step_deg: float = 2.0) -> np.ndarray:
+    """Azimuths start..stop (inclusive) at elevation 0 -> [M][2] radians."""
+    count = int(round((stop_deg - start_deg) / step_deg)) + 1
+    az = np.deg2rad(start_deg + step_deg * np.arange(count))
+    return np.stack([az, np.zeros_like(az)], axis=1)
+
+
+def azel_grid(n_az: int, n_el: int, lim_deg: float = 60.0) -> np.ndarray:
+    """n_az x n_el grid uniform over [-lim, lim] in both angles -> [M][2]."""
+    az = np.deg2rad(np.linspace(-lim_deg, lim_deg, n_az))
+    el = np.deg2rad(np.linspace(-lim_deg, lim_deg, n_el))
+    A, E = np.meshgrid(az, el, indexing="xy")
+    return np.stack([A.reshape(-1), E.reshape(-1)], axis=1)
+
+
+def fibonacci_hemisphere(m: int) -> np.ndarray:
+    """m unit vectors on the frontal (+z) hemisphere, Fibonacci spiral."""
+    k = np.arange(m, dtype=np.float64)
+    z = (k + 0.5) / m
+    rho = np.sqrt(1.0 - z * z)
+    ang = k * np.pi * (3.0 - math.sqrt(5.0))
+    return np.stack([rho * np.cos(ang), rho * np.sin(ang), z], axis=1)
+
+
+def _point(az: float, el: float, rng_m: float) -> np.ndarray:
+    """Scene position at azimuth/elevation/range (x horizontal, y up, z ahead)."""
+    return rng_m * np.array([math.sin(az) * math.cos(el), math.sin(el),
+                             math.cos(az) * math.cos(el)])
+
+
+# --------------------------------------------------------------------------
+# signals
+# --------------------------------------------------------------------------
+def _echo_frame(rng, mic_xyz, positions, amps, fs, T, c, f0, sigma, noise_eta):
+    N = mic_xyz.shape[0]
+    t = np.arange(T) / fs
+    sig = np.zeros((N, T))
+    for p, a in zip(positions, amps):
+        d = np.linalg.norm(mic_xyz - p[None, :], axis=1)
+        for i in range(N):
+            tt = t - d[i] / c
+            sig[i] += a / d[i] * np.exp(-tt * tt / (2.0 * sigma * sigma)) * \
+                np.cos(2.0 * np.pi * f0 * tt)
+    sig += noise_eta * rng.standard_normal((N, T))
+    return sig
+
+
+def small_2d(seed: int = 1, n_mics: int = 32, n_samples: int = 4096,
+             n_reflectors: int = 3, snr_db: float = 20.0) -> Scene:
+    """2-D scene: 12 cm disc, 91 azimuths at elevation 0."""
+    rng = np.random.default_rng(seed)
+    fs, c = 450e3, SOUND_SPEED
+    mic = disc_array(rng, n_mics, 0.06)
+    pos, amps = [], []
+    for _ in range(n_reflectors):
+        az = math.radians(rng.uniform(-60.0, 60.0))
+        rg = rng.uniform(0.5, 3.0)
+        pos.append(_point(az, 0.0, rg))
+        amps.append(1.0)
+    eta = 10.0 ** (-snr_db / 20.0)
+    frame = _echo_frame(rng, mic, pos, amps, fs, n_samples, c, 40e3, 50e-6, eta)
+    return Scene("small_2d", mic, frame.astype(np.float32), fs, c,
+                 azimuth_fan(), None,
+                 {"seed": seed, "reflectors": np.array(pos), "snr_db": snr_db})
+
+
+def hemi_3d(seed: int = 2, n_samples: int = 16384, n_dirs: int = 2048,
+            n_reflectors: int = 8, snr_db: float = 10.0, array_seed: int = 1) -> Scene:
+    """3-D scene: the small_2d array, Fibonacci hemisphere of directions."""
+    mic = disc_array(np.random.default_rng(array_seed), 32, 0.06)
+    rng = np.random.default_rng(seed)
+    fs, c = 450e3, SOUND_SPEED
+    pos, amps = [], []
+    for _ in range(n_reflectors):
+        z = rng.random()
+        ang = 2.0 * np.pi * rng.random()
+        rho = math.sqrt(1.0 - z * z)
+        u = np.array([rho * math.cos(ang), rho * math.sin(ang), z])
+        rg = rng.uniform(0.3, 6.0)
+        pos.append(rg * u)
+        amps.append(10.0 ** (-2.0 * rng.random()))
+    eta = 10.0 ** (-snr_db / 20.0)
+    frame = _echo_frame(rng, mic, pos, amps, fs, n_samples, c, 40e3, 50e-6, eta)
+    return Scene("hemi_3d", mic, frame.astype(np.float32), fs, c, None,
+                 fibonacci_hemisphere(n_dirs),
+                 {"seed": seed, "reflectors": np.array(pos), "amps": np.array(amps),
+                  "snr_db": snr_db})
+
+
+def passive(seed: int = 4, n_mics: int = 64, n_samples: int = 32768,
+            n_az: int = 128, n_el: int = 64, n_sources: int = 4) -> Scene:
+    """Large passive array: broadband sources, 0 dB sensor noise."""
+    rng = np.random.default_rng(seed)
+    fs, c = 400e3, SOUND_SPEED
+    mic = square_array(rng, n_mics, 0.4)
+    T = n_samples
+    freqs = np.fft.rfftfreq(T, 1.0 / fs)
+    band = (freqs >= 20e3) & (freqs <= 80e3)
+    sig = np.zeros((n_mics, T))
+    pos = []
+    for _ in range(n_sources):
+        w = rng.standard_normal(T)
+        W = np.fft.rfft(w)
+        W[~band] = 0.0
+        s = np.fft.irfft(W, T)
+        s /= np.sqrt(np.mean(s * s))
+        S = np.fft.rfft(s)
+        az = math.radians(rng.uniform(-60.0, 60.0))
+        el = math.radians(rng.uniform(-60.0, 60.0))
+        rg = rng.uniform(1.0, 5.0)
+        p = _point(az, el, rg)
+        pos.append(p)
+        d = np.linalg.norm(mic - p[None, :], axis=1)
+        for i in range(n_mics):
+            shift = np.exp(-2j * np.pi * freqs * d[i] / c)
+            sig[i] += np.fft.irfft(S * shift, T) / d[i]
+    rms = float(np.mean(np.sqrt(np.mean(sig * sig, axis=1))))
+    sig += rms * rng.standard_normal((n_mics, T))
+    return Scene("passive", mic, sig.astype(np.float32), fs, c,
+                 azel_grid(n_az, n_el), None,
+                 {"seed": seed, "sources": np.array(pos)})
+
+
+def plane_wave(n_mics: int, n_samples: int, az_deg: float, el_deg: float = 0.0,
+               fs: float = 450e3, c: float = SOUND_SPEED, seed: int = 7,
+               radius: float = 0.06, t0: float = 2e-3) -> Scene:
+    """Far-field pulse from one direction, sampled with its exact arrival times.
+
+    Mic i receives the pulse at t0 - (p_i - p_bar).u / c: microphones further
+    along the arrival direction u hear it earlier.
+    """
+    rng = np.random.default_rng(seed)
+    mic = disc_array(rng, n_mics, radius)
+    u = _point(math.radians(az_deg), math.radians(el_deg), 1.0)
+    proj = (mic - mic.mean(axis=0)) @ u
+    t = np.arange(n_samples) / fs
+    frame = np.zeros((n_mics, n_samples))
+    for i in range(n_mics):
+        tt = t - (t0 - proj[i] / c)
+        frame[i] = np.exp(-tt * tt / (2.0 * (50e-6) ** 2)) * np.cos(2.0 * np.pi * 40e3 * tt)
+    return Scene("plane_wave", mic, frame.astype(np.float32), fs, c,
+                 azimuth_fan(-90.0, 90.0, 1.0), None, {"az_deg": az_deg})
+
+
+def random_frame(seed: int, n_mics: int, n_samples: int, scale: float = 1.0,
+                 zero_fraction: float = 0.0) -> np.ndarray:
+    """Gaussian frame [N][T] float32, optionally with exact zeros sprinkled in."""
+    rng = np.random.default_rng(seed)
+    f = scale * rng.standard_normal((n_mics, n_samples))
+    if zero_fraction > 0.0:
+        f[rng.random(f.shape) < zero_fraction] = 0.0
+    return f.astype(np.float32)
