@@ -1,0 +1,244 @@
+/*
+ * dmas.h -- C ABI of the B300 (sm_103a) n-th order Delay-Multiply-and-Sum
+ * beamformer with Coherence Factor weighting and envelope detection.
+ *
+ * Method: W. Jansen, W. Daems, J. Steckel, "Delay-Multiply-And-Sum Beamforming
+ * for Real-Time In-Air Acoustic Imaging".  Section and equation names below
+ * are that paper's.
+ *
+ *   For every steering direction psi and output sample t the library
+ *     1. pre-steers: x_i = m_i(t + tau_{i,psi})                 (Eq. signal_delay)
+ *     2. takes signed n-th roots s_i = sgn(x_i)|x_i|^(1/n)      (Sec. II-B)
+ *     3. accumulates the power sums P_k = sum_i s_i^k, k=1..n  (Eq. power_sum)
+ *        and sum_i x_i, sum_i x_i^2 for the coherence factor
+ *     4. forms E_n from the power sums by Newton-Girard        (Eqs. dmas2_impl..
+ *                                                               dmas5_impl,
+ *                                                               girard_newton_general)
+ *     5. weights by CF = (sum x_i)^2 / (N sum x_i^2 + eps)      (Eq. cf, Sec. II-D)
+ *     6. takes |.| and low-pass filters along t (envelope)      (Sec. II, step 3)
+ *   and writes image[psi][t].
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns a dmas_status and never aborts, traps or exits.
+ *   - "device" pointers are CUDA device (or managed) memory on the device that
+ *     was current when the plan was created; "host" pointers are ordinary host
+ *     memory.  The caller owns every buffer it passes; the library never frees
+ *     or retains caller pointers beyond the call.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Device work is enqueued asynchronously on that stream.
+ *   - Sizes are element counts unless the name says bytes.
+ *   - Frame values are not checked: a NaN or Inf sample propagates to the
+ *     pixels that read it.
+ */
+#ifndef DMAS_H
+#define DMAS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DMAS_OK = 0,
+    DMAS_EINVAL = 1,   /* a NULL, out-of-range size, order, mode or non-finite parameter */
+    DMAS_ENOMEM = 2,   /* a device or host allocation failed */
+    DMAS_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed (see dmas_plan_last_error) */
+    DMAS_EBUSY = 4,    /* reserved for the serving layer: no capacity right now */
+    DMAS_ETIMEOUT = 5  /* a device-side bounded wait expired (error word set by a kernel) */
+} dmas_status;
+
+/* How tau_{i,psi} * fs is turned into a sample position (Eq. signal_delay). */
+typedef enum {
+    DMAS_DELAY_ROUND = 0,  /* nearest sample, ties away from zero */
+    DMAS_DELAY_LINEAR = 1  /* every power channel linearly interpolated between
+                              floor(delta) and floor(delta) + 1 */
+} dmas_delay_mode;
+
+/* Storage type of the per-microphone root channel that the beamform kernel
+ * gathers.  Power sums always accumulate in FP32. */
+typedef enum {
+    DMAS_CH_F32 = 0,
+    DMAS_CH_F16 = 1,   /* roots stored as FP16 (halves the gather bytes) */
+    DMAS_CH_BF16 = 2   /* roots stored as BF16 */
+} dmas_chan_prec;
+
+/* Arithmetic of the Newton-Girard step (power sums -> E_n). */
+typedef enum {
+    DMAS_NG_F32 = 0,   /* plain FP32 */
+    DMAS_NG_F64 = 1,   /* FP64 */
+    DMAS_NG_CF32 = 2   /* compensated FP32 (double-float: error-free sums and products) */
+} dmas_ng_prec;
+
+/* dmas_plan_desc.flags */
+enum {
+    DMAS_F_CF = 1,        /* multiply by the coherence factor (Eq. cf) */
+    DMAS_F_ENVELOPE = 2   /* |.| then low-pass along t; without it image = E_n (x CF) */
+};
+
+typedef struct dmas_plan dmas_plan;
+
+/*
+ * Plan description.  All pointers are HOST memory, read during
+ * dmas_plan_create only (the plan keeps its own copies).
+ *
+ * Geometry (Sec. II, delay look-up table): with delays_s == NULL the plan
+ * computes tau_{i,psi} = -((p_i - p_bar) . u_psi) / c in FP64, p_bar the mean of
+ * the microphone positions, u_psi the unit vector of direction psi.  The array
+ * frame has x horizontal, y vertical and broadside along +z; a direction given
+ * as (azimuth theta, elevation phi) is u = (sin th cos ph, sin ph, cos th cos ph)
+ * (Fig. 1's azimuth/elevation).
+ */
+typedef struct {
+    int n_mics;               /* N, 1 .. 4096 */
+    const double *mic_xyz;    /* [N][3] metres; required unless delays_s is given */
+    int n_dirs;               /* M, 1 .. 1<<20 */
+    const double *dir_azel;   /* [M][2] radians (azimuth, elevation), or NULL */
+    const double *dir_unit;   /* [M][3] unit vectors; used instead of dir_azel if non-NULL */
+    const double *delays_s;   /* optional [M][N] seconds; overrides the geometry */
+    int n_samples;            /* T, samples per microphone per frame, 1 .. 1<<24 */
+    double fs;                /* sample rate, Hz, finite and > 0 */
+    double c;                 /* speed of sound, m/s, finite and > 0 (geometry only) */
+    int order;                /* n, 1 .. 8 */
+    int delay_mode;           /* dmas_delay_mode */
+    int flags;                /* DMAS_F_* */
+    double cf_eps;            /* CF denominator constant (Eq. cf); <= 0 selects 1e-30 */
+    double env_cutoff_hz;     /* envelope low-pass cutoff; <= 0 selects 5000 Hz */
+    int env_taps;             /* odd FIR length <= 1023; 0 selects 2*ceil(fs/fc)+1 */
+    int chan_prec;            /* dmas_chan_prec */
+    int ng_prec;              /* dmas_ng_prec */
+} dmas_plan_desc;
+
+/* Read-only summary of a plan. */
+typedef struct {
+    int n_mics, n_dirs, n_samples, order, delay_mode, flags;
+    int chan_prec, ng_prec;
+    int env_taps;              /* L actually used (0 without DMAS_F_ENVELOPE) */
+    int n_groups;              /* direction groups (CTA rows) */
+    int group_size;            /* directions per group */
+    int window;                /* staged samples per microphone per time tile */
+    int mic_chunk;             /* microphones staged per pass */
+    int time_tile;             /* output samples per CTA */
+    size_t workspace_bytes;    /* device scratch a beamform call uses */
+    size_t table_bytes;        /* device bytes of the resident delay tables */
+} dmas_plan_info;
+
+/*
+ * Create a plan: validates `desc`, computes the delay table in FP64, groups
+ * neighbouring directions, computes the envelope taps, and allocates and
+ * uploads every device table and the scratch a beamform call needs, on the
+ * current CUDA device.  On success *out owns all of it.
+ * Errors: DMAS_EINVAL (bad desc or out == NULL), DMAS_ENOMEM, DMAS_ECUDA.
+ * On error *out is set to NULL and nothing is leaked.
+ */
+dmas_status dmas_plan_create(const dmas_plan_desc *desc, dmas_plan **out);
+
+/* Release a plan and all its device memory.  NULL is a no-op returning DMAS_OK.
+ * Synchronises the device before freeing. */
+dmas_status dmas_destroy(dmas_plan *plan);
+
+/*
+ * Beamform one frame (the whole path, steps 1-6 above).
+ *   d_frame : device [N][T] float32, row-major (microphone-major).
+ *   d_image : device [M][T] float32, row-major, direction order of the desc;
+ *             the envelope, or E_n (x CF) when DMAS_F_ENVELOPE is off.
+ *   d_y     : optional device [M][T] float32: E_n (x CF) before the envelope.
+ *   d_cf    : optional device [M][T] float32: the coherence factor.
+ * The plan's scratch is reused by every call: calls on one plan must be
+ * ordered on one stream (or synchronised); use one plan per concurrent stream.
+ * Errors: DMAS_EINVAL (NULL plan/frame/image), DMAS_ECUDA (launch failure).
+ * Device-side wait timeouts surface as DMAS_ETIMEOUT from dmas_plan_check.
+ */
+dmas_status dmas_beamform(dmas_plan *plan, const float *d_frame, float *d_image,
+                          float *d_y, float *d_cf, void *stream);
+
+/*
+ * Same as dmas_beamform but with HOST buffers: copies h_frame ([N][T] float32)
+ * to the device, beamforms, copies the image back to h_image ([M][T] float32)
+ * and synchronises `stream` before returning.  Pinned (page-locked) host memory
+ * gives the fastest copies.  The device staging buffers are allocated on the
+ * first call and kept by the plan.
+ */
+dmas_status dmas_beamform_host(dmas_plan *plan, const float *h_frame, float *h_image,
+                               void *stream);
+
+/*
+ * Serving: beamform `count` frames, each with its own plan.  plans/d_frames/
+ * d_images are HOST arrays of `count` entries; each frame and image is a
+ * device buffer shaped as for dmas_beamform.  The same plan may appear more
+ * than once (each entry gets its own scratch from the workspace).
+ * d_workspace is device memory of at least dmas_batch_workspace_bytes(count,
+ * plans) bytes, 256-byte aligned, owned by the caller and not used by anything
+ * else while the batch runs.  Each entry's image is bitwise identical to
+ * dmas_beamform of that entry alone.
+ * Errors: DMAS_EINVAL (count < 1, a NULL entry, small or misaligned
+ * workspace), DMAS_ECUDA.
+ */
+dmas_status dmas_beamform_batch(int count, dmas_plan *const *plans,
+                                const float *const *d_frames, float *const *d_images,
+                                void *d_workspace, size_t workspace_bytes, void *stream);
+
+/* Device bytes a batch of these plans needs (0 on a NULL argument). */
+size_t dmas_batch_workspace_bytes(int count, dmas_plan *const *plans);
+
+/* Device scratch bytes one dmas_beamform call of this plan uses (admission
+ * control), or 0 for NULL. */
+size_t dmas_plan_workspace_bytes(const dmas_plan *plan);
+
+/* Fill *info.  Errors: DMAS_EINVAL on NULL. */
+dmas_status dmas_plan_get_info(const dmas_plan *plan, dmas_plan_info *info);
+
+/*
+ * Copy the plan's delay table to host memory in the desc's direction order:
+ * shift[M][N] int32 sample offsets (ROUND: llround(tau*fs); LINEAR:
+ * floor(tau*fs)) and, if frac != NULL, frac[M][N] float32 interpolation weights
+ * (tau*fs - floor(tau*fs) for LINEAR, 0 for ROUND).
+ */
+dmas_status dmas_plan_get_delays(const dmas_plan *plan, int32_t *shift, float *frac);
+
+/* Copy the envelope taps (env_taps float32 values, h[-H..H]) to host memory. */
+dmas_status dmas_plan_get_taps(const dmas_plan *plan, float *taps);
+
+/*
+ * Synchronise the plan's last stream and read the device error word that the
+ * kernels set when a bounded wait expired.  Returns DMAS_OK, DMAS_ETIMEOUT or
+ * DMAS_ECUDA; clears the error word.
+ */
+dmas_status dmas_plan_check(dmas_plan *plan);
+
+/* Text of the last CUDA error this plan saw ("" if none); owned by the plan. */
+const char *dmas_plan_last_error(const dmas_plan *plan);
+
+/*
+ * Per-stage timing (the tracing hook of the path).  With profiling enabled a
+ * dmas_beamform call records a CUDA event on its stream before and after each
+ * kernel stage; nothing is skipped.  dmas_plan_stage_ms synchronises on the
+ * last call's final event and writes the stage durations in milliseconds
+ * (roots, beamform, envelope; 0 for a stage that did not run).
+ * Errors: DMAS_EINVAL (NULL, or no profiled call yet), DMAS_ECUDA.
+ */
+dmas_status dmas_plan_set_profiling(dmas_plan *plan, int enable);
+dmas_status dmas_plan_stage_ms(dmas_plan *plan, float *roots_ms, float *beam_ms,
+                               float *env_ms);
+
+/*
+ * Self-test of the kernels' bounded waits: launches one CTA that waits on a
+ * shared-memory barrier no copy ever completes, with a limit of `limit_ms`
+ * milliseconds (1 .. 10000).  The kernel gives up, sets its error word and
+ * returns normally.  Returns DMAS_ETIMEOUT when that happened (the expected
+ * result), DMAS_OK if the wait somehow completed, DMAS_EINVAL or DMAS_ECUDA.
+ */
+dmas_status dmas_selftest_wait_timeout(double limit_ms, void *stream);
+
+/* Static text for a status code. */
+const char *dmas_status_string(dmas_status status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int dmas_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DMAS_H */

@@ -1,0 +1,8 @@
+// Beamform kernels of order n = 8 (all delay modes, channel types and
+// Newton-Girard precisions), instantiated in their own translation unit.
+#include "dmas_launch.cuh"
+
+namespace dmas {
+template cudaError_t launch_beamform_order<8>(const BeamParams &, int, int, int, unsigned,
+                                               size_t, cudaStream_t);
+}  // namespace dmas

@@ -1,0 +1,477 @@
+// C ABI of the DMAS-CF beamformer (declared in include/dmas.h): plan
+// lifecycle, device tables and scratch, and the launch sequence of one frame:
+//   roots_kernel -> beamform_kernel -> envelope_kernel.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "dmas.h"
+#include "dmas_internal.h"
+#include "dmas_launch.cuh"
+
+namespace dmas {
+extern template cudaError_t launch_beamform_order<1>(const BeamParams &, int, int, int, unsigned,
+                                                     size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_order<2>(const BeamParams &, int, int, int, unsigned,
+                                                     size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_order<3>(const BeamParams &, int, int, int, unsigned,
+                                                     size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_order<4>(const BeamParams &, int, int, int, unsigned,
+                                                     size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_order<5>(const BeamParams &, int, int, int, unsigned,
+                                                     size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_order<6>(const BeamParams &, int, int, int, unsigned,
+                                                     size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_order<7>(const BeamParams &, int, int, int, unsigned,
+                                                     size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_order<8>(const BeamParams &, int, int, int, unsigned,
+                                                     size_t, cudaStream_t);
+
+static const BeamLauncher kBeamLaunchers[9] = {
+    nullptr,
+    &launch_beamform_order<1>, &launch_beamform_order<2>, &launch_beamform_order<3>,
+    &launch_beamform_order<4>, &launch_beamform_order<5>, &launch_beamform_order<6>,
+    &launch_beamform_order<7>, &launch_beamform_order<8>};
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+}  // namespace dmas
+
+using namespace dmas;
+
+struct dmas_plan {
+    HostPlan hp;
+    int device = 0;
+    int *d_gdir = nullptr, *d_gws = nullptr, *d_rel = nullptr;
+    float *d_frac = nullptr;
+    unsigned *d_err = nullptr;
+    void *d_scratch = nullptr;        // root channels (+ y buffer with the envelope)
+    size_t chan_bytes = 0, ybuf_bytes = 0, table_bytes = 0;
+    float *d_io_frame = nullptr, *d_io_image = nullptr;  // dmas_beamform_host staging
+    size_t smem_beam = 0, smem_env = 0;
+    EnvTaps taps{};
+    cudaStream_t last_stream = nullptr;
+    std::string last_error;
+    // stage profiling
+    bool profiling = false;
+    bool profiled_once = false;
+    bool env_ran = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded wait: the barrier expects two arrivals and gets one,
+// so the phase never completes; the wait must give up and report.
+// ---------------------------------------------------------------------------
+__global__ void wait_timeout_selftest_kernel(unsigned *err, unsigned long long limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 2);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive(&bar);
+        if (!mbar_wait_bounded(&bar, 0, limit_ns)) atomicOr(err, kErrTimeout);
+    }
+}
+
+
+dmas_status cuda_fail(dmas_plan *p, cudaError_t e, const char *what) {
+    if (p) p->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return DMAS_ECUDA;
+}
+
+void free_plan_memory(dmas_plan *p) {
+    cudaFree(p->d_gdir);
+    cudaFree(p->d_gws);
+    cudaFree(p->d_rel);
+    cudaFree(p->d_frac);
+    cudaFree(p->d_err);
+    cudaFree(p->d_scratch);
+    cudaFree(p->d_io_frame);
+    cudaFree(p->d_io_image);
+    for (auto &e : p->ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    p->d_gdir = p->d_gws = p->d_rel = nullptr;
+    p->d_frac = nullptr;
+    p->d_err = nullptr;
+    p->d_scratch = nullptr;
+    p->d_io_frame = p->d_io_image = nullptr;
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const std::vector<T> &src) {
+    size_t bytes = std::max<size_t>(src.size() * sizeof(T), 16);
+    cudaError_t e = cudaMalloc((void **)dst, bytes);
+    if (e != cudaSuccess) return e;
+    if (!src.empty())
+        e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+size_t beam_smem_bytes(const HostPlan &hp) {
+    const size_t eb = chan_elem_bytes(hp.chan_prec);
+    const size_t win = ((size_t)hp.mic_chunk * hp.window * eb + 127) & ~(size_t)127;
+    const size_t tabs = (size_t)hp.mic_chunk * kGroup * 4 * (hp.delay_mode ? 2 : 1);
+    return 128 + win + tabs;
+}
+
+size_t env_smem_bytes(const HostPlan &hp) {
+    if (hp.L == 0) return 0;
+    const int H = (hp.L - 1) / 2;
+    return sizeof(float) * ((size_t)kEnvTile + 2 * H + hp.L);
+}
+
+void mark(dmas_plan *p, int k, cudaStream_t s) {
+    if (p->profiling) cudaEventRecord(p->ev[k], s);
+}
+
+// Enqueue the whole path for one frame with the given scratch.
+dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, float *d_y,
+                          float *d_cf, void *scratch, cudaStream_t s) {
+    const HostPlan &hp = p->hp;
+    cudaError_t e;
+    mark(p, 0, s);
+    // K1: roots
+    RootsParams rp;
+    rp.frame = d_frame;
+    rp.chan = scratch;
+    rp.N = hp.N;
+    rp.T = hp.T;
+    rp.row = hp.row;
+    rp.padl = hp.padl;
+    rp.order = hp.order;
+    rp.inv_order = 1.0f / (float)hp.order;
+    const size_t total = (size_t)hp.N * hp.row;
+    const unsigned rgrid = (unsigned)std::min<size_t>((total + 255) / 256, 148 * 32);
+    switch (hp.chan_prec) {
+        case DMAS_CH_F16: roots_kernel<__half><<<rgrid, 256, 0, s>>>(rp); break;
+        case DMAS_CH_BF16: roots_kernel<__nv_bfloat16><<<rgrid, 256, 0, s>>>(rp); break;
+        default: roots_kernel<float><<<rgrid, 256, 0, s>>>(rp); break;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(p, e, "roots_kernel launch");
+    mark(p, 1, s);
+
+    // K2: beamform into y (the image itself without the envelope)
+    const bool env = hp.L > 0;
+    float *ybuf = d_image;
+    if (env) ybuf = d_y ? d_y : (float *)((char *)scratch + align256(p->chan_bytes));
+    BeamParams bp;
+    bp.chan = scratch;
+    bp.gdir = p->d_gdir;
+    bp.gws = p->d_gws;
+    bp.rel = p->d_rel;
+    bp.frac = p->d_frac;
+    bp.y = ybuf;
+    bp.cf = d_cf;
+    bp.err = p->d_err;
+    bp.N = hp.N;
+    bp.T = hp.T;
+    bp.row = hp.row;
+    bp.padl = hp.padl;
+    bp.window = hp.window;
+    bp.mic_chunk = hp.mic_chunk;
+    bp.n_groups = hp.n_groups;
+    bp.n_mics_f = (float)hp.N;
+    bp.cf_eps = (float)hp.cf_eps;
+    bp.use_cf = (hp.flags & DMAS_F_CF) ? 1 : 0;
+    const unsigned bgrid = (unsigned)((size_t)hp.n_groups * hp.n_tiles);
+    e = kBeamLaunchers[hp.order](bp, hp.delay_mode, hp.chan_prec, hp.ng_prec, bgrid,
+                                 p->smem_beam, s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "beamform_kernel launch");
+    mark(p, 2, s);
+
+    if (!env) {
+        if (d_y && d_y != d_image) {
+            e = cudaMemcpyAsync(d_y, d_image, sizeof(float) * (size_t)hp.M * hp.T,
+                                cudaMemcpyDeviceToDevice, s);
+            if (e != cudaSuccess) return cuda_fail(p, e, "copy of y");
+        }
+        mark(p, 3, s);
+        p->env_ran = false;
+        p->profiled_once = p->profiled_once || p->profiling;
+        return DMAS_OK;
+    }
+    // K3: envelope
+    EnvParams ep;
+    ep.y = ybuf;
+    ep.img = d_image;
+    ep.T = hp.T;
+    ep.n_tiles = (hp.T + kEnvTile - 1) / kEnvTile;
+    ep.L = hp.L;
+    const unsigned egrid = (unsigned)((size_t)hp.M * ep.n_tiles);
+    const int H = (hp.L - 1) / 2;
+    if (H == 90)
+        envelope_kernel<90><<<egrid, kEnvThreads, p->smem_env, s>>>(ep, p->taps);
+    else if (H == 80)
+        envelope_kernel<80><<<egrid, kEnvThreads, p->smem_env, s>>>(ep, p->taps);
+    else
+        envelope_kernel<-1><<<egrid, kEnvThreads, p->smem_env, s>>>(ep, p->taps);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(p, e, "envelope_kernel launch");
+    mark(p, 3, s);
+    p->env_ran = true;
+    p->profiled_once = p->profiled_once || p->profiling;
+    return DMAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dmas_version(void) { return 100; }
+
+const char *dmas_status_string(dmas_status s) {
+    switch (s) {
+        case DMAS_OK: return "ok";
+        case DMAS_EINVAL: return "invalid argument";
+        case DMAS_ENOMEM: return "out of memory";
+        case DMAS_ECUDA: return "CUDA error";
+        case DMAS_EBUSY: return "busy";
+        case DMAS_ETIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+dmas_status dmas_plan_create(const dmas_plan_desc *desc, dmas_plan **out) {
+    if (!out) return DMAS_EINVAL;
+    *out = nullptr;
+    if (!desc) return DMAS_EINVAL;
+    dmas_plan *p = new (std::nothrow) dmas_plan();
+    if (!p) return DMAS_ENOMEM;
+    std::string why;
+    dmas_status st;
+    try {
+        st = build_host_plan(*desc, p->hp, &why);
+    } catch (const std::bad_alloc &) {
+        delete p;
+        return DMAS_ENOMEM;
+    }
+    if (st != DMAS_OK) {
+        delete p;
+        return st;
+    }
+    HostPlan &hp = p->hp;
+    cudaGetDevice(&p->device);
+    p->smem_beam = beam_smem_bytes(hp);
+    p->smem_env = env_smem_bytes(hp);
+    for (int k = 0; k < hp.L; ++k) p->taps.h[k] = hp.taps[k];
+    cudaError_t e;
+    if ((e = upload(&p->d_gdir, hp.gdir)) != cudaSuccess ||
+        (e = upload(&p->d_gws, hp.gws)) != cudaSuccess ||
+        (e = upload(&p->d_rel, hp.rel)) != cudaSuccess ||
+        (e = upload(&p->d_frac, hp.gfrac)) != cudaSuccess) {
+        free_plan_memory(p);
+        delete p;
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? DMAS_ENOMEM : DMAS_ECUDA;
+    }
+    p->table_bytes = (hp.gdir.size() + hp.gws.size() + hp.rel.size()) * 4 + hp.gfrac.size() * 4;
+    p->chan_bytes = (size_t)hp.N * hp.row * chan_elem_bytes(hp.chan_prec);
+    p->ybuf_bytes = hp.L > 0 ? sizeof(float) * (size_t)hp.M * hp.T : 0;
+    if ((e = cudaMalloc((void **)&p->d_err, 256)) != cudaSuccess ||
+        (e = cudaMemset(p->d_err, 0, 256)) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_scratch, align256(p->chan_bytes) + align256(p->ybuf_bytes))) !=
+            cudaSuccess) {
+        free_plan_memory(p);
+        delete p;
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? DMAS_ENOMEM : DMAS_ECUDA;
+    }
+    *out = p;
+    return DMAS_OK;
+}
+
+dmas_status dmas_destroy(dmas_plan *p) {
+    if (!p) return DMAS_OK;
+    cudaDeviceSynchronize();
+    free_plan_memory(p);
+    delete p;
+    return DMAS_OK;
+}
+
+size_t dmas_plan_workspace_bytes(const dmas_plan *p) {
+    if (!p) return 0;
+    return align256(p->chan_bytes) + align256(p->ybuf_bytes);
+}
+
+dmas_status dmas_beamform(dmas_plan *p, const float *d_frame, float *d_image, float *d_y,
+                          float *d_cf, void *stream) {
+    if (!p || !d_frame || !d_image) return DMAS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    return enqueue_frame(p, d_frame, d_image, d_y, d_cf, p->d_scratch, s);
+}
+
+dmas_status dmas_beamform_host(dmas_plan *p, const float *h_frame, float *h_image,
+                               void *stream) {
+    if (!p || !h_frame || !h_image) return DMAS_EINVAL;
+    const HostPlan &hp = p->hp;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t fbytes = sizeof(float) * (size_t)hp.N * hp.T;
+    const size_t ibytes = sizeof(float) * (size_t)hp.M * hp.T;
+    cudaError_t e;
+    if (!p->d_io_frame && cudaMalloc((void **)&p->d_io_frame, fbytes) != cudaSuccess) {
+        p->d_io_frame = nullptr;
+        cudaGetLastError();
+        return DMAS_ENOMEM;
+    }
+    if (!p->d_io_image && cudaMalloc((void **)&p->d_io_image, ibytes) != cudaSuccess) {
+        p->d_io_image = nullptr;
+        cudaGetLastError();
+        return DMAS_ENOMEM;
+    }
+    p->last_stream = s;
+    if ((e = cudaMemcpyAsync(p->d_io_frame, h_frame, fbytes, cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+        return cuda_fail(p, e, "frame upload");
+    dmas_status st =
+        enqueue_frame(p, p->d_io_frame, p->d_io_image, nullptr, nullptr, p->d_scratch, s);
+    if (st != DMAS_OK) return st;
+    if ((e = cudaMemcpyAsync(h_image, p->d_io_image, ibytes, cudaMemcpyDeviceToHost, s)) !=
+        cudaSuccess)
+        return cuda_fail(p, e, "image download");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(p, e, "synchronise");
+    return DMAS_OK;
+}
+
+size_t dmas_batch_workspace_bytes(int count, dmas_plan *const *plans) {
+    if (count < 1 || !plans) return 0;
+    size_t total = 0;
+    for (int k = 0; k < count; ++k) {
+        if (!plans[k]) return 0;
+        total += dmas_plan_workspace_bytes(plans[k]);
+    }
+    return total;
+}
+
+dmas_status dmas_beamform_batch(int count, dmas_plan *const *plans, const float *const *d_frames,
+                                float *const *d_images, void *d_workspace, size_t workspace_bytes,
+                                void *stream) {
+    if (count < 1 || !plans || !d_frames || !d_images || !d_workspace) return DMAS_EINVAL;
+    for (int k = 0; k < count; ++k)
+        if (!plans[k] || !d_frames[k] || !d_images[k]) return DMAS_EINVAL;
+    if (((uintptr_t)d_workspace & 255) != 0) return DMAS_EINVAL;
+    if (workspace_bytes < dmas_batch_workspace_bytes(count, plans)) return DMAS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *ws = (char *)d_workspace;
+    for (int k = 0; k < count; ++k) {
+        plans[k]->last_stream = s;
+        dmas_status st = enqueue_frame(plans[k], d_frames[k], d_images[k], nullptr, nullptr, ws, s);
+        if (st != DMAS_OK) return st;
+        ws += dmas_plan_workspace_bytes(plans[k]);
+    }
+    return DMAS_OK;
+}
+
+dmas_status dmas_plan_get_info(const dmas_plan *p, dmas_plan_info *info) {
+    if (!p || !info) return DMAS_EINVAL;
+    const HostPlan &hp = p->hp;
+    info->n_mics = hp.N;
+    info->n_dirs = hp.M;
+    info->n_samples = hp.T;
+    info->order = hp.order;
+    info->delay_mode = hp.delay_mode;
+    info->flags = hp.flags;
+    info->chan_prec = hp.chan_prec;
+    info->ng_prec = hp.ng_prec;
+    info->env_taps = hp.L;
+    info->n_groups = hp.n_groups;
+    info->group_size = kGroup;
+    info->window = hp.window;
+    info->mic_chunk = hp.mic_chunk;
+    info->time_tile = kTimeTile;
+    info->workspace_bytes = dmas_plan_workspace_bytes(p);
+    info->table_bytes = p->table_bytes;
+    return DMAS_OK;
+}
+
+dmas_status dmas_plan_get_delays(const dmas_plan *p, int32_t *shift, float *frac) {
+    if (!p || !shift) return DMAS_EINVAL;
+    std::memcpy(shift, p->hp.shift.data(), p->hp.shift.size() * sizeof(int32_t));
+    if (frac) std::memcpy(frac, p->hp.frac.data(), p->hp.frac.size() * sizeof(float));
+    return DMAS_OK;
+}
+
+dmas_status dmas_plan_get_taps(const dmas_plan *p, float *taps) {
+    if (!p || !taps) return DMAS_EINVAL;
+    if (p->hp.L > 0) std::memcpy(taps, p->hp.taps.data(), sizeof(float) * p->hp.L);
+    return DMAS_OK;
+}
+
+dmas_status dmas_plan_check(dmas_plan *p) {
+    if (!p) return DMAS_EINVAL;
+    cudaError_t e = cudaStreamSynchronize(p->last_stream);
+    if (e != cudaSuccess) return cuda_fail(p, e, "synchronise");
+    unsigned word = 0;
+    if ((e = cudaMemcpy(&word, p->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(p, e, "error word read");
+    if (word) {
+        cudaMemset(p->d_err, 0, sizeof(unsigned));
+        p->last_error = "a device wait timed out";
+        return DMAS_ETIMEOUT;
+    }
+    return DMAS_OK;
+}
+
+const char *dmas_plan_last_error(const dmas_plan *p) {
+    if (!p) return "";
+    return p->last_error.c_str();
+}
+
+dmas_status dmas_plan_set_profiling(dmas_plan *p, int enable) {
+    if (!p) return DMAS_EINVAL;
+    if (enable && !p->ev[0]) {
+        for (auto &e : p->ev) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return cuda_fail(p, r, "event create");
+        }
+    }
+    p->profiling = enable != 0;
+    return DMAS_OK;
+}
+
+dmas_status dmas_plan_stage_ms(dmas_plan *p, float *roots_ms, float *beam_ms, float *env_ms) {
+    if (!p || !p->profiled_once || !p->ev[0]) return DMAS_EINVAL;
+    cudaError_t e = cudaEventSynchronize(p->ev[3]);
+    if (e != cudaSuccess) return cuda_fail(p, e, "event synchronise");
+    float t[3] = {0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+        e = cudaEventElapsedTime(&t[k], p->ev[k], p->ev[k + 1]);
+        if (e != cudaSuccess) return cuda_fail(p, e, "event elapsed");
+    }
+    if (roots_ms) *roots_ms = t[0];
+    if (beam_ms) *beam_ms = t[1];
+    if (env_ms) *env_ms = p->env_ran ? t[2] : 0.0f;
+    return DMAS_OK;
+}
+
+dmas_status dmas_selftest_wait_timeout(double limit_ms, void *stream) {
+    if (!(limit_ms >= 1.0 && limit_ms <= 10000.0)) return DMAS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned *d_err = nullptr;
+    cudaError_t e = cudaMalloc((void **)&d_err, sizeof(unsigned));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? DMAS_ENOMEM : DMAS_ECUDA;
+    }
+    unsigned word = 0;
+    if ((e = cudaMemsetAsync(d_err, 0, sizeof(unsigned), s)) == cudaSuccess) {
+        wait_timeout_selftest_kernel<<<1, 32, 0, s>>>(
+            d_err, (unsigned long long)(limit_ms * 1.0e6));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&word, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(d_err);
+    if (e != cudaSuccess) return DMAS_ECUDA;
+    return word ? DMAS_ETIMEOUT : DMAS_OK;
+}
+
+}  // extern "C"

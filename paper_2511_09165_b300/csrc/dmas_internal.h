@@ -1,0 +1,61 @@
+// Private declarations shared by the host plan builder (dmas_plan.cpp) and the
+// CUDA side of the library (dmas_api.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dmas.h"
+
+namespace dmas {
+
+// Directions per CTA row ("group"): one warp of the beamform kernel per direction.
+constexpr int kGroup = 8;
+// Output samples per CTA along t (8 per lane, lanes strided by one sample).
+constexpr int kTimeTile = 256;
+// Sample alignment of every staged window start and length (8 elements = 32 B
+// of FP32, 16 B of FP16/BF16: every bulk copy starts and ends 16-byte aligned).
+constexpr int kAlign = 8;
+// Largest envelope FIR.
+constexpr int kMaxTaps = 1023;
+// Shared memory a beamform CTA may use for its staged windows (two CTAs per SM).
+constexpr size_t kWindowSmemBudget = 96 * 1024;
+
+// Host-side result of planning: everything the device needs, before upload.
+struct HostPlan {
+    // desc, normalised
+    int N = 0, M = 0, T = 0, order = 0, delay_mode = 0, flags = 0;
+    int chan_prec = 0, ng_prec = 0;
+    double fs = 0.0, c = 0.0, cf_eps = 1e-30, env_fc = 5000.0;
+    int L = 0;  // envelope taps (0 without DMAS_F_ENVELOPE)
+
+    // delay table in desc order: shift[M*N], frac[M*N]
+    std::vector<int32_t> shift;
+    std::vector<float> frac;
+
+    // grouping
+    int n_groups = 0;
+    std::vector<int32_t> gdir;  // [n_groups * kGroup], -1 = empty slot
+    std::vector<int32_t> gws;   // [n_groups * N] window start relative to t0
+    std::vector<int32_t> rel;   // [n_groups][N][kGroup] shift - window start
+    std::vector<float> gfrac;   // [n_groups][N][kGroup] interpolation weight f
+
+    int window = 0;      // staged samples per microphone row (multiple of kAlign)
+    int mic_chunk = 0;   // microphones staged per pass
+    int n_tiles = 0;     // time tiles of kTimeTile
+    int padl = 0;        // zero samples before t = 0 in the root channel rows
+    int row = 0;         // root channel row length (multiple of kAlign)
+
+    std::vector<float> taps;  // [L]
+};
+
+// Validate the desc and build the host tables.  Returns DMAS_OK or DMAS_EINVAL
+// with a reason in *why.
+dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *why);
+
+// Bytes of one element of the root channel for a dmas_chan_prec.
+inline size_t chan_elem_bytes(int chan_prec) { return chan_prec == DMAS_CH_F32 ? 4 : 2; }
+
+}  // namespace dmas

@@ -1,0 +1,486 @@
+// Device code of the DMAS-CF beamformer for sm_103a.
+//
+//   roots_kernel      per microphone sample: s = sgn(m)|m|^(1/n) (Sec. II-B),
+//                     written into a zero-padded channel row so the beamform
+//                     kernel never tests bounds (samples outside the frame are
+//                     zero).
+//   beamform_kernel   one CTA per (group of 8 neighbouring directions, tile of
+//                     256 output samples).  The bulk-copy (TMA) engine stages
+//                     each microphone's window of roots into shared memory;
+//                     each warp owns one direction and each lane 8 samples
+//                     (strided by 32, so every gather is one contiguous
+//                     128-byte shared-memory row).  Per pixel it accumulates
+//                     the power sums P_1..P_n (Eq. power_sum) plus sum x and
+//                     sum x^2 in FP32 registers, then applies Newton-Girard
+//                     (Eqs. dmas2_impl..dmas5_impl, or the recurrence for
+//                     n > 5) and the coherence factor (Eq. cf).
+//   envelope_kernel   |y| then a zero-phase FIR low-pass along t.
+//
+// Every wait on an mbarrier is bounded by wall-clock time (globaltimer); on
+// expiry the kernel sets a bit in the plan's error word and returns.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dmas {
+
+constexpr int kThreads = 256;      // 8 warps, one direction each
+constexpr int kPix = 8;            // output samples per lane (kTimeTile / 32)
+constexpr unsigned kErrTimeout = 1u;
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier, giving up after limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long start = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - start > limit_ns) return false;
+    }
+    return true;
+}
+
+// 1-D bulk copy global -> shared, completion counted in bytes on `bar`.
+// Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes,
+                                         uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// channel element conversions
+// ---------------------------------------------------------------------------
+template <typename CH> __device__ __forceinline__ float ld_ch(const CH *p);
+template <> __device__ __forceinline__ float ld_ch<float>(const float *p) { return *p; }
+template <> __device__ __forceinline__ float ld_ch<__half>(const __half *p) {
+    return __half2float(*p);
+}
+template <> __device__ __forceinline__ float ld_ch<__nv_bfloat16>(const __nv_bfloat16 *p) {
+    return __bfloat162float(*p);
+}
+template <typename CH> __device__ __forceinline__ CH to_ch(float v);
+template <> __device__ __forceinline__ float to_ch<float>(float v) { return v; }
+template <> __device__ __forceinline__ __half to_ch<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 to_ch<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+
+// ---------------------------------------------------------------------------
+// K1: signed n-th roots into zero-padded channel rows
+// ---------------------------------------------------------------------------
+struct RootsParams {
+    const float *frame;  // [N][T]
+    void *chan;          // [N][row] CH
+    int N, T, row, padl, order;
+    float inv_order;
+};
+
+__device__ __forceinline__ float signed_root(float m, int order, float inv_order) {
+    switch (order) {
+        case 1: return m;
+        case 2: return copysignf(sqrtf(fabsf(m)), m);
+        case 3: return cbrtf(m);
+        default: return copysignf(powf(fabsf(m), inv_order), m);
+    }
+}
+
+template <typename CH>
+__global__ void __launch_bounds__(256) roots_kernel(const __grid_constant__ RootsParams p) {
+    const size_t total = (size_t)p.N * (size_t)p.row;
+    CH *chan = reinterpret_cast<CH *>(p.chan);
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / (size_t)p.row);
+        const int c = (int)(idx - (size_t)i * p.row);
+        const int t = c - p.padl;
+        float r = 0.0f;
+        if (t >= 0 && t < p.T) r = signed_root(p.frame[(size_t)i * p.T + t], p.order, p.inv_order);
+        chan[idx] = to_ch<CH>(r);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Newton-Girard: E_n from power sums P[1..n]
+// ---------------------------------------------------------------------------
+enum { NG_F32 = 0, NG_F64 = 1, NG_CF32 = 2 };
+
+// The paper's pre-expanded equations for n <= 5, the recurrence
+// k e_k = sum_{i=1..k} (-1)^(i-1) e_{k-i} P_i above that.
+template <int ORDER, typename R>
+__device__ __forceinline__ R newton_girard(const R (&P)[ORDER + 1]) {
+    if constexpr (ORDER == 1) {
+        return P[1];
+    } else if constexpr (ORDER == 2) {
+        return (R)0.5 * (P[1] * P[1] - P[2]);
+    } else if constexpr (ORDER == 3) {
+        const R p1 = P[1];
+        return (p1 * p1 * p1 + (R)2 * P[3] - (R)3 * p1 * P[2]) * ((R)1 / (R)6);
+    } else if constexpr (ORDER == 4) {
+        const R p1 = P[1], p2 = P[2], q = p1 * p1;
+        return (q * q - (R)6 * P[4] + (R)3 * p2 * p2 - (R)6 * p2 * q + (R)8 * P[3] * p1) *
+               ((R)1 / (R)24);
+    } else if constexpr (ORDER == 5) {
+        const R p1 = P[1], p2 = P[2], p3 = P[3], q = p1 * p1;
+        return (q * q * p1 - (R)10 * p2 * q * p1 + (R)15 * p2 * p2 * p1 + (R)20 * p3 * q -
+                (R)20 * p3 * p2 - (R)30 * p1 * P[4] + (R)24 * P[5]) *
+               ((R)1 / (R)120);
+    } else {
+        R e[ORDER + 1];
+        e[0] = (R)1;
+#pragma unroll
+        for (int k = 1; k <= ORDER; ++k) {
+            R s = (R)0;
+#pragma unroll
+            for (int i = 1; i <= k; ++i) {
+                const R term = e[k - i] * P[i];
+                s = (i & 1) ? s + term : s - term;
+            }
+            e[k] = s / (R)k;
+        }
+        return e[ORDER];
+    }
+}
+
+// Double-float ("compensated FP32") numbers: value = hi + lo, |lo| <= ulp(hi)/2.
+// Error-free transformations: Knuth's TwoSum and the FMA-based TwoProduct
+// (Dekker; Ogita, Rump and Oishi).  The _rn intrinsics keep the compiler from
+// fusing or reassociating the steps.
+struct dfloat {
+    float hi, lo;
+};
+__device__ __forceinline__ dfloat df_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ dfloat df_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ dfloat df_add(dfloat x, dfloat y) {
+    dfloat s = df_two_sum(x.hi, y.hi);
+    const float lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    return df_fast_two_sum(s.hi, lo);
+}
+__device__ __forceinline__ dfloat df_neg(dfloat x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ dfloat df_mul(dfloat x, dfloat y) {
+    const float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, e));
+    return df_fast_two_sum(p, e);
+}
+// x / k for a small positive integer k: exact remainder by FMA, then a
+// second quotient for the low part.
+__device__ __forceinline__ dfloat df_div_int(dfloat x, float k) {
+    const float q1 = __fdiv_rn(x.hi, k);
+    const float r = __fadd_rn(__fmaf_rn(-q1, k, x.hi), x.lo);
+    const float q2 = __fdiv_rn(r, k);
+    return df_fast_two_sum(q1, q2);
+}
+
+template <int ORDER>
+__device__ __forceinline__ float newton_girard_cf32(const float (&P)[ORDER + 1]) {
+    dfloat e[ORDER + 1];
+    e[0] = {1.0f, 0.0f};
+#pragma unroll
+    for (int k = 1; k <= ORDER; ++k) {
+        dfloat s = {0.0f, 0.0f};
+#pragma unroll
+        for (int i = 1; i <= k; ++i) {
+            const dfloat term = df_mul(e[k - i], dfloat{P[i], 0.0f});
+            s = df_add(s, (i & 1) ? term : df_neg(term));
+        }
+        e[k] = df_div_int(s, (float)k);
+    }
+    return __fadd_rn(e[ORDER].hi, e[ORDER].lo);
+}
+
+template <int ORDER, int NGP>
+__device__ __forceinline__ float esym_from_power_sums(const float (&P)[ORDER + 1]) {
+    if constexpr (NGP == NG_F64) {
+        double D[ORDER + 1];
+#pragma unroll
+        for (int k = 0; k <= ORDER; ++k) D[k] = (double)P[k];
+        return (float)newton_girard<ORDER, double>(D);
+    } else if constexpr (NGP == NG_CF32) {
+        return newton_girard_cf32<ORDER>(P);
+    } else {
+        return newton_girard<ORDER, float>(P);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K2: gather + power sums + Newton-Girard + CF
+// ---------------------------------------------------------------------------
+struct BeamParams {
+    const void *chan;    // [N][row] roots, zero padded
+    const int *gdir;     // [n_groups * 8] direction index or -1
+    const int *gws;      // [n_groups][N] window start relative to t0
+    const int *rel;      // [n_groups][N][8] shift relative to window start
+    const float *frac;   // [n_groups][N][8] interpolation weight (LINEAR)
+    float *y;            // [M][T] E_n (x CF)
+    float *cf;           // [M][T] or nullptr
+    unsigned *err;       // error word
+    int N, T, row, padl, window, mic_chunk, n_groups;
+    float n_mics_f, cf_eps;
+    int use_cf;
+};
+
+// Running sums per pixel: P_1..P_n, sum x, sum x^2, where for odd n
+// P_n == sum x (s^n = x), so P_n is not kept separately.
+template <int ORDER> struct SumLayout {
+    static constexpr bool kPnIsA = (ORDER & 1) != 0;
+    static constexpr int kNumP = kPnIsA ? ORDER - 1 : ORDER;  // P_1..P_kNumP stored
+    static constexpr int kNum = kNumP + 2;                    // + A, B
+};
+
+// Accumulate one delayed root s (x rebuilt from it as sgn(s)|s|^n) with weight w.
+template <int ORDER, bool WEIGHTED>
+__device__ __forceinline__ void accumulate(float (&a)[SumLayout<ORDER>::kNum], float s,
+                                           float w) {
+    constexpr int NP = SumLayout<ORDER>::kNumP;
+    float pw = s;
+    if constexpr (NP >= 1) a[0] = WEIGHTED ? fmaf(w, s, a[0]) : a[0] + s;
+#pragma unroll
+    for (int q = 2; q <= ORDER; ++q) {
+        pw *= s;
+        if (q <= NP) a[q - 1] = WEIGHTED ? fmaf(w, pw, a[q - 1]) : a[q - 1] + pw;
+    }
+    const float x = (ORDER & 1) ? pw : copysignf(pw, s);
+    a[NP] = WEIGHTED ? fmaf(w, x, a[NP]) : a[NP] + x;
+    const float wx = WEIGHTED ? w * x : x;
+    a[NP + 1] = fmaf(wx, x, a[NP + 1]);
+}
+
+template <int ORDER, bool LINEAR, typename CH, int NGP>
+__global__ void __launch_bounds__(kThreads, 2)
+    beamform_kernel(const __grid_constant__ BeamParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int NA = SumLayout<ORDER>::kNum;
+    constexpr int NP = SumLayout<ORDER>::kNumP;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    const int WS = p.window;
+    const int NC = p.mic_chunk;
+    CH *win = reinterpret_cast<CH *>(smem + 128);
+    const size_t win_bytes = ((size_t)NC * WS * sizeof(CH) + 127) & ~(size_t)127;
+    int *s_rel = reinterpret_cast<int *>(smem + 128 + win_bytes);
+    float *s_frac = reinterpret_cast<float *>(s_rel + NC * 8);
+
+    const int tile = (int)(blockIdx.x / (unsigned)p.n_groups);
+    const int g = (int)(blockIdx.x - (unsigned)tile * (unsigned)p.n_groups);
+    const int t0 = tile * (32 * kPix);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    float acc[kPix][NA];
+#pragma unroll
+    for (int k = 0; k < kPix; ++k)
+#pragma unroll
+        for (int j = 0; j < NA; ++j) acc[k][j] = 0.0f;
+
+    const CH *chan = reinterpret_cast<const CH *>(p.chan);
+    uint32_t parity = 0;
+    for (int c0 = 0; c0 < p.N; c0 += NC) {
+        const int nc = min(NC, p.N - c0);
+        if (c0 > 0) __syncthreads();  // every warp is done with the previous chunk
+        if (warp == 0) {
+            const uint32_t row_bytes = (uint32_t)(WS * sizeof(CH));
+            const uint32_t tab_bytes = (uint32_t)(nc * 8 * 4);
+            if (lane == 0)
+                mbar_arrive_expect_tx(bar, nc * row_bytes + tab_bytes * (LINEAR ? 2u : 1u));
+            __syncwarp();
+            for (int il = lane; il < nc; il += 32) {
+                const int i = c0 + il;
+                const CH *src =
+                    chan + (size_t)i * p.row + p.padl + t0 + p.gws[(size_t)g * p.N + i];
+                bulk_g2s(win + (size_t)il * WS, src, row_bytes, bar);
+            }
+            if (lane == 0) {
+                bulk_g2s(s_rel, p.rel + ((size_t)g * p.N + c0) * 8, tab_bytes, bar);
+                if (LINEAR) bulk_g2s(s_frac, p.frac + ((size_t)g * p.N + c0) * 8, tab_bytes, bar);
+            }
+        }
+        const bool ok = mbar_wait_bounded(bar, parity);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(p.err, kErrTimeout);
+                mbar_wait_bounded(bar, parity);  // let copies in flight land
+            }
+            return;
+        }
+        parity ^= 1u;
+
+#pragma unroll 2
+        for (int il = 0; il < nc; ++il) {
+            const int off = s_rel[il * 8 + warp];
+            const CH *rowp = win + (size_t)il * WS + off + lane;
+            if constexpr (LINEAR) {
+                const float f = s_frac[il * 8 + warp];
+                const float w0 = 1.0f - f;
+#pragma unroll
+                for (int k = 0; k < kPix; ++k) {
+                    const float a = ld_ch<CH>(rowp + 32 * k);
+                    const float b = ld_ch<CH>(rowp + 32 * k + 1);
+                    accumulate<ORDER, true>(acc[k], a, w0);
+                    accumulate<ORDER, true>(acc[k], b, f);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kPix; ++k)
+                    accumulate<ORDER, false>(acc[k], ld_ch<CH>(rowp + 32 * k), 0.0f);
+            }
+        }
+    }
+
+    const int dir = p.gdir[(size_t)g * 8 + warp];
+    if (dir < 0) return;
+    float *yrow = p.y + (size_t)dir * p.T;
+    float *cfrow = p.cf ? p.cf + (size_t)dir * p.T : nullptr;
+#pragma unroll
+    for (int k = 0; k < kPix; ++k) {
+        const int t = t0 + lane + 32 * k;
+        if (t >= p.T) continue;
+        float P[ORDER + 1];
+        P[0] = 0.0f;
+#pragma unroll
+        for (int q = 1; q <= NP; ++q) P[q] = acc[k][q - 1];
+        const float A = acc[k][NP], B = acc[k][NP + 1];
+        if constexpr (SumLayout<ORDER>::kPnIsA) P[ORDER] = A;
+        const float E = esym_from_power_sums<ORDER, NGP>(P);
+        const float cf = (A * A) / fmaf(p.n_mics_f, B, p.cf_eps);
+        yrow[t] = p.use_cf ? E * cf : E;
+        if (cfrow) cfrow[t] = cf;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K3: envelope, |y| filtered along t with a zero-phase FIR
+// ---------------------------------------------------------------------------
+constexpr int kEnvThreads = 128;
+constexpr int kEnvR = 8;                              // outputs per lane
+constexpr int kEnvTile = kEnvThreads * kEnvR;         // outputs per CTA
+
+struct EnvParams {
+    const float *y;   // [M][T]
+    float *img;       // [M][T]
+    int T, n_tiles, L;
+};
+struct EnvTaps {
+    float h[1023];
+};
+
+// HH >= 0: taps length 2*HH+1 fixed at compile time (taps read straight from
+// the parameter bank); HH < 0: any length, taps from shared memory.
+template <int HH>
+__global__ void __launch_bounds__(kEnvThreads)
+    envelope_kernel(const __grid_constant__ EnvParams p, const __grid_constant__ EnvTaps taps) {
+    extern __shared__ __align__(16) float s_abs[];
+    const int H = (HH >= 0) ? HH : (p.L - 1) / 2;
+    const int rowi = (int)(blockIdx.x / (unsigned)p.n_tiles);
+    const int tile = (int)(blockIdx.x - (unsigned)rowi * (unsigned)p.n_tiles);
+    const int t0 = tile * kEnvTile;
+    const float *y = p.y + (size_t)rowi * p.T;
+    const int span = kEnvTile + 2 * H;
+    for (int idx = threadIdx.x; idx < span; idx += kEnvThreads) {
+        const int t = t0 - H + idx;
+        s_abs[idx] = (t >= 0 && t < p.T) ? fabsf(y[t]) : 0.0f;
+    }
+    float *s_h = s_abs + span;
+    if constexpr (HH < 0) {
+        for (int k = threadIdx.x; k < p.L; k += kEnvThreads) s_h[k] = taps.h[k];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int base = warp * 32 * kEnvR;  // first output of this warp, relative to t0
+    float acc[kEnvR];
+#pragma unroll
+    for (int j = 0; j < kEnvR; ++j) acc[j] = 0.0f;
+    // output j of this lane: t0 + base + lane + 32 j; input offset m relative to
+    // t0 + base + lane; tap index k = 32 j - m (e[t] = sum_k h[k] |y[t - k]|).
+    const float *src = s_abs + base + lane + H;
+    if constexpr (HH >= 0) {
+#pragma unroll
+        for (int m = -HH; m <= 32 * (kEnvR - 1) + HH; ++m) {
+            const float a = src[m];
+#pragma unroll
+            for (int j = 0; j < kEnvR; ++j) {
+                const int k = 32 * j - m;
+                if (k >= -HH && k <= HH) acc[j] = fmaf(taps.h[k + HH], a, acc[j]);
+            }
+        }
+    } else {
+        for (int m = -H; m <= 32 * (kEnvR - 1) + H; ++m) {
+            const float a = src[m];
+#pragma unroll
+            for (int j = 0; j < kEnvR; ++j) {
+                const int k = 32 * j - m;
+                if (k >= -H && k <= H) acc[j] = fmaf(s_h[k + H], a, acc[j]);
+            }
+        }
+    }
+    float *img = p.img + (size_t)rowi * p.T;
+#pragma unroll
+    for (int j = 0; j < kEnvR; ++j) {
+        const int t = t0 + base + lane + 32 * j;
+        if (t < p.T) img[t] = acc[j];
+    }
+}
+
+}  // namespace dmas

@@ -1,0 +1,62 @@
+// Launch helpers for the templated kernels.  Each order's beamform kernels are
+// instantiated in their own translation unit (beam_o<n>.cu) so the build runs
+// in parallel; dmas_api.cu calls launch_beamform_order<n> through a table.
+#pragma once
+
+#include <algorithm>
+#include <mutex>
+
+#include "dmas_kernels.cuh"
+
+namespace dmas {
+
+// Dynamic shared memory a beamform kernel is allowed to request (the sm_100
+// family's per-CTA opt-in maximum, 227 KB).
+constexpr int kBeamSmemOptIn = 227 * 1024;
+
+template <int ORDER, bool LINEAR, typename CH, int NGP>
+cudaError_t launch_beam_variant(const BeamParams &p, unsigned grid, size_t smem,
+                                cudaStream_t s) {
+    auto kern = beamform_kernel<ORDER, LINEAR, CH, NGP>;
+    static std::once_flag once;
+    static cudaError_t attr_err = cudaSuccess;
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kBeamSmemOptIn);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    kern<<<grid, kThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int ORDER, bool LINEAR, typename CH>
+cudaError_t launch_beam_ng(const BeamParams &p, int ngp, unsigned grid, size_t smem,
+                           cudaStream_t s) {
+    switch (ngp) {
+        case NG_F64: return launch_beam_variant<ORDER, LINEAR, CH, NG_F64>(p, grid, smem, s);
+        case NG_CF32: return launch_beam_variant<ORDER, LINEAR, CH, NG_CF32>(p, grid, smem, s);
+        default: return launch_beam_variant<ORDER, LINEAR, CH, NG_F32>(p, grid, smem, s);
+    }
+}
+
+template <int ORDER, bool LINEAR>
+cudaError_t launch_beam_ch(const BeamParams &p, int chan, int ngp, unsigned grid, size_t smem,
+                           cudaStream_t s) {
+    switch (chan) {
+        case 1: return launch_beam_ng<ORDER, LINEAR, __half>(p, ngp, grid, smem, s);
+        case 2: return launch_beam_ng<ORDER, LINEAR, __nv_bfloat16>(p, ngp, grid, smem, s);
+        default: return launch_beam_ng<ORDER, LINEAR, float>(p, ngp, grid, smem, s);
+    }
+}
+
+template <int ORDER>
+cudaError_t launch_beamform_order(const BeamParams &p, int linear, int chan, int ngp,
+                                  unsigned grid, size_t smem, cudaStream_t s) {
+    if (linear) return launch_beam_ch<ORDER, true>(p, chan, ngp, grid, smem, s);
+    return launch_beam_ch<ORDER, false>(p, chan, ngp, grid, smem, s);
+}
+
+using BeamLauncher = cudaError_t (*)(const BeamParams &, int, int, int, unsigned, size_t,
+                                     cudaStream_t);
+
+}  // namespace dmas

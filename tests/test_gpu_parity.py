@@ -1,0 +1,342 @@
+"""CUDA path against the FP64 oracle on the same seeded inputs.
+
+FP32 gate: eps_peak <= 1e-5 on E_n*CF (y) and on the envelope image, |CF err|
+<= 1e-5.  Cases span several direction groups and time tiles with ragged
+tails, every order 1..8, both delay modes, all Newton-Girard precisions, the
+reduced-precision channels, microphone chunking, and the degenerate cases.
+"""
+import functools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import scenes
+from parity import TOL_F32, db_error, eps_peak, gpu_plan, oracle_run, scene_tau
+
+torch = pytest.importorskip("torch")
+dm = pytest.importorskip("paper_2511_09165_b300")
+
+pytestmark = pytest.mark.gpu
+
+
+@functools.lru_cache(maxsize=None)
+def small_2d(T=4096):
+    return scenes.small_2d(seed=1, n_samples=T)
+
+
+@functools.lru_cache(maxsize=None)
+def hemi(T=2048, M=256):
+    return scenes.hemi_3d(seed=2, n_samples=T, n_dirs=M)
+
+
+@functools.lru_cache(maxsize=None)
+def passive(N=100, T=700, n_az=16, n_el=8):
+    return scenes.passive(seed=4, n_mics=N, n_samples=T, n_az=n_az, n_el=n_el)
+
+
+def run_gpu(scene, order, mode, want_y=True, want_cf=True, **kw):
+    plan = gpu_plan(dm, scene, order, mode, **kw)
+    frame = torch.from_numpy(scene.frame).cuda()
+    M, T = scene.n_dirs, scene.n_samples
+    y = torch.empty((M, T), device="cuda") if want_y else None
+    cf = torch.empty((M, T), device="cuda") if want_cf else None
+    img = plan(frame, y=y, cf=cf)
+    torch.cuda.synchronize()
+    plan.check()
+    out = {"img": img.cpu().numpy()}
+    if want_y:
+        out["y"] = y.cpu().numpy()
+    if want_cf:
+        out["cf"] = cf.cpu().numpy()
+    plan.close()
+    return out
+
+
+def assert_parity(g, r, tol=TOL_F32, envelope=True):
+    assert eps_peak(g["y"], r["y"]) <= tol, eps_peak(g["y"], r["y"])
+    assert float(np.max(np.abs(g["cf"] - r["cf"]))) <= max(tol, 1e-5)
+    if envelope:
+        assert eps_peak(g["img"], r["img"]) <= tol, eps_peak(g["img"], r["img"])
+
+
+# ---------------------------------------------------------------------------
+# plan tables and bounded waits
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("which", ["small_2d", "hemi", "passive"])
+def test_delay_table_matches_oracle(which):
+    sc = {"small_2d": small_2d, "hemi": hemi, "passive": passive}[which]()
+    tau = scene_tau(sc)
+    for mode in (dm.ROUND, dm.LINEAR):
+        plan = gpu_plan(dm, sc, 3, mode)
+        shift, frac = plan.delays()
+        plan.close()
+        delta = tau * sc.fs
+        if mode == dm.ROUND:
+            assert np.array_equal(shift, oracle.round_shifts(tau, sc.fs))
+            assert np.all(frac == 0)
+        else:
+            assert np.array_equal(shift, np.floor(delta).astype(np.int64))
+            np.testing.assert_allclose(frac, delta - np.floor(delta), rtol=0, atol=2 ** -24)
+
+
+def test_taps_match_oracle():
+    sc = small_2d(512)
+    plan = gpu_plan(dm, sc, 5, dm.ROUND)
+    h = plan.taps()
+    plan.close()
+    ref = oracle.fir_taps(sc.fs, 5000.0)
+    assert h.size == ref.size == 181
+    np.testing.assert_allclose(h, ref, rtol=1e-7, atol=1e-12)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    assert dm.selftest_wait_timeout(20.0) == 5   # DMAS_ETIMEOUT, by design
+    x = torch.ones(4, device="cuda")
+    assert float((x * 2).sum()) == 8.0           # the context is still usable
+
+
+def test_stage_profiling_events():
+    sc = small_2d(2048)
+    plan = gpu_plan(dm, sc, 5, dm.ROUND)
+    plan.set_profiling(True)
+    plan(torch.from_numpy(sc.frame).cuda())
+    r, b, e = plan.stage_ms()
+    plan.close()
+    assert r > 0 and b > 0 and e > 0
+
+
+# ---------------------------------------------------------------------------
+# FP32 path against the oracle
+# ---------------------------------------------------------------------------
+def test_small_2d_order5_full_frame():
+    """32 mics, 91 azimuths, 4096 samples, n = 5, nearest-sample delays, CF,
+    envelope: the whole small 2-D workload."""
+    sc = small_2d()
+    g = run_gpu(sc, 5, dm.ROUND)
+    r = oracle_run(sc, 5, oracle.ROUND)
+    assert_parity(g, r)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_every_order_round(order):
+    sc = small_2d(1000)  # 4 time tiles, the last one ragged; 12 groups, last ragged
+    g = run_gpu(sc, order, dm.ROUND)
+    r = oracle_run(sc, order, oracle.ROUND)
+    assert_parity(g, r)
+
+
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5])
+def test_every_order_linear(order):
+    sc = hemi(1500, 200)
+    g = run_gpu(sc, order, dm.LINEAR)
+    r = oracle_run(sc, order, oracle.LINEAR)
+    assert_parity(g, r)
+
+
+@pytest.mark.parametrize("ng", ["f64", "cf32"])
+@pytest.mark.parametrize("order", [3, 5, 7])
+def test_newton_girard_precisions(ng, order):
+    sc = small_2d(1000)
+    ngp = {"f64": dm.NG_F64, "cf32": dm.NG_CF32}[ng]
+    g = run_gpu(sc, order, dm.ROUND, ng_prec=ngp)
+    r = oracle_run(sc, order, oracle.ROUND)
+    assert_parity(g, r)
+
+
+def test_microphone_chunks_and_wide_delays():
+    sc = passive()  # 100 mics in a 0.4 m square
+    plan = gpu_plan(dm, sc, 3, dm.ROUND)
+    info = plan.info()
+    plan.close()
+    assert info.window > 256
+    for mode in (dm.ROUND, dm.LINEAR):
+        g = run_gpu(sc, 3, mode)
+        r = oracle_run(sc, 3, mode)
+        assert_parity(g, r)
+
+
+def test_several_staging_passes():
+    """Directions spread over the whole field in one group force a wide window,
+    so fewer microphones fit per staging pass than the array has."""
+    rng = np.random.default_rng(9)
+    N, T, M, fs = 300, 600, 16, 1000.0
+    frame = rng.standard_normal((N, T)).astype(np.float32)
+    tau = rng.integers(-60, 61, size=(M, N)) / fs
+    plan = dm.Plan(delays_s=tau, n_samples=T, fs=fs, order=3)
+    info = plan.info()
+    plan.close()
+    assert info.mic_chunk < N
+    g = _explicit(frame, tau, fs, 3, env_cutoff_hz=100.0, env_taps=15)
+    r = oracle.dmas(frame.astype(np.float64), tau, fs, 3, oracle.ROUND, use_cf=True,
+                    taps=oracle.fir_taps(fs, 100.0, 15))
+    assert_parity(g, r)
+
+
+def test_cf_and_envelope_flags():
+    sc = small_2d(700)
+    for cf in (False, True):
+        for env in (False, True):
+            g = run_gpu(sc, 4, dm.ROUND, cf=cf, envelope=env)
+            r = oracle_run(sc, 4, oracle.ROUND, cf=cf, envelope=env)
+            assert eps_peak(g["y"], r["y"]) <= TOL_F32
+            if env:
+                assert eps_peak(g["img"], r["img"]) <= TOL_F32
+            else:
+                assert np.array_equal(g["img"], g["y"])
+
+
+def test_generic_envelope_length():
+    sc = small_2d(900)
+    g = run_gpu(sc, 3, dm.ROUND, env_cutoff_hz=12000.0, env_taps=45)
+    r = oracle_run(sc, 3, oracle.ROUND, env_cutoff_hz=12000.0, env_taps=45)
+    assert_parity(g, r)
+
+
+# ---------------------------------------------------------------------------
+# reduced-precision channels (measured bounds)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("chan,tol", [("f16", 3e-3), ("bf16", 3e-2)])
+@pytest.mark.parametrize("order", [3, 5])
+def test_reduced_precision_channels(chan, tol, order):
+    sc = small_2d()
+    cp = {"f16": dm.CH_F16, "bf16": dm.CH_BF16}[chan]
+    g = run_gpu(sc, order, dm.ROUND, chan_prec=cp)
+    r = oracle_run(sc, order, oracle.ROUND)
+    ey, ei = eps_peak(g["y"], r["y"]), eps_peak(g["img"], r["img"])
+    print(f"{chan} n={order}: eps_peak y {ey:.3e} img {ei:.3e} "
+          f"dB(60) {db_error(g['img'], r['img'])}")
+    assert ey <= tol and ei <= tol
+
+
+# ---------------------------------------------------------------------------
+# degenerate inputs
+# ---------------------------------------------------------------------------
+def _explicit(frame, tau, fs, order, mode=dm.ROUND, **kw):
+    N, T = frame.shape
+    plan = dm.Plan(delays_s=tau, n_samples=T, fs=fs, order=order, delay_mode=mode, **kw)
+    x = torch.from_numpy(np.ascontiguousarray(frame, dtype=np.float32)).cuda()
+    y = torch.empty((tau.shape[0], T), device="cuda")
+    cf = torch.empty((tau.shape[0], T), device="cuda")
+    img = plan(x, y=y, cf=cf)
+    torch.cuda.synchronize()
+    plan.check()
+    plan.close()
+    return {"img": img.cpu().numpy(), "y": y.cpu().numpy(), "cf": cf.cpu().numpy()}
+
+
+@pytest.mark.parametrize("T", [1, 2, 37, 255, 256, 257])
+def test_short_frames(T):
+    rng = np.random.default_rng(T)
+    frame = rng.standard_normal((9, T)).astype(np.float32)
+    fs = 1000.0
+    tau = rng.integers(-5, 6, size=(11, 9)) / fs
+    for mode in (dm.ROUND, dm.LINEAR):
+        t = tau + (0.3 / fs if mode == dm.LINEAR else 0.0)
+        g = _explicit(frame, t, fs, 3, mode, env_cutoff_hz=100.0, env_taps=9)
+        r = oracle.dmas(frame.astype(np.float64), t, fs, 3, mode, use_cf=True,
+                        taps=oracle.fir_taps(fs, 100.0, 9))
+        assert_parity(g, r)
+
+
+def test_single_mic_and_single_direction():
+    rng = np.random.default_rng(3)
+    frame = rng.standard_normal((1, 300)).astype(np.float32)
+    tau = np.array([[2.0 / 1000.0]])
+    g = _explicit(frame, tau, 1000.0, 1, cf=False, envelope=False)
+    want = np.zeros(300, dtype=np.float32)
+    want[:298] = frame[0, 2:]
+    np.testing.assert_array_equal(g["y"][0], want)
+    g2 = _explicit(frame, tau, 1000.0, 2, cf=False, envelope=False)
+    assert np.all(np.abs(g2["y"]) <= 1e-6 * np.max(np.abs(frame)))  # E_2 of one value is 0
+
+
+def test_order_above_mic_count_is_zero():
+    rng = np.random.default_rng(4)
+    frame = rng.standard_normal((3, 400)).astype(np.float32)
+    tau = np.zeros((8, 3))
+    g = _explicit(frame, tau, 1000.0, 5, cf=False, envelope=False)
+    roots = np.abs(frame.astype(np.float64)) ** 0.2
+    scale = np.sum(roots, axis=0) ** 5          # magnitude of the largest NG term
+    assert np.all(np.abs(g["y"]) <= 1e-5 * scale[None, :])
+
+
+def test_zero_frame_and_out_of_range_delays_give_exact_zero():
+    frame = np.zeros((6, 500), dtype=np.float32)
+    g = _explicit(frame, np.zeros((10, 6)), 1000.0, 5)
+    assert np.all(g["img"] == 0) and np.all(g["y"] == 0) and np.all(g["cf"] == 0)
+    rng = np.random.default_rng(5)
+    frame = rng.standard_normal((6, 500)).astype(np.float32)
+    tau = np.full((10, 6), 900.0 / 1000.0)   # every delayed sample beyond the frame
+    g = _explicit(frame, tau, 1000.0, 3)
+    assert np.all(g["img"] == 0) and np.all(g["y"] == 0)
+
+
+def test_sign_flip_is_exact_for_odd_orders():
+    sc = small_2d(800)
+    plan = gpu_plan(dm, sc, 5, dm.ROUND)
+    x = torch.from_numpy(sc.frame).cuda()
+    y1 = torch.empty((sc.n_dirs, sc.n_samples), device="cuda")
+    y2 = torch.empty_like(y1)
+    a = plan(x, y=y1).clone()
+    b = plan(-x, y=y2)
+    torch.cuda.synchronize()
+    plan.close()
+    assert torch.equal(y1, -y2)
+    assert torch.equal(a, b)
+
+
+def test_explicit_delays_equal_geometry():
+    sc = small_2d(600)
+    tau = scene_tau(sc)
+    g1 = run_gpu(sc, 5, dm.ROUND)
+    g2 = _explicit(sc.frame, tau, sc.fs, 5)
+    np.testing.assert_array_equal(g1["y"], g2["y"])
+
+
+# ---------------------------------------------------------------------------
+# other entry points
+# ---------------------------------------------------------------------------
+def test_host_buffers_and_batch_equal_device_path():
+    sc1, sc2 = small_2d(1000), hemi(1200, 64)
+    p1 = gpu_plan(dm, sc1, 5, dm.ROUND)
+    p2 = gpu_plan(dm, sc2, 3, dm.LINEAR)
+    f1 = torch.from_numpy(sc1.frame).cuda()
+    f2 = torch.from_numpy(sc2.frame).cuda()
+    a1, a2 = p1(f1).clone(), p2(f2).clone()
+    h1 = p1.beamform_host(sc1.frame)
+    b1, b2, b3 = dm.beamform_batch([p1, p2, p1], [f1, f2, f1])
+    torch.cuda.synchronize()
+    assert np.array_equal(h1, a1.cpu().numpy())
+    assert torch.equal(b1, a1) and torch.equal(b2, a2) and torch.equal(b3, a1)
+    p1.close()
+    p2.close()
+
+
+def test_full_size_hemisphere_sampled_rows():
+    """The timed workload (2048 directions x 16384 samples, linear delays,
+    n = 5, CF, envelope) in the benchmark's launch configuration; rows sampled
+    across the direction range, plus the rows around the image peak, are
+    compared with the oracle."""
+    sc = scenes.hemi_3d(seed=2)
+    plan = gpu_plan(dm, sc, 5, dm.LINEAR)
+    x = torch.from_numpy(sc.frame).cuda()
+    y = torch.empty((sc.n_dirs, sc.n_samples), device="cuda")
+    img = plan(x, y=y)
+    torch.cuda.synchronize()
+    plan.check()
+    plan.close()
+    tau = scene_tau(sc)
+    y_all, img_all = y.cpu().numpy(), img.cpu().numpy()
+    peak_row = int(np.argmax(np.max(np.abs(y_all), axis=1)))
+    starts = sorted({0, 517, 1024, 1500, 2040, min(max(peak_row - 4, 0), 2040)})
+    peak_y = peak_i = err_y = err_i = 0.0
+    for b in starts:
+        r = oracle_run(sc, 5, oracle.LINEAR, dir_range=(b, b + 8), tau=tau)
+        peak_y = max(peak_y, np.max(np.abs(r["y"])))
+        peak_i = max(peak_i, np.max(np.abs(r["img"])))
+        err_y = max(err_y, np.max(np.abs(y_all[b:b + 8] - r["y"])))
+        err_i = max(err_i, np.max(np.abs(img_all[b:b + 8] - r["img"])))
+    assert err_y <= TOL_F32 * peak_y
+    assert err_i <= TOL_F32 * peak_i
