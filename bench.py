@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the n-th order DMAS + CF beamformer.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME]
+
+A step is one frame through the whole path (signed roots, gather + power sums
++ Newton-Girard + CF, envelope) with the frame already resident in HBM.  L2 is
+flushed (a 256 MB write) before every timed step, outside the step's CUDA
+events.  The default workload is the 3-D hemisphere scene at 5th order: 32
+microphones, 2048 directions, 16384 samples, linear (fractional) delays.
+
+Prints ONE JSON line (rank 0).  Under torchrun each rank beamforms its own
+frames on its own GPU with no data exchange (weak scaling); the step time is
+the maximum over ranks.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the reference implementation of the paper's
+method is not available as code).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from workloads import scenes  # noqa: E402
+
+METRIC = "direction·samples/s for 5th-order DMAS+CF at N=32 mics; p50/p99 frame latency"
+UNIT = "direction·samples/s"
+
+# MEASURED_PEAKS.json carries the HBM and tensor peaks; the FP32 ALU peak of
+# this path is derived from the unit counts: 148 SMs x 128 FP32 lanes x 2032 MHz.
+SM_COUNT = 148
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2032.0
+
+WORKLOADS = {
+    "hemi_3d_n5": dict(
+        scene=lambda: scenes.hemi_3d(seed=2), order=5, mode="linear",
+        text="3-D hemisphere: 32 mics in a 12 cm disc, 2048 Fibonacci directions, "
+             "16384 samples at 450 kHz, 8 reflectors, 10 dB SNR, n=5, linear delays, "
+             "CF, 181-tap envelope"),
+    "small_2d_n5": dict(
+        scene=lambda: scenes.small_2d(seed=1), order=5, mode="round",
+        text="2-D fan: 32 mics in a 12 cm disc, 91 azimuths, 4096 samples at 450 kHz, "
+             "3 reflectors, 20 dB SNR, n=5, nearest-sample delays, CF, 181-tap envelope"),
+    "passive64_n5": dict(
+        scene=lambda: scenes.passive(seed=4, n_mics=64), order=5, mode="round",
+        text="passive: 64 mics in a 0.4 m square, 8192 az/el directions, 32768 samples "
+             "at 400 kHz, 4 broadband sources, 0 dB SNR, n=5, nearest-sample delays, "
+             "CF, 161-tap envelope"),
+}
+
+
+def algorithmic_ops_per_pixel(N: int, n: int, linear: bool) -> dict:
+    """FP32 operations one output pixel needs (FADD, FMUL and FFMA each count 1):
+    N(n+2) channel accumulations (twice with interpolation), ~n(n+1)/2 + n
+    Newton-Girard mult-adds, 6 for CF and weighting; the envelope adds L."""
+    main = N * (n + 2) * (2 if linear else 1)
+    ng = n * (n + 1) // 2 + n
+    return {"main": main, "newton_girard": ng, "cf": 6, "beam_total": main + ng + 6}
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=5)
+
+    def summary(self, t0: float, t1: float) -> dict:
+        rows = []
+        for ts, line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            rows.append((ts, parts))
+        inside = [r for r in rows if t0 <= r[0] <= t1] or rows
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(p[0]) for _, p in inside if p[0].replace(".", "").isdigit()]
+        mx = [float(p[1]) for _, p in inside if p[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for _, p in inside for k in range(4)
+                          if p[3 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(inside)}
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (torchrun): barrier and max over ranks only
+# ---------------------------------------------------------------------------
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as td
+    if not td.is_initialized():
+        td.init_process_group(backend=backend)
+    return td
+
+
+def dist_max(td, value: float, device) -> float:
+    if td is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(td):
+    if td is not None:
+        td.barrier()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing
+# ---------------------------------------------------------------------------
+def oracle_sample(scene, order, linear, n_dirs):
+    import oracle
+    u = scene.dir_unit if scene.dir_unit is not None else oracle.unit_vectors(scene.dir_azel)
+    tau = oracle.geometric_delays(scene.mic_xyz, u, scene.c)
+    taps = oracle.fir_taps(scene.fs, 5000.0)
+    frame = scene.frame.astype(np.float64)
+    D = min(n_dirs, scene.n_dirs)
+    t0 = time.perf_counter()
+    oracle.dmas(frame, tau, scene.fs, order, oracle.LINEAR if linear else oracle.ROUND,
+                use_cf=True, taps=taps, dir_range=(0, D))
+    dt = time.perf_counter() - t0
+    return D * scene.n_samples, dt
+
+
+def cpu_baseline(scene, order, linear, min_s=10.0) -> dict:
+    """The oracle as it stands, on all host cores: whole frames of the workload
+    (or a direction subset if a frame takes longer than min_s), repeated until
+    at least min_s seconds of CPU work."""
+    import oracle
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    px, dt = oracle_sample(scene, order, linear, 64)
+    D = int(max(64, min(scene.n_dirs, min_s * px / dt / scene.n_samples)))
+    total_px, total_s, reps = 0, 0.0, 0
+    while total_s < min_s:
+        px, dt = oracle_sample(scene, order, linear, D)
+        total_px += px
+        total_s += dt
+        reps += 1
+    what = "all" if D == scene.n_dirs else f"directions 0..{D - 1} of"
+    return {"value": total_px / total_s, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{reps} x ({what} {scene.n_dirs} directions x {scene.n_samples} "
+                      f"samples), {total_s:.1f} s, FP64"}
+
+
+def run_reference(args, wl, scene) -> None:
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    linear = wl["mode"] == "linear"
+    cores = oracle.set_threads(os.cpu_count() or 1)
+    px, dt = oracle_sample(scene, wl["order"], linear, 16)
+    rate = px / dt
+    D = int(max(8, min(scene.n_dirs, 0.4 * rate / scene.n_samples)))  # ~0.4 s a step
+    for _ in range(args.warmup):
+        oracle_sample(scene, wl["order"], linear, D)
+    times = []
+    for _ in range(args.steps):
+        px, dt = oracle_sample(scene, wl["order"], linear, D)
+        times.append(dt)
+    value = px * len(times) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "description": wl["text"],
+                   "step": f"oracle on directions 0..{D - 1} x {scene.n_samples} samples"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{D} directions x {scene.n_samples} samples per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our path
+# ---------------------------------------------------------------------------
+def run_ours(args, wl, scene) -> None:
+    import torch
+    import paper_2511_09165_b300 as dm
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    td = dist_init(world, "nccl")
+    linear = wl["mode"] == "linear"
+    order = wl["order"]
+    plan = dm.Plan(mic_xyz=scene.mic_xyz, dir_azel=scene.dir_azel, dir_unit=scene.dir_unit,
+                   n_samples=scene.n_samples, fs=scene.fs, c=scene.c, order=order,
+                   delay_mode=dm.LINEAR if linear else dm.ROUND)
+    info = plan.info()
+    N, M, T = scene.n_mics, scene.n_dirs, scene.n_samples
+    px = M * T
+    stream = torch.cuda.current_stream(dev)
+    frame = torch.from_numpy(scene.frame).to(dev)
+    image = torch.empty((M, T), device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+    plan.set_profiling(True)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        plan(frame, out=image, stream=stream)
+    torch.cuda.synchronize(dev)
+    plan.check()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stage = []
+    dist_barrier(td)
+    torch.cuda.synchronize(dev)
+    wall0 = time.time()
+    for k in range(args.steps):
+        flush.zero_()
+        ev0[k].record(stream)
+        plan(frame, out=image, stream=stream)
+        ev1[k].record(stream)
+        stage.append(plan.stage_ms())
+    torch.cuda.synchronize(dev)
+    dist_barrier(td)
+    wall1 = time.time()
+    plan.check()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    total_ms = dist_max(td, sum(step_ms), dev)
+    ms_per_step = total_ms / args.steps
+    value = px * world * args.steps / (total_ms * 1e-3)
+    stage = np.array(stage)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    h_frame = torch.from_numpy(scene.frame).pin_memory()
+    h_image = torch.empty((M, T), dtype=torch.float32).pin_memory()
+    for _ in range(3):
+        plan.beamform_host_ptr(h_frame.data_ptr(), h_image.data_ptr(), stream=stream)
+    e2e_steps = max(3, min(args.steps, 50))
+    e2e_t = []
+    dist_barrier(td)
+    for _ in range(e2e_steps):
+        t0 = time.perf_counter()
+        plan.beamform_host_ptr(h_frame.data_ptr(), h_image.data_ptr(), stream=stream)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_total = dist_max(td, sum(e2e_t), dev)
+    clocks.stop()
+    plan.close()
+
+    if rank != 0:
+        return
+    ops = algorithmic_ops_per_pixel(N, order, linear)
+    beam_ms = float(np.mean(stage[:, 1]))
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12   # T op/s
+    achieved = ops["beam_total"] * px / (beam_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "description": wl["text"],
+                   "n_mics": N, "n_dirs": M, "n_samples": T, "order": order,
+                   "delays": wl["mode"], "l2": "flushed (256 MB write) before every step",
+                   "parallelism": f"replicas x{world}"},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99))},
+        "stage_ms": {"roots": float(np.mean(stage[:, 0])), "beamform": beam_ms,
+                     "envelope": float(np.mean(stage[:, 2]))},
+        "roofline": {"bound": "alu", "kernel": "beamform_kernel", "achieved": achieved,
+                     "peak": peak, "unit": "Top/s", "frac": achieved / peak,
+                     "ops_per_pixel": ops, "pixels_per_launch": px,
+                     "peak_source": "148 SMs x 128 FP32 lanes x 2032 MHz (unit counts)",
+                     "traffic": None},
+        "e2e": {"value": px * world * e2e_steps / e2e_total, "unit": UNIT,
+                "h2d_bytes_per_step": N * T * 4, "d2h_bytes_per_step": M * T * 4},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks.summary(wall0, wall1),
+        "plan": {"window": info.window, "mic_chunk": info.mic_chunk,
+                 "groups": info.n_groups},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene, order, linear)
+    print(json.dumps(line), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="hemi_3d_n5")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    wl = WORKLOADS[args.workload]
+    scene = wl["scene"]()
+    if args.impl == "reference":
+        run_reference(args, wl, scene)
+    else:
+        run_ours(args, wl, scene)
+
+
+if __name__ == "__main__":
+    main()

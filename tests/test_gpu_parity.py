@@ -164,7 +164,8 @@ def test_several_staging_passes():
     N, T, M, fs = 300, 600, 16, 1000.0
     frame = rng.standard_normal((N, T)).astype(np.float32)
     tau = rng.integers(-60, 61, size=(M, N)) / fs
-    plan = dm.Plan(delays_s=tau, n_samples=T, fs=fs, order=3)
+    plan = dm.Plan(delays_s=tau, n_samples=T, fs=fs, order=3, env_cutoff_hz=100.0,
+                   env_taps=15)
     info = plan.info()
     plan.close()
     assert info.mic_chunk < N
@@ -264,12 +265,13 @@ def test_order_above_mic_count_is_zero():
 
 def test_zero_frame_and_out_of_range_delays_give_exact_zero():
     frame = np.zeros((6, 500), dtype=np.float32)
-    g = _explicit(frame, np.zeros((10, 6)), 1000.0, 5)
+    env = dict(env_cutoff_hz=100.0, env_taps=9)
+    g = _explicit(frame, np.zeros((10, 6)), 1000.0, 5, **env)
     assert np.all(g["img"] == 0) and np.all(g["y"] == 0) and np.all(g["cf"] == 0)
     rng = np.random.default_rng(5)
     frame = rng.standard_normal((6, 500)).astype(np.float32)
     tau = np.full((10, 6), 900.0 / 1000.0)   # every delayed sample beyond the frame
-    g = _explicit(frame, tau, 1000.0, 3)
+    g = _explicit(frame, tau, 1000.0, 3, **env)
     assert np.all(g["img"] == 0) and np.all(g["y"] == 0)
 
 
