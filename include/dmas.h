@@ -231,6 +231,35 @@ dmas_status dmas_plan_stage_ms(dmas_plan *plan, float *roots_ms, float *beam_ms,
  */
 dmas_status dmas_selftest_wait_timeout(double limit_ms, void *stream);
 
+/*
+ * Beamform one frame without allocating anything.  This entry point has no
+ * counterpart in the paper; it exists for callers that must not allocate
+ * device memory while they process frames: a real-time sonar loop where a
+ * cudaMalloc (which can synchronise the whole device) would blow the frame
+ * deadline, or a process whose GPU memory is already reserved by another
+ * allocator so that a new cudaMalloc would fail.
+ *
+ * It runs the same kernels as dmas_beamform with the same results, but its
+ * scratch (the root channels and, with DMAS_F_ENVELOPE, the pre-envelope
+ * image) lives in one static device array of DMAS_NOALLOC_SCRATCH_BYTES that
+ * the library holds on every GPU it is loaded on until the process exits.
+ * The plan itself is created beforehand with dmas_plan_create, which does
+ * allocate (once, at set-up).
+ *   d_frame : device [N][T] float32;  d_image : device [M][T] float32.
+ * The plan's device must be the current device.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture.  Every call shares the one array: calls that
+ * overlap on the GPU (other streams, other threads) race and corrupt each
+ * other's results, so serialise them.  Nothing from an earlier call leaks into
+ * a later one: each call rewrites every byte of scratch it reads.
+ * Errors: DMAS_EINVAL (NULL argument, plan on another device, or a plan whose
+ * dmas_plan_workspace_bytes exceeds DMAS_NOALLOC_SCRATCH_BYTES; the reason is
+ * in dmas_plan_last_error), DMAS_ECUDA.
+ */
+#define DMAS_NOALLOC_SCRATCH_BYTES (16u << 20) /* 16 MiB */
+dmas_status dmas_beamform_noalloc(dmas_plan *plan, const float *d_frame, float *d_image,
+                                  void *stream);
+
 /* Static text for a status code. */
 const char *dmas_status_string(dmas_status status);
 

@@ -35,7 +35,8 @@ EXPORTS = [
     "dmas_beamform_batch", "dmas_batch_workspace_bytes", "dmas_plan_workspace_bytes",
     "dmas_plan_get_info", "dmas_plan_get_delays", "dmas_plan_get_taps", "dmas_plan_check",
     "dmas_plan_last_error", "dmas_plan_set_profiling", "dmas_plan_stage_ms",
-    "dmas_selftest_wait_timeout", "dmas_status_string", "dmas_version",
+    "dmas_selftest_wait_timeout", "dmas_beamform_noalloc", "dmas_status_string",
+    "dmas_version",
 ]
 
 
@@ -100,6 +101,7 @@ def load_library(path: str | None = None):
             "dmas_plan_set_profiling": ([vp, i], i),
             "dmas_plan_stage_ms": ([vp, fp, fp, fp], i),
             "dmas_selftest_wait_timeout": ([ctypes.c_double, vp], i),
+            "dmas_beamform_noalloc": ([vp, vp, vp, vp], i),
             "dmas_status_string": ([i], ctypes.c_char_p),
             "dmas_version": ([], i),
         }

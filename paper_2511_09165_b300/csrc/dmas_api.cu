@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -475,3 +476,75 @@ dmas_status dmas_selftest_wait_timeout(double limit_ms, void *stream) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Beamforming without any device allocation: the scratch lives in a static
+// device array that the library holds on every GPU it is loaded on.
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[DMAS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+// The array's name in host code is only a stand-in; the device address comes
+// from the runtime, looked up once per device with that device current.
+dmas_status noalloc_scratch_address(int device, void **addr, std::string *why) {
+    if (device < 0 || device >= kMaxDevices) {
+        *why = "device ordinal out of range for the static scratch table";
+        return DMAS_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            *why = std::string("cudaGetSymbolAddress of the static scratch: ") +
+                   cudaGetErrorString(e);
+            cudaGetLastError();
+            return DMAS_ECUDA;
+        }
+        g_noalloc_addr[device] = p;
+    }
+    *addr = g_noalloc_addr[device];
+    return DMAS_OK;
+}
+
+}  // namespace
+
+extern "C" dmas_status dmas_beamform_noalloc(dmas_plan *p, const float *d_frame, float *d_image,
+                                             void *stream) {
+    if (!p || !d_frame || !d_image) return DMAS_EINVAL;
+    const size_t need = dmas_plan_workspace_bytes(p);
+    if (need > DMAS_NOALLOC_SCRATCH_BYTES) {
+        p->last_error = "dmas_beamform_noalloc: this plan needs " + std::to_string(need) +
+                        " bytes of scratch, more than the static " +
+                        std::to_string((size_t)DMAS_NOALLOC_SCRATCH_BYTES) +
+                        "-byte array; use dmas_beamform";
+        return DMAS_EINVAL;
+    }
+    int device = -1;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaGetDevice");
+    if (device != p->device) {
+        p->last_error = "dmas_beamform_noalloc: the plan belongs to device " +
+                        std::to_string(p->device) + " but device " + std::to_string(device) +
+                        " is current";
+        return DMAS_EINVAL;
+    }
+    void *scratch = nullptr;
+    std::string why;
+    dmas_status st = noalloc_scratch_address(device, &scratch, &why);
+    if (st != DMAS_OK) {
+        p->last_error = why;
+        return st;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    // The roots stage rewrites the whole channel region, zero pads included,
+    // and the beamform stage writes every y sample the envelope reads, so
+    // nothing from an earlier call survives into this one.
+    return enqueue_frame(p, d_frame, d_image, nullptr, nullptr, scratch, s);
+}

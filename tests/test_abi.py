@@ -115,6 +115,7 @@ def test_null_arguments(lib):
     assert lib.dmas_plan_stage_ms(None, None, None, None) == 1
     assert lib.dmas_selftest_wait_timeout(0.0, None) == 1
     assert lib.dmas_selftest_wait_timeout(math.nan, None) == 1
+    assert lib.dmas_beamform_noalloc(None, None, None, None) == 1
 
 
 def test_python_binding_requires_geometry():

@@ -1,0 +1,65 @@
+"""dmas_beamform_noalloc: beamforming for callers that must not allocate
+device memory while processing frames (a real-time loop that cannot afford a
+cudaMalloc, which may synchronise the device, or a process whose GPU memory is
+already reserved by another allocator).  Its scratch is a static device array
+inside the library.
+
+The test calls the entry point through the C ABI twice in a row, on two
+different frames, and compares each result with dmas_beamform on the same
+plan and frame.  It lives in its own file, collected last, and passes both
+alone in a fresh process and after the rest of the suite.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from workloads import scenes
+from parity import TOL_F32, eps_peak
+
+torch = pytest.importorskip("torch")
+dm = pytest.importorskip("paper_2511_09165_b300")
+
+pytestmark = pytest.mark.gpu
+
+
+def _call_noalloc(lib, plan, frame, image):
+    stream = torch.cuda.current_stream().cuda_stream
+    return lib.dmas_beamform_noalloc(plan.handle, ctypes.c_void_p(frame.data_ptr()),
+                                     ctypes.c_void_p(image.data_ptr()),
+                                     ctypes.c_void_p(stream))
+
+
+def test_noalloc_matches_beamform_on_two_calls_in_a_row():
+    lib = dm.load_library()
+    sc = scenes.small_2d(seed=1)            # 32 mics, 91 azimuths, 4096 samples
+    plan = dm.Plan(mic_xyz=sc.mic_xyz, dir_azel=sc.dir_azel, n_samples=sc.n_samples,
+                   fs=sc.fs, c=sc.c, order=5, delay_mode=dm.ROUND)
+    assert plan.workspace_bytes() <= 16 << 20
+    frames = [torch.from_numpy(sc.frame).cuda(),
+              torch.from_numpy(scenes.small_2d(seed=11).frame).cuda()]
+    for frame in frames:
+        want = plan(frame)
+        got = torch.full_like(want, float("nan"))
+        assert _call_noalloc(lib, plan, frame, got) == 0
+        torch.cuda.synchronize()
+        plan.check()
+        w, g = want.cpu().numpy(), got.cpu().numpy()
+        assert np.all(np.isfinite(g))
+        assert eps_peak(g, w) <= TOL_F32
+    plan.close()
+
+
+def test_noalloc_rejects_plans_larger_than_its_scratch():
+    lib = dm.load_library()
+    sc = scenes.hemi_3d(seed=2, n_samples=2048, n_dirs=2048)   # 16 MiB of pre-envelope image
+    plan = dm.Plan(mic_xyz=sc.mic_xyz, dir_unit=sc.dir_unit, n_samples=sc.n_samples,
+                   fs=sc.fs, c=sc.c, order=5, delay_mode=dm.LINEAR)
+    assert plan.workspace_bytes() > 16 << 20
+    frame = torch.from_numpy(sc.frame).cuda()
+    image = torch.zeros((sc.n_dirs, sc.n_samples), device="cuda")
+    assert _call_noalloc(lib, plan, frame, image) == 1       # DMAS_EINVAL
+    msg = lib.dmas_plan_last_error(plan.handle).decode()
+    assert "static" in msg and str(16 << 20) in msg
+    assert torch.count_nonzero(image).item() == 0             # nothing was launched
+    plan.close()
