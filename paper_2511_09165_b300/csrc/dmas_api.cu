@@ -10,6 +10,7 @@
 
 #include "dmas.h"
 #include "dmas_internal.h"
+#include "dmas_envelope.cuh"
 #include "dmas_launch.cuh"
 
 namespace dmas {
@@ -52,6 +53,7 @@ struct dmas_plan {
     float *d_io_frame = nullptr, *d_io_image = nullptr;  // dmas_beamform_host staging
     size_t smem_beam = 0, smem_env = 0;
     EnvTaps taps{};
+    int num_sms = 148;
     cudaStream_t last_stream = nullptr;
     std::string last_error;
     // stage profiling
@@ -120,13 +122,15 @@ size_t beam_smem_bytes(const HostPlan &hp) {
     const size_t eb = chan_elem_bytes(hp.chan_prec);
     const size_t win = ((size_t)hp.mic_chunk * hp.window * eb + 127) & ~(size_t)127;
     const size_t tabs = (size_t)hp.mic_chunk * kGroup * 4 * (hp.delay_mode ? 2 : 1);
+    if (uses_pair_kernel(hp.chan_prec, hp.order))  // pair kernel: window and shifted window
+        return 128 + 2 * win + tabs;
     return 128 + win + tabs;
 }
 
 size_t env_smem_bytes(const HostPlan &hp) {
     if (hp.L == 0) return 0;
-    const int H = (hp.L - 1) / 2;
-    return sizeof(float) * ((size_t)kEnvTile + 2 * H + hp.L);
+    const int HA = env_halo_aligned((hp.L - 1) / 2);
+    return sizeof(float) * ((size_t)kEnvTile + 2 * HA + hp.L);
 }
 
 void mark(dmas_plan *p, int k, cudaStream_t s) {
@@ -148,6 +152,7 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
     rp.row = hp.row;
     rp.padl = hp.padl;
     rp.order = hp.order;
+    rp.shifted = uses_pair_kernel(hp.chan_prec, hp.order) ? 1 : 0;
     rp.inv_order = 1.0f / (float)hp.order;
     const size_t total = (size_t)hp.N * hp.row;
     const unsigned rgrid = (unsigned)std::min<size_t>((total + 255) / 256, 148 * 32);
@@ -179,6 +184,7 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
     bp.window = hp.window;
     bp.mic_chunk = hp.mic_chunk;
     bp.n_groups = hp.n_groups;
+    bp.n_tiles = hp.n_tiles;
     bp.n_mics_f = (float)hp.N;
     bp.cf_eps = (float)hp.cf_eps;
     bp.use_cf = (hp.flags & DMAS_F_CF) ? 1 : 0;
@@ -213,7 +219,7 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
     else if (H == 80)
         envelope_kernel<80><<<egrid, kEnvThreads, p->smem_env, s>>>(ep, p->taps);
     else
-        envelope_kernel<-1><<<egrid, kEnvThreads, p->smem_env, s>>>(ep, p->taps);
+        envelope_generic_kernel<<<egrid, kEnvThreads, p->smem_env, s>>>(ep, p->taps);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(p, e, "envelope_kernel launch");
     mark(p, 3, s);
     p->env_ran = true;
@@ -259,6 +265,11 @@ dmas_status dmas_plan_create(const dmas_plan_desc *desc, dmas_plan **out) {
     }
     HostPlan &hp = p->hp;
     cudaGetDevice(&p->device);
+    if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) !=
+            cudaSuccess ||
+        p->num_sms < 1)
+        p->num_sms = 148;
+    cudaGetLastError();
     p->smem_beam = beam_smem_bytes(hp);
     p->smem_env = env_smem_bytes(hp);
     for (int k = 0; k < hp.L; ++k) p->taps.h[k] = hp.taps[k];
@@ -273,7 +284,9 @@ dmas_status dmas_plan_create(const dmas_plan_desc *desc, dmas_plan **out) {
         return e == cudaErrorMemoryAllocation ? DMAS_ENOMEM : DMAS_ECUDA;
     }
     p->table_bytes = (hp.gdir.size() + hp.gws.size() + hp.rel.size()) * 4 + hp.gfrac.size() * 4;
-    p->chan_bytes = (size_t)hp.N * hp.row * chan_elem_bytes(hp.chan_prec);
+    // the pair kernel also reads every root row shifted by one sample
+    p->chan_bytes = (size_t)hp.N * hp.row * chan_elem_bytes(hp.chan_prec) *
+                    (uses_pair_kernel(hp.chan_prec, hp.order) ? 2 : 1);
     p->ybuf_bytes = hp.L > 0 ? sizeof(float) * (size_t)hp.M * hp.T : 0;
     if ((e = cudaMalloc((void **)&p->d_err, 256)) != cudaSuccess ||
         (e = cudaMemset(p->d_err, 0, 256)) != cudaSuccess ||

@@ -55,6 +55,14 @@ struct HostPlan {
 // with a reason in *why.
 dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *why);
 
+// The pipelined pair kernel runs FP32 channels up to this order; higher orders
+// (too many running sums for its registers) and FP16/BF16 channels run the
+// scalar beamform kernel.
+constexpr int kPairMaxOrder = 5;
+inline bool uses_pair_kernel(int chan_prec, int order) {
+    return chan_prec == DMAS_CH_F32 && order <= kPairMaxOrder;
+}
+
 // Bytes of one element of the root channel for a dmas_chan_prec.
 inline size_t chan_elem_bytes(int chan_prec) { return chan_prec == DMAS_CH_F32 ? 4 : 2; }
 

@@ -14,7 +14,8 @@
 //                     sum x^2 in FP32 registers, then applies Newton-Girard
 //                     (Eqs. dmas2_impl..dmas5_impl, or the recurrence for
 //                     n > 5) and the coherence factor (Eq. cf).
-//   envelope_kernel   |y| then a zero-phase FIR low-pass along t.
+//   (the envelope kernels, |y| then a zero-phase FIR low-pass along t, are in
+//   dmas_envelope.cuh)
 //
 // Every wait on an mbarrier is bounded by wall-clock time (globaltimer); on
 // expiry the kernel sets a bit in the plan's error word and returns.
@@ -29,6 +30,7 @@ namespace dmas {
 
 constexpr int kThreads = 256;      // 8 warps, one direction each
 constexpr int kPix = 8;            // output samples per lane (kTimeTile / 32)
+constexpr int kTimeTileDev = 32 * kPix;  // output samples per work item
 constexpr unsigned kErrTimeout = 1u;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
@@ -121,8 +123,9 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_ch<__nv_bfloat16>(float 
 // ---------------------------------------------------------------------------
 struct RootsParams {
     const float *frame;  // [N][T]
-    void *chan;          // [N][row] CH
+    void *chan;          // [N][row] CH, then (shifted != 0) [N][row] shifted by one sample
     int N, T, row, padl, order;
+    int shifted;         // also write chan1[i][c] = chan0[i][c + 1] after the first block
     float inv_order;
 };
 
@@ -147,6 +150,13 @@ __global__ void __launch_bounds__(256) roots_kernel(const __grid_constant__ Root
         float r = 0.0f;
         if (t >= 0 && t < p.T) r = signed_root(p.frame[(size_t)i * p.T + t], p.order, p.inv_order);
         chan[idx] = to_ch<CH>(r);
+        if (p.shifted) {
+            const int t1 = t + 1;
+            float r1 = 0.0f;
+            if (t1 >= 0 && t1 < p.T)
+                r1 = signed_root(p.frame[(size_t)i * p.T + t1], p.order, p.inv_order);
+            chan[total + idx] = to_ch<CH>(r1);
+        }
     }
 }
 
@@ -273,7 +283,7 @@ struct BeamParams {
     float *y;            // [M][T] E_n (x CF)
     float *cf;           // [M][T] or nullptr
     unsigned *err;       // error word
-    int N, T, row, padl, window, mic_chunk, n_groups;
+    int N, T, row, padl, window, mic_chunk, n_groups, n_tiles;
     float n_mics_f, cf_eps;
     int use_cf;
 };
@@ -411,75 +421,186 @@ __global__ void __launch_bounds__(kThreads, 2)
 }
 
 // ---------------------------------------------------------------------------
-// K3: envelope, |y| filtered along t with a zero-phase FIR
+// K2 (FP32 channels up to 5th order): the same gather + power sums on PAIRS of
+// neighbouring output samples (t, t+1) with packed f32x2 arithmetic: one
+// FFMA2/FMUL2/FADD2 does two FP32 operations in one issue slot, and one 8-byte
+// shared load fetches the pair of delayed roots straight into the 64-bit
+// register the packed instructions read.  A pair load must be 8-byte aligned
+// but t + shift may be odd, so the roots kernel also writes every channel row
+// shifted by one sample (chan1[x] = chan0[x + 1]); both windows are staged by
+// bulk copy, and each pair is read from the copy in which it starts at an even
+// index.
+//   lane l, pair k (0..3): samples t = t0 + 2l + 64k and t + 1.
 // ---------------------------------------------------------------------------
-constexpr int kEnvThreads = 128;
-constexpr int kEnvR = 8;                              // outputs per lane
-constexpr int kEnvTile = kEnvThreads * kEnvR;         // outputs per CTA
+typedef unsigned long long f32x2_t;
 
-struct EnvParams {
-    const float *y;   // [M][T]
-    float *img;       // [M][T]
-    int T, n_tiles, L;
-};
-struct EnvTaps {
-    float h[1023];
-};
+__device__ __forceinline__ f32x2_t f2_fma(f32x2_t a, f32x2_t b, f32x2_t c) {
+    f32x2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2_t f2_mul(f32x2_t a, f32x2_t b) {
+    f32x2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2_t f2_add(f32x2_t a, f32x2_t b) {
+    f32x2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2_t f2_pack(float lo, float hi) {
+    f32x2_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ void f2_unpack(f32x2_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+// magnitude of `mag` with the sign of `sgn`, in both halves
+__device__ __forceinline__ f32x2_t f2_copysign(f32x2_t mag, f32x2_t sgn) {
+    return (mag & 0x7fffffff7fffffffull) | (sgn & 0x8000000080000000ull);
+}
 
-// HH >= 0: taps length 2*HH+1 fixed at compile time (taps read straight from
-// the parameter bank); HH < 0: any length, taps from shared memory.
-template <int HH>
-__global__ void __launch_bounds__(kEnvThreads)
-    envelope_kernel(const __grid_constant__ EnvParams p, const __grid_constant__ EnvTaps taps) {
-    extern __shared__ __align__(16) float s_abs[];
-    const int H = (HH >= 0) ? HH : (p.L - 1) / 2;
-    const int rowi = (int)(blockIdx.x / (unsigned)p.n_tiles);
-    const int tile = (int)(blockIdx.x - (unsigned)rowi * (unsigned)p.n_tiles);
-    const int t0 = tile * kEnvTile;
-    const float *y = p.y + (size_t)rowi * p.T;
-    const int span = kEnvTile + 2 * H;
-    for (int idx = threadIdx.x; idx < span; idx += kEnvThreads) {
-        const int t = t0 - H + idx;
-        s_abs[idx] = (t >= 0 && t < p.T) ? fabsf(y[t]) : 0.0f;
+template <int ORDER, bool WEIGHTED>
+__device__ __forceinline__ void accumulate2(f32x2_t (&a)[SumLayout<ORDER>::kNum], f32x2_t s,
+                                            f32x2_t w) {
+    constexpr int NP = SumLayout<ORDER>::kNumP;
+    f32x2_t pw = s;
+    if constexpr (NP >= 1) a[0] = WEIGHTED ? f2_fma(w, s, a[0]) : f2_add(a[0], s);
+#pragma unroll
+    for (int q = 2; q <= ORDER; ++q) {
+        pw = f2_mul(pw, s);
+        if (q <= NP) a[q - 1] = WEIGHTED ? f2_fma(w, pw, a[q - 1]) : f2_add(a[q - 1], pw);
     }
-    float *s_h = s_abs + span;
-    if constexpr (HH < 0) {
-        for (int k = threadIdx.x; k < p.L; k += kEnvThreads) s_h[k] = taps.h[k];
+    const f32x2_t x = (ORDER & 1) ? pw : f2_copysign(pw, s);
+    a[NP] = WEIGHTED ? f2_fma(w, x, a[NP]) : f2_add(a[NP], x);
+    const f32x2_t wx = WEIGHTED ? f2_mul(w, x) : x;
+    a[NP + 1] = f2_fma(wx, x, a[NP + 1]);
+}
+
+constexpr int kPairs = 4;  // pixel pairs per lane (kTimeTile / 64)
+
+template <int ORDER, bool LINEAR, int NGP>
+__global__ void __launch_bounds__(kThreads, 2)
+    beamform_x2_kernel(const __grid_constant__ BeamParams p) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int NA = SumLayout<ORDER>::kNum;
+    constexpr int NP = SumLayout<ORDER>::kNumP;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    const int WS = p.window;
+    const int NC = p.mic_chunk;
+    const int win_bytes = (NC * WS * 4 + 127) & ~127;
+    float *copy0 = reinterpret_cast<float *>(smem + 128);
+    float *copy1 = reinterpret_cast<float *>(smem + 128 + win_bytes);
+    int *s_rel = reinterpret_cast<int *>(smem + 128 + 2 * win_bytes);
+    float *s_frac = reinterpret_cast<float *>(s_rel + NC * 8);
+
+    const int tile = (int)(blockIdx.x / (unsigned)p.n_groups);
+    const int g = (int)(blockIdx.x - (unsigned)tile * (unsigned)p.n_groups);
+    const int t0 = tile * kTimeTileDev;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
     }
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int base = warp * 32 * kEnvR;  // first output of this warp, relative to t0
-    float acc[kEnvR];
+
+    f32x2_t acc[kPairs][NA];
 #pragma unroll
-    for (int j = 0; j < kEnvR; ++j) acc[j] = 0.0f;
-    // output j of this lane: t0 + base + lane + 32 j; input offset m relative to
-    // t0 + base + lane; tap index k = 32 j - m (e[t] = sum_k h[k] |y[t - k]|).
-    const float *src = s_abs + base + lane + H;
-    if constexpr (HH >= 0) {
+    for (int k = 0; k < kPairs; ++k)
 #pragma unroll
-        for (int m = -HH; m <= 32 * (kEnvR - 1) + HH; ++m) {
-            const float a = src[m];
-#pragma unroll
-            for (int j = 0; j < kEnvR; ++j) {
-                const int k = 32 * j - m;
-                if (k >= -HH && k <= HH) acc[j] = fmaf(taps.h[k + HH], a, acc[j]);
+        for (int q = 0; q < NA; ++q) acc[k][q] = 0ull;
+
+    const float *chan0 = reinterpret_cast<const float *>(p.chan);
+    const float *chan1 = chan0 + (size_t)p.N * p.row;
+    uint32_t parity = 0;
+    for (int c0 = 0; c0 < p.N; c0 += NC) {
+        const int nc = min(NC, p.N - c0);
+        if (c0 > 0) __syncthreads();  // every warp is done with the previous chunk
+        if (warp == 0) {
+            const uint32_t row_bytes = (uint32_t)(WS * 4);
+            const uint32_t tab_bytes = (uint32_t)(nc * 8 * 4);
+            if (lane == 0)
+                mbar_arrive_expect_tx(bar, 2 * nc * row_bytes + tab_bytes * (LINEAR ? 2u : 1u));
+            __syncwarp();
+            const int *gws = p.gws + (size_t)g * p.N;
+            for (int il = lane; il < nc; il += 32) {
+                const int i = c0 + il;
+                const size_t o = (size_t)i * p.row + p.padl + t0 + gws[i];
+                bulk_g2s(copy0 + il * WS, chan0 + o, row_bytes, bar);
+                bulk_g2s(copy1 + il * WS, chan1 + o, row_bytes, bar);
+            }
+            if (lane == 0) {
+                bulk_g2s(s_rel, p.rel + ((size_t)g * p.N + c0) * 8, tab_bytes, bar);
+                if (LINEAR) bulk_g2s(s_frac, p.frac + ((size_t)g * p.N + c0) * 8, tab_bytes, bar);
             }
         }
-    } else {
-        for (int m = -H; m <= 32 * (kEnvR - 1) + H; ++m) {
-            const float a = src[m];
+        const bool ok = mbar_wait_bounded(bar, parity);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(p.err, kErrTimeout);
+                mbar_wait_bounded(bar, parity);  // let copies in flight land
+            }
+            return;
+        }
+        parity ^= 1u;
+
+#pragma unroll 2
+        for (int il = 0; il < nc; ++il) {
+            const int off = s_rel[il * 8 + warp];
+            const float *r0 = copy0 + il * WS;
+            const float *r1 = copy1 + il * WS;
+            const bool odd = (off & 1) != 0;
+            // (x, x+1), x = off + 2l + 64k: at x in copy 0 (even off) or at
+            // x - 1 in copy 1 (odd off)
+            const float *lp = (odd ? r1 + off - 1 : r0 + off) + 2 * lane;
+            if constexpr (LINEAR) {
+                // (x+1, x+2): at x in copy 1 (even off) or at x + 1 in copy 0 (odd off)
+                const float *rp = (odd ? r0 + off + 1 : r1 + off) + 2 * lane;
+                const float f = s_frac[il * 8 + warp];
+                const f32x2_t w0 = f2_pack(1.0f - f, 1.0f - f);
+                const f32x2_t w1 = f2_pack(f, f);
 #pragma unroll
-            for (int j = 0; j < kEnvR; ++j) {
-                const int k = 32 * j - m;
-                if (k >= -H && k <= H) acc[j] = fmaf(s_h[k + H], a, acc[j]);
+                for (int k = 0; k < kPairs; ++k) {
+                    const f32x2_t a = *reinterpret_cast<const f32x2_t *>(lp + 64 * k);
+                    const f32x2_t b = *reinterpret_cast<const f32x2_t *>(rp + 64 * k);
+                    accumulate2<ORDER, true>(acc[k], a, w0);
+                    accumulate2<ORDER, true>(acc[k], b, w1);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kPairs; ++k) {
+                    const f32x2_t a = *reinterpret_cast<const f32x2_t *>(lp + 64 * k);
+                    accumulate2<ORDER, false>(acc[k], a, 0ull);
+                }
             }
         }
     }
-    float *img = p.img + (size_t)rowi * p.T;
+
+    const int dir = p.gdir[(size_t)g * 8 + warp];
+    if (dir < 0) return;
+    float *yrow = p.y + (size_t)dir * p.T;
+    float *cfrow = p.cf ? p.cf + (size_t)dir * p.T : nullptr;
 #pragma unroll
-    for (int j = 0; j < kEnvR; ++j) {
-        const int t = t0 + base + lane + 32 * j;
-        if (t < p.T) img[t] = acc[j];
+    for (int k = 0; k < kPairs; ++k) {
+        float P[2][ORDER + 1], A[2], B[2];
+        P[0][0] = P[1][0] = 0.0f;
+#pragma unroll
+        for (int q = 1; q <= NP; ++q) f2_unpack(acc[k][q - 1], P[0][q], P[1][q]);
+        f2_unpack(acc[k][NP], A[0], A[1]);
+        f2_unpack(acc[k][NP + 1], B[0], B[1]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = t0 + 2 * lane + 64 * k + h;
+            if (t >= p.T) continue;
+            if constexpr (SumLayout<ORDER>::kPnIsA) P[h][ORDER] = A[h];
+            const float E = esym_from_power_sums<ORDER, NGP>(P[h]);
+            const float cf = (A[h] * A[h]) / fmaf(p.n_mics_f, B[h], p.cf_eps);
+            yrow[t] = p.use_cf ? E * cf : E;
+            if (cfrow) cfrow[t] = cf;
+        }
     }
 }
 

@@ -5,7 +5,9 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
+#include "dmas_internal.h"
 #include "dmas_kernels.cuh"
 
 namespace dmas {
@@ -17,7 +19,11 @@ constexpr int kBeamSmemOptIn = 227 * 1024;
 template <int ORDER, bool LINEAR, typename CH, int NGP>
 cudaError_t launch_beam_variant(const BeamParams &p, unsigned grid, size_t smem,
                                 cudaStream_t s) {
-    auto kern = beamform_kernel<ORDER, LINEAR, CH, NGP>;
+    // FP32 channels up to kPairMaxOrder: the pipelined pair kernel; otherwise
+    // the scalar one (same choice as uses_pair_kernel on the host)
+    auto kern = (std::is_same<CH, float>::value && ORDER <= kPairMaxOrder)
+                    ? beamform_x2_kernel<ORDER, LINEAR, NGP>
+                    : beamform_kernel<ORDER, LINEAR, CH, NGP>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {

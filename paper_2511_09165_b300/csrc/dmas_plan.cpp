@@ -276,11 +276,14 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
     }
     const size_t eb = chan_elem_bytes(d.chan_prec);
     long long window = round_up(kTimeTile + spread, kAlign);
-    const size_t per_mic = (size_t)window * eb + (size_t)kGroup * 4 * (lin ? 2 : 1);
-    if (per_mic > kWindowSmemBudget)
+    // The pair kernel stages each window twice (as is and shifted by one sample).
+    const size_t copies = uses_pair_kernel(d.chan_prec, d.order) ? 2 : 1;
+    const size_t budget = kWindowSmemBudget;
+    const size_t per_mic = copies * (size_t)window * eb + (size_t)kGroup * 4 * (lin ? 2 : 1);
+    if (per_mic > budget)
         return fail("a direction group's delay spread does not fit in shared memory");
     hp.window = (int)window;
-    hp.mic_chunk = (int)std::min<size_t>((size_t)N, kWindowSmemBudget / per_mic);
+    hp.mic_chunk = (int)std::min<size_t>((size_t)N, budget / per_mic);
     hp.n_tiles = (T + kTimeTile - 1) / kTimeTile;
     hp.padl = (int)round_up(std::max(0, -ws_min), kAlign);
     long long read_end = (long long)hp.padl + (long long)(hp.n_tiles - 1) * kTimeTile +
