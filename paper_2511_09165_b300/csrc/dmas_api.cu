@@ -188,6 +188,7 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
     bp.n_mics_f = (float)hp.N;
     bp.cf_eps = (float)hp.cf_eps;
     bp.use_cf = (hp.flags & DMAS_F_CF) ? 1 : 0;
+    bp.pairs = hp.pairs;
     const unsigned bgrid = (unsigned)((size_t)hp.n_groups * hp.n_tiles);
     e = kBeamLaunchers[hp.order](bp, hp.delay_mode, hp.chan_prec, hp.ng_prec, bgrid,
                                  p->smem_beam, s);
@@ -399,7 +400,7 @@ dmas_status dmas_plan_get_info(const dmas_plan *p, dmas_plan_info *info) {
     info->group_size = kGroup;
     info->window = hp.window;
     info->mic_chunk = hp.mic_chunk;
-    info->time_tile = kTimeTile;
+    info->time_tile = hp.tile;
     info->workspace_bytes = dmas_plan_workspace_bytes(p);
     info->table_bytes = p->table_bytes;
     return DMAS_OK;

@@ -13,7 +13,8 @@ namespace dmas {
 
 // Directions per CTA row ("group"): one warp of the beamform kernel per direction.
 constexpr int kGroup = 8;
-// Output samples per CTA along t (8 per lane, lanes strided by one sample).
+// Output samples per CTA along t for the scalar beamform kernel (8 per lane,
+// lanes strided by one sample); the pair kernel uses 64 * pairs.
 constexpr int kTimeTile = 256;
 // Sample alignment of every staged window start and length (8 elements = 32 B
 // of FP32, 16 B of FP16/BF16: every bulk copy starts and ends 16-byte aligned).
@@ -44,7 +45,9 @@ struct HostPlan {
 
     int window = 0;      // staged samples per microphone row (multiple of kAlign)
     int mic_chunk = 0;   // microphones staged per pass
-    int n_tiles = 0;     // time tiles of kTimeTile
+    int tile = 0;        // output samples per CTA along t
+    int pairs = 0;       // pair kernel: pixel pairs per lane (tile = 64 * pairs); 0 = scalar kernel
+    int n_tiles = 0;     // time tiles of `tile` samples
     int padl = 0;        // zero samples before t = 0 in the root channel rows
     int row = 0;         // root channel row length (multiple of kAlign)
 

@@ -286,6 +286,7 @@ struct BeamParams {
     int N, T, row, padl, window, mic_chunk, n_groups, n_tiles;
     float n_mics_f, cf_eps;
     int use_cf;
+    int pairs;           // pair kernel: pixel pairs per lane (time tile 64 * pairs)
 };
 
 // Running sums per pixel: P_1..P_n, sum x, sum x^2, where for odd n
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 // shifted by one sample (chan1[x] = chan0[x + 1]); both windows are staged by
 // bulk copy, and each pair is read from the copy in which it starts at an even
 // index.
-//   lane l, pair k (0..3): samples t = t0 + 2l + 64k and t + 1.
+//   lane l, pair k (0..PAIRS-1): samples t = t0 + 2l + 64k and t + 1.
 // ---------------------------------------------------------------------------
 typedef unsigned long long f32x2_t;
 
@@ -479,11 +480,12 @@ __device__ __forceinline__ void accumulate2(f32x2_t (&a)[SumLayout<ORDER>::kNum]
     a[NP + 1] = f2_fma(wx, x, a[NP + 1]);
 }
 
-constexpr int kPairs = 4;  // pixel pairs per lane (kTimeTile / 64)
-
-template <int ORDER, bool LINEAR, int NGP>
-__global__ void __launch_bounds__(kThreads, 2)
+// PAIRS pixel pairs per lane: time tile 64 * PAIRS.  PAIRS = 2 keeps few
+// enough registers and shared memory for four CTAs per SM, PAIRS = 4 two.
+template <int ORDER, bool LINEAR, int NGP, int PAIRS>
+__global__ void __launch_bounds__(kThreads, PAIRS == 2 ? 4 : 2)
     beamform_x2_kernel(const __grid_constant__ BeamParams p) {
+    constexpr int kPairs = PAIRS;
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int NA = SumLayout<ORDER>::kNum;
     constexpr int NP = SumLayout<ORDER>::kNumP;
@@ -498,7 +500,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 
     const int tile = (int)(blockIdx.x / (unsigned)p.n_groups);
     const int g = (int)(blockIdx.x - (unsigned)tile * (unsigned)p.n_groups);
-    const int t0 = tile * kTimeTileDev;
+    const int t0 = tile * (64 * kPairs);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {

@@ -16,16 +16,9 @@ namespace dmas {
 // family's per-CTA opt-in maximum, 227 KB).
 constexpr int kBeamSmemOptIn = 227 * 1024;
 
-template <int ORDER, bool LINEAR, typename CH, int NGP>
-cudaError_t launch_beam_variant(const BeamParams &p, unsigned grid, size_t smem,
-                                cudaStream_t s) {
-    // FP32 channels up to kPairMaxOrder: the pipelined pair kernel; otherwise
-    // the scalar one (same choice as uses_pair_kernel on the host)
-    auto kern = (std::is_same<CH, float>::value && ORDER <= kPairMaxOrder)
-                    ? beamform_x2_kernel<ORDER, LINEAR, NGP>
-                    : beamform_kernel<ORDER, LINEAR, CH, NGP>;
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
+template <typename K>
+cudaError_t launch_kernel(K kern, std::once_flag &once, cudaError_t &attr_err,
+                          const BeamParams &p, unsigned grid, size_t smem, cudaStream_t s) {
     std::call_once(once, [&] {
         attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kBeamSmemOptIn);
@@ -33,6 +26,30 @@ cudaError_t launch_beam_variant(const BeamParams &p, unsigned grid, size_t smem,
     if (attr_err != cudaSuccess) return attr_err;
     kern<<<grid, kThreads, smem, s>>>(p);
     return cudaGetLastError();
+}
+
+// FP32 channels up to kPairMaxOrder: the pair kernel (p.pairs pairs per lane);
+// otherwise the scalar one (the same choice as uses_pair_kernel on the host).
+template <int ORDER, bool LINEAR, typename CH, int NGP>
+cudaError_t launch_beam_variant(const BeamParams &p, unsigned grid, size_t smem,
+                                cudaStream_t s) {
+    if constexpr (std::is_same<CH, float>::value && ORDER <= kPairMaxOrder) {
+        if (p.pairs == 4) {
+            static std::once_flag once;
+            static cudaError_t err = cudaSuccess;
+            return launch_kernel(beamform_x2_kernel<ORDER, LINEAR, NGP, 4>, once, err, p, grid,
+                                 smem, s);
+        }
+        static std::once_flag once;
+        static cudaError_t err = cudaSuccess;
+        return launch_kernel(beamform_x2_kernel<ORDER, LINEAR, NGP, 2>, once, err, p, grid, smem,
+                             s);
+    } else {
+        static std::once_flag once;
+        static cudaError_t err = cudaSuccess;
+        return launch_kernel(beamform_kernel<ORDER, LINEAR, CH, NGP>, once, err, p, grid, smem,
+                             s);
+    }
 }
 
 template <int ORDER, bool LINEAR, typename CH>

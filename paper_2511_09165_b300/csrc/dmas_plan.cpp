@@ -275,7 +275,18 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
         }
     }
     const size_t eb = chan_elem_bytes(d.chan_prec);
-    long long window = round_up(kTimeTile + spread, kAlign);
+    if (uses_pair_kernel(d.chan_prec, d.order)) {
+        // Measured on B300 (hemisphere scene, n = 5): nearest-sample delays run
+        // best with 2 pairs per lane (128-sample tiles, four CTAs per SM hide
+        // the staging), interpolated delays, with twice the arithmetic per
+        // staged sample, with 4 pairs (256-sample tiles, less halo).
+        hp.pairs = lin ? 4 : 2;
+        hp.tile = 64 * hp.pairs;
+    } else {
+        hp.pairs = 0;
+        hp.tile = kTimeTile;
+    }
+    long long window = round_up(hp.tile + spread, kAlign);
     // The pair kernel stages each window twice (as is and shifted by one sample).
     const size_t copies = uses_pair_kernel(d.chan_prec, d.order) ? 2 : 1;
     const size_t budget = kWindowSmemBudget;
@@ -284,9 +295,9 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
         return fail("a direction group's delay spread does not fit in shared memory");
     hp.window = (int)window;
     hp.mic_chunk = (int)std::min<size_t>((size_t)N, budget / per_mic);
-    hp.n_tiles = (T + kTimeTile - 1) / kTimeTile;
+    hp.n_tiles = (T + hp.tile - 1) / hp.tile;
     hp.padl = (int)round_up(std::max(0, -ws_min), kAlign);
-    long long read_end = (long long)hp.padl + (long long)(hp.n_tiles - 1) * kTimeTile +
+    long long read_end = (long long)hp.padl + (long long)(hp.n_tiles - 1) * hp.tile +
                          ws_max + window;
     hp.row = (int)round_up(std::max<long long>(read_end, (long long)hp.padl + T), kAlign);
 
