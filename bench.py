@@ -52,6 +52,9 @@ WORKLOADS = {
         text="3-D hemisphere: 32 mics in a 12 cm disc, 2048 Fibonacci directions, "
              "16384 samples at 450 kHz, 8 reflectors, 10 dB SNR, n=5, linear delays, "
              "CF, 181-tap envelope"),
+    "hemi_3d_n5_round": dict(
+        scene=lambda: scenes.hemi_3d(seed=2), order=5, mode="round",
+        text="3-D hemisphere as hemi_3d_n5 with nearest-sample delays"),
     "small_2d_n5": dict(
         scene=lambda: scenes.small_2d(seed=1), order=5, mode="round",
         text="2-D fan: 32 mics in a 12 cm disc, 91 azimuths, 4096 samples at 450 kHz, "
@@ -59,6 +62,11 @@ WORKLOADS = {
     "passive64_n5": dict(
         scene=lambda: scenes.passive(seed=4, n_mics=64), order=5, mode="round",
         text="passive: 64 mics in a 0.4 m square, 8192 az/el directions, 32768 samples "
+             "at 400 kHz, 4 broadband sources, 0 dB SNR, n=5, nearest-sample delays, "
+             "CF, 161-tap envelope"),
+    "passive256_n5": dict(
+        scene=lambda: scenes.passive(seed=4, n_mics=256), order=5, mode="round",
+        text="passive: 256 mics in a 0.4 m square, 8192 az/el directions, 32768 samples "
              "at 400 kHz, 4 broadband sources, 0 dB SNR, n=5, nearest-sample delays, "
              "CF, 161-tap envelope"),
 }
@@ -344,17 +352,126 @@ def run_ours(args, wl, scene) -> None:
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# serving: Poisson arrivals from 16 mixed sensors
+# ---------------------------------------------------------------------------
+def run_serving(args) -> None:
+    import torch
+    import paper_2511_09165_b300 as dm
+    from paper_2511_09165_b300 import serving
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    mix = scenes.serving_mix(seed=5 + rank)
+    sensors = [serving.Sensor(dm.Plan(mic_xyz=s.mic_xyz, dir_azel=s.dir_azel,
+                                      dir_unit=s.dir_unit, n_samples=s.n_samples, fs=s.fs,
+                                      c=s.c, order=s.order), s.name) for s in mix]
+    host = [[torch.from_numpy(f).pin_memory() for f in s.frames] for s in mix]
+    px = [s.n_dirs * s.n_samples for s in mix]
+    for sn, h in zip(sensors, host):          # warm-up: every sensor once
+        sn.plan(h[0].cuda())
+    torch.cuda.synchronize()
+
+    def schedule(rate, seed):
+        offs, which = serving.poisson_arrivals(rate, args.serve_seconds, len(mix), seed)
+        rng = np.random.default_rng(seed + 1)
+        frames = [int(rng.integers(len(host[w]))) for w in which]
+        return offs, which, frames
+
+    def run_server(rate, seed):
+        offs, which, fidx = schedule(rate, seed)
+        reqs = []
+        with serving.Server(sensors, budget_bytes=args.serve_budget_gb << 30, streams=2) as srv:
+            t0 = time.perf_counter() + 0.05
+            for o, w, f in zip(offs, which, fidx):
+                while time.perf_counter() < t0 + o:
+                    time.sleep(0.0002)
+                reqs.append(srv.submit(int(w), host[w][f], t_arrival=t0 + o))
+            srv.drain(600.0)
+            nb = srv.batches
+        return reqs, t0, nb
+
+    def run_baseline(rate, seed):
+        offs, which, fidx = schedule(rate, seed)
+        t0 = time.perf_counter() + 0.05
+        reqs = [serving.Request(int(w), host[w][f], t0 + o)
+                for o, w, f in zip(offs, which, fidx)]
+        serving.one_frame_per_launch(sensors, reqs)
+        return reqs, t0
+
+    def summary(reqs, t0, batches=None):
+        done = [r for r in reqs if not r.rejected]
+        span = max(r.t_done for r in done) - t0
+        d = serving.latency_summary(reqs)
+        d["frames_per_s"] = len(done) / span
+        d["dir_samples_per_s"] = sum(px[r.sensor] for r in done) / span
+        d["rejected"] = sum(r.rejected for r in reqs)
+        if batches is not None:
+            d["batches"] = batches
+            d["mean_batch"] = len(done) / max(batches, 1)
+        return d
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    wall0 = time.time()
+    results = {}
+    for k, rate in enumerate(args.serve_rates):
+        reqs, t0, nb = run_server(rate, 100 + k)
+        sv = summary(reqs, t0, nb)
+        reqs, t0 = run_baseline(rate, 100 + k)
+        bl = summary(reqs, t0)
+        results[f"{rate:g}_fps"] = {"server": sv, "one_frame_per_launch": bl}
+    wall1 = time.time()
+    clocks.stop()
+    for sn in sensors:
+        sn.plan.close()
+    if rank != 0:
+        return
+    top = results[f"{args.serve_rates[-1]:g}_fps"]["server"]
+    line = {
+        "metric": METRIC, "value": top["dir_samples_per_s"] * world, "unit": UNIT,
+        "n_gpus": world, "steps": sum(v["server"]["frames"] for v in results.values()),
+        "warmup": len(mix), "ms_per_step": 1e3 / top["frames_per_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "serving", "description":
+                   "16 sensors (N in {32,64,128}, M in {91,2048,8192}, T in "
+                   "{4096,16384,32768}, n in {3,5}, nearest-sample delays, CF, envelope), "
+                   "small_2d-style echo frames, Poisson arrivals at " +
+                   ", ".join(f"{r:g}" for r in args.serve_rates) + " frames/s for "
+                   f"{args.serve_seconds:g} s each; latency = arrival to image resident "
+                   "on the device; value = delivered direction*samples/s at the highest rate",
+                   "budget_gb": args.serve_budget_gb, "streams": 2,
+                   "sensors": [f"N{s.n_mics} M{s.n_dirs} T{s.n_samples} n{s.order}"
+                               for s in mix]},
+        "latency_ms": {"p50": top.get("p50_ms"), "p99": top.get("p99_ms")},
+        "serving": results,
+        "clocks": clocks.summary(wall0, wall1),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="hemi_3d_n5")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving"], default="hemi_3d_n5")
+    ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 1000.0])
+    ap.add_argument("--serve-seconds", type=float, default=5.0)
+    ap.add_argument("--serve-budget-gb", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "serving":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the serving workload has no CPU reference arm"}))
+            return
+        run_serving(args)
+        return
     wl = WORKLOADS[args.workload]
     scene = wl["scene"]()
     if args.impl == "reference":

@@ -164,16 +164,19 @@ dmas_status dmas_beamform_host(dmas_plan *plan, const float *h_frame, float *h_i
                                void *stream);
 
 /*
- * Serving: beamform `count` frames, each with its own plan.  plans/d_frames/
- * d_images are HOST arrays of `count` entries; each frame and image is a
- * device buffer shaped as for dmas_beamform.  The same plan may appear more
- * than once (each entry gets its own scratch from the workspace).
- * d_workspace is device memory of at least dmas_batch_workspace_bytes(count,
- * plans) bytes, 256-byte aligned, owned by the caller and not used by anything
- * else while the batch runs.  Each entry's image is bitwise identical to
- * dmas_beamform of that entry alone.
+ * Serving: beamform `count` frames, each with its own plan, batched.  Entries
+ * that run the same kernel variant (order, delay mode, channel and
+ * Newton-Girard precision, tile; for the envelope, the same taps) share one
+ * launch per stage, up to 64 entries per launch, so a mixed batch costs a few
+ * launches instead of three per frame.  plans/d_frames/d_images are HOST
+ * arrays of `count` entries; each frame and image is a device buffer shaped as
+ * for dmas_beamform.  The same plan may appear more than once (each entry gets
+ * its own scratch from the workspace).  d_workspace is device memory of at
+ * least dmas_batch_workspace_bytes(count, plans) bytes, 256-byte aligned, owned
+ * by the caller and not used by anything else while the batch runs.  Each
+ * entry's image is bitwise identical to dmas_beamform of that entry alone.
  * Errors: DMAS_EINVAL (count < 1, a NULL entry, small or misaligned
- * workspace), DMAS_ECUDA.
+ * workspace), DMAS_ENOMEM, DMAS_ECUDA.
  */
 dmas_status dmas_beamform_batch(int count, dmas_plan *const *plans,
                                 const float *const *d_frames, float *const *d_images,

@@ -7,6 +7,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "dmas.h"
 #include "dmas_internal.h"
@@ -30,6 +31,30 @@ extern template cudaError_t launch_beamform_order<7>(const BeamParams &, int, in
                                                      size_t, cudaStream_t);
 extern template cudaError_t launch_beamform_order<8>(const BeamParams &, int, int, int, unsigned,
                                                      size_t, cudaStream_t);
+
+extern template cudaError_t launch_beamform_batch_order<1>(const BeamBatch &, int, int, int,
+                                                           int, unsigned, size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_batch_order<2>(const BeamBatch &, int, int, int,
+                                                           int, unsigned, size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_batch_order<3>(const BeamBatch &, int, int, int,
+                                                           int, unsigned, size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_batch_order<4>(const BeamBatch &, int, int, int,
+                                                           int, unsigned, size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_batch_order<5>(const BeamBatch &, int, int, int,
+                                                           int, unsigned, size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_batch_order<6>(const BeamBatch &, int, int, int,
+                                                           int, unsigned, size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_batch_order<7>(const BeamBatch &, int, int, int,
+                                                           int, unsigned, size_t, cudaStream_t);
+extern template cudaError_t launch_beamform_batch_order<8>(const BeamBatch &, int, int, int,
+                                                           int, unsigned, size_t, cudaStream_t);
+
+static const BeamBatchLauncher kBeamBatchLaunchers[9] = {
+    nullptr,
+    &launch_beamform_batch_order<1>, &launch_beamform_batch_order<2>,
+    &launch_beamform_batch_order<3>, &launch_beamform_batch_order<4>,
+    &launch_beamform_batch_order<5>, &launch_beamform_batch_order<6>,
+    &launch_beamform_batch_order<7>, &launch_beamform_batch_order<8>};
 
 static const BeamLauncher kBeamLaunchers[9] = {
     nullptr,
@@ -137,13 +162,9 @@ void mark(dmas_plan *p, int k, cudaStream_t s) {
     if (p->profiling) cudaEventRecord(p->ev[k], s);
 }
 
-// Enqueue the whole path for one frame with the given scratch.
-dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, float *d_y,
-                          float *d_cf, void *scratch, cudaStream_t s) {
+// ---- per-stage launch parameters of one frame ----------------------------
+RootsParams roots_params(const dmas_plan *p, const float *d_frame, void *scratch) {
     const HostPlan &hp = p->hp;
-    cudaError_t e;
-    mark(p, 0, s);
-    // K1: roots
     RootsParams rp;
     rp.frame = d_frame;
     rp.chan = scratch;
@@ -154,20 +175,23 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
     rp.order = hp.order;
     rp.shifted = uses_pair_kernel(hp.chan_prec, hp.order) ? 1 : 0;
     rp.inv_order = 1.0f / (float)hp.order;
-    const size_t total = (size_t)hp.N * hp.row;
-    const unsigned rgrid = (unsigned)std::min<size_t>((total + 255) / 256, 148 * 32);
-    switch (hp.chan_prec) {
-        case DMAS_CH_F16: roots_kernel<__half><<<rgrid, 256, 0, s>>>(rp); break;
-        case DMAS_CH_BF16: roots_kernel<__nv_bfloat16><<<rgrid, 256, 0, s>>>(rp); break;
-        default: roots_kernel<float><<<rgrid, 256, 0, s>>>(rp); break;
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(p, e, "roots_kernel launch");
-    mark(p, 1, s);
+    return rp;
+}
 
-    // K2: beamform into y (the image itself without the envelope)
-    const bool env = hp.L > 0;
-    float *ybuf = d_image;
-    if (env) ybuf = d_y ? d_y : (float *)((char *)scratch + align256(p->chan_bytes));
+unsigned roots_blocks(const dmas_plan *p) {
+    const size_t total = (size_t)p->hp.N * p->hp.row;
+    return (unsigned)std::min<size_t>((total + 255) / 256, 148 * 32);
+}
+
+// Where y (E_n x CF before the envelope) goes: the image itself without the
+// envelope, else d_y or the scratch after the root channels.
+float *y_target(const dmas_plan *p, float *d_image, float *d_y, void *scratch) {
+    if (p->hp.L == 0) return d_image;
+    return d_y ? d_y : (float *)((char *)scratch + align256(p->chan_bytes));
+}
+
+BeamParams beam_params(const dmas_plan *p, void *scratch, float *ybuf, float *d_cf) {
+    const HostPlan &hp = p->hp;
     BeamParams bp;
     bp.chan = scratch;
     bp.gdir = p->d_gdir;
@@ -189,8 +213,49 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
     bp.cf_eps = (float)hp.cf_eps;
     bp.use_cf = (hp.flags & DMAS_F_CF) ? 1 : 0;
     bp.pairs = hp.pairs;
-    const unsigned bgrid = (unsigned)((size_t)hp.n_groups * hp.n_tiles);
-    e = kBeamLaunchers[hp.order](bp, hp.delay_mode, hp.chan_prec, hp.ng_prec, bgrid,
+    return bp;
+}
+
+unsigned beam_blocks(const dmas_plan *p) {
+    return (unsigned)((size_t)p->hp.n_groups * p->hp.n_tiles);
+}
+
+EnvParams env_params(const dmas_plan *p, const float *ybuf, float *d_image) {
+    EnvParams ep;
+    ep.y = ybuf;
+    ep.img = d_image;
+    ep.T = p->hp.T;
+    ep.n_tiles = (p->hp.T + kEnvTile - 1) / kEnvTile;
+    ep.L = p->hp.L;
+    return ep;
+}
+
+unsigned env_blocks(const dmas_plan *p) {
+    return (unsigned)((size_t)p->hp.M * ((p->hp.T + kEnvTile - 1) / kEnvTile));
+}
+
+// Enqueue the whole path for one frame with the given scratch.
+dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, float *d_y,
+                          float *d_cf, void *scratch, cudaStream_t s) {
+    const HostPlan &hp = p->hp;
+    cudaError_t e;
+    mark(p, 0, s);
+    // K1: roots
+    const RootsParams rp = roots_params(p, d_frame, scratch);
+    const unsigned rgrid = roots_blocks(p);
+    switch (hp.chan_prec) {
+        case DMAS_CH_F16: roots_kernel<__half><<<rgrid, 256, 0, s>>>(rp); break;
+        case DMAS_CH_BF16: roots_kernel<__nv_bfloat16><<<rgrid, 256, 0, s>>>(rp); break;
+        default: roots_kernel<float><<<rgrid, 256, 0, s>>>(rp); break;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(p, e, "roots_kernel launch");
+    mark(p, 1, s);
+
+    // K2: beamform into y (the image itself without the envelope)
+    const bool env = hp.L > 0;
+    float *ybuf = y_target(p, d_image, d_y, scratch);
+    const BeamParams bp = beam_params(p, scratch, ybuf, d_cf);
+    e = kBeamLaunchers[hp.order](bp, hp.delay_mode, hp.chan_prec, hp.ng_prec, beam_blocks(p),
                                  p->smem_beam, s);
     if (e != cudaSuccess) return cuda_fail(p, e, "beamform_kernel launch");
     mark(p, 2, s);
@@ -207,13 +272,8 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
         return DMAS_OK;
     }
     // K3: envelope
-    EnvParams ep;
-    ep.y = ybuf;
-    ep.img = d_image;
-    ep.T = hp.T;
-    ep.n_tiles = (hp.T + kEnvTile - 1) / kEnvTile;
-    ep.L = hp.L;
-    const unsigned egrid = (unsigned)((size_t)hp.M * ep.n_tiles);
+    const EnvParams ep = env_params(p, ybuf, d_image);
+    const unsigned egrid = env_blocks(p);
     const int H = (hp.L - 1) / 2;
     if (H == 90)
         envelope_kernel<90><<<egrid, kEnvThreads, p->smem_env, s>>>(ep, p->taps);
@@ -225,6 +285,112 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
     mark(p, 3, s);
     p->env_ran = true;
     p->profiled_once = p->profiled_once || p->profiling;
+    return DMAS_OK;
+}
+
+// ---- batches ----------------------------------------------------------------
+struct BatchEntry {
+    dmas_plan *plan;
+    const float *frame;
+    float *image;
+    void *scratch;
+    float *ybuf;
+};
+
+// Enqueue a batch: one launch per (stage, kernel variant) for up to kBatchMax
+// entries at a time.
+dmas_status enqueue_batch(const std::vector<BatchEntry> &v, cudaStream_t s) {
+    cudaError_t e;
+    // K1: roots, grouped by channel type
+    for (int chan = 0; chan < 3; ++chan) {
+        std::vector<const BatchEntry *> sel;
+        for (const auto &x : v)
+            if (x.plan->hp.chan_prec == chan) sel.push_back(&x);
+        for (size_t b0 = 0; b0 < sel.size(); b0 += kBatchMax) {
+            RootsBatch rb{};
+            rb.count = (int)std::min<size_t>(kBatchMax, sel.size() - b0);
+            unsigned blocks = 0;
+            for (int k = 0; k < rb.count; ++k) {
+                const BatchEntry &x = *sel[b0 + k];
+                rb.start[k] = blocks;
+                rb.e[k] = roots_params(x.plan, x.frame, x.scratch);
+                blocks += roots_blocks(x.plan);
+            }
+            rb.start[rb.count] = blocks;
+            if (chan == DMAS_CH_F16) roots_batch_kernel<__half><<<blocks, 256, 0, s>>>(rb);
+            else if (chan == DMAS_CH_BF16) roots_batch_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(rb);
+            else roots_batch_kernel<float><<<blocks, 256, 0, s>>>(rb);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(sel[b0]->plan, e, "roots batch");
+        }
+    }
+    // K2: beamform, grouped by kernel variant
+    std::vector<bool> done(v.size(), false);
+    for (size_t i = 0; i < v.size(); ++i) {
+        if (done[i]) continue;
+        const HostPlan &a = v[i].plan->hp;
+        std::vector<size_t> cls;
+        for (size_t j = i; j < v.size(); ++j) {
+            const HostPlan &b = v[j].plan->hp;
+            if (!done[j] && b.order == a.order && b.delay_mode == a.delay_mode &&
+                b.chan_prec == a.chan_prec && b.ng_prec == a.ng_prec && b.pairs == a.pairs) {
+                cls.push_back(j);
+                done[j] = true;
+            }
+        }
+        for (size_t b0 = 0; b0 < cls.size(); b0 += kBatchMax) {
+            BeamBatch bb{};
+            bb.count = (int)std::min<size_t>(kBatchMax, cls.size() - b0);
+            unsigned blocks = 0;
+            size_t smem = 0;
+            for (int k = 0; k < bb.count; ++k) {
+                const BatchEntry &x = v[cls[b0 + k]];
+                bb.start[k] = blocks;
+                bb.e[k] = beam_params(x.plan, x.scratch, x.ybuf, nullptr);
+                blocks += beam_blocks(x.plan);
+                smem = std::max(smem, x.plan->smem_beam);
+            }
+            bb.start[bb.count] = blocks;
+            e = kBeamBatchLaunchers[a.order](bb, a.delay_mode, a.chan_prec, a.ng_prec, a.pairs,
+                                             blocks, smem, s);
+            if (e != cudaSuccess) return cuda_fail(v[cls[b0]].plan, e, "beamform batch");
+        }
+    }
+    // K3: envelope, grouped by identical taps
+    std::fill(done.begin(), done.end(), false);
+    for (size_t i = 0; i < v.size(); ++i) {
+        if (done[i] || v[i].plan->hp.L == 0) continue;
+        const HostPlan &a = v[i].plan->hp;
+        std::vector<size_t> cls;
+        for (size_t j = i; j < v.size(); ++j) {
+            const HostPlan &b = v[j].plan->hp;
+            if (!done[j] && b.L == a.L && b.taps == a.taps) {
+                cls.push_back(j);
+                done[j] = true;
+            }
+        }
+        const int H = (a.L - 1) / 2;
+        for (size_t b0 = 0; b0 < cls.size(); b0 += kBatchMax) {
+            EnvBatch eb{};
+            eb.count = (int)std::min<size_t>(kBatchMax, cls.size() - b0);
+            unsigned blocks = 0;
+            for (int k = 0; k < eb.count; ++k) {
+                const BatchEntry &x = v[cls[b0 + k]];
+                eb.start[k] = blocks;
+                eb.e[k] = env_params(x.plan, x.ybuf, x.image);
+                blocks += env_blocks(x.plan);
+            }
+            eb.start[eb.count] = blocks;
+            const dmas_plan *pa = v[cls[b0]].plan;
+            if (H == 90)
+                envelope_batch_kernel<90><<<blocks, kEnvThreads, pa->smem_env, s>>>(eb, pa->taps);
+            else if (H == 80)
+                envelope_batch_kernel<80><<<blocks, kEnvThreads, pa->smem_env, s>>>(eb, pa->taps);
+            else
+                envelope_batch_kernel<-1><<<blocks, kEnvThreads, pa->smem_env, s>>>(eb, pa->taps);
+            if ((e = cudaGetLastError()) != cudaSuccess)
+                return cuda_fail(v[cls[b0]].plan, e, "envelope batch");
+        }
+    }
     return DMAS_OK;
 }
 
@@ -375,13 +541,24 @@ dmas_status dmas_beamform_batch(int count, dmas_plan *const *plans, const float 
     if (workspace_bytes < dmas_batch_workspace_bytes(count, plans)) return DMAS_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     char *ws = (char *)d_workspace;
+    std::vector<BatchEntry> v;
+    try {
+        v.reserve(count);
+    } catch (const std::bad_alloc &) {
+        return DMAS_ENOMEM;
+    }
     for (int k = 0; k < count; ++k) {
         plans[k]->last_stream = s;
-        dmas_status st = enqueue_frame(plans[k], d_frames[k], d_images[k], nullptr, nullptr, ws, s);
-        if (st != DMAS_OK) return st;
+        BatchEntry x;
+        x.plan = plans[k];
+        x.frame = d_frames[k];
+        x.image = d_images[k];
+        x.scratch = ws;
+        x.ybuf = y_target(plans[k], d_images[k], nullptr, ws);
+        v.push_back(x);
         ws += dmas_plan_workspace_bytes(plans[k]);
     }
-    return DMAS_OK;
+    return enqueue_batch(v, s);
 }
 
 dmas_status dmas_plan_get_info(const dmas_plan *p, dmas_plan_info *info) {

@@ -43,13 +43,13 @@ __device__ __forceinline__ void env_stage(const float *__restrict__ y, int T, in
 }
 
 template <int HH>
-__global__ void __launch_bounds__(kEnvThreads)
-    envelope_kernel(const __grid_constant__ EnvParams p, const __grid_constant__ EnvTaps taps) {
+__device__ __forceinline__ void envelope_body(const EnvParams &p, const EnvTaps &taps,
+                                              unsigned block) {
     extern __shared__ __align__(16) float s_abs[];
     constexpr int HA = env_halo_aligned(HH);
     constexpr int Q = (kEnvR + HA + HH + 3) / 4;  // float4 loads per thread
-    const int rowi = (int)(blockIdx.x / (unsigned)p.n_tiles);
-    const int tile = (int)(blockIdx.x - (unsigned)rowi * (unsigned)p.n_tiles);
+    const int rowi = (int)(block / (unsigned)p.n_tiles);
+    const int tile = (int)(block - (unsigned)rowi * (unsigned)p.n_tiles);
     const int t0 = tile * kEnvTile;
     env_stage(p.y + (size_t)rowi * p.T, p.T, t0, HA, s_abs);
     __syncthreads();
@@ -81,14 +81,13 @@ __global__ void __launch_bounds__(kEnvThreads)
 }
 
 // Any FIR length (taps from shared memory, runtime loops).
-__global__ void __launch_bounds__(kEnvThreads)
-    envelope_generic_kernel(const __grid_constant__ EnvParams p,
-                            const __grid_constant__ EnvTaps taps) {
+__device__ __forceinline__ void envelope_generic_body(const EnvParams &p, const EnvTaps &taps,
+                                                      unsigned block) {
     extern __shared__ __align__(16) float s_abs[];
     const int H = (p.L - 1) / 2;
     const int HA = env_halo_aligned(H);
-    const int rowi = (int)(blockIdx.x / (unsigned)p.n_tiles);
-    const int tile = (int)(blockIdx.x - (unsigned)rowi * (unsigned)p.n_tiles);
+    const int rowi = (int)(block / (unsigned)p.n_tiles);
+    const int tile = (int)(block - (unsigned)rowi * (unsigned)p.n_tiles);
     const int t0 = tile * kEnvTile;
     float *s_h = s_abs + kEnvTile + 2 * HA;
     for (int k = threadIdx.x; k < p.L; k += kEnvThreads) s_h[k] = taps.h[k];
@@ -102,6 +101,35 @@ __global__ void __launch_bounds__(kEnvThreads)
         const int t = t0 + o;
         if (t < p.T) img[t] = acc;
     }
+}
+
+struct EnvBatch {
+    int count;
+    unsigned start[kBatchMax + 1];
+    EnvParams e[kBatchMax];
+};
+
+template <int HH>
+__global__ void __launch_bounds__(kEnvThreads)
+    envelope_kernel(const __grid_constant__ EnvParams p, const __grid_constant__ EnvTaps taps) {
+    envelope_body<HH>(p, taps, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kEnvThreads)
+    envelope_generic_kernel(const __grid_constant__ EnvParams p,
+                            const __grid_constant__ EnvTaps taps) {
+    envelope_generic_body(p, taps, blockIdx.x);
+}
+
+// A batch whose entries share one set of taps.
+template <int HH>
+__global__ void __launch_bounds__(kEnvThreads)
+    envelope_batch_kernel(const __grid_constant__ EnvBatch b, const __grid_constant__ EnvTaps taps) {
+    const int k = batch_entry(b.start, b.count, blockIdx.x);
+    if constexpr (HH >= 0)
+        envelope_body<HH>(b.e[k], taps, blockIdx.x - b.start[k]);
+    else
+        envelope_generic_body(b.e[k], taps, blockIdx.x - b.start[k]);
 }
 
 }  // namespace dmas

@@ -139,11 +139,10 @@ __device__ __forceinline__ float signed_root(float m, int order, float inv_order
 }
 
 template <typename CH>
-__global__ void __launch_bounds__(256) roots_kernel(const __grid_constant__ RootsParams p) {
+__device__ __forceinline__ void roots_body(const RootsParams &p, size_t first, size_t stride) {
     const size_t total = (size_t)p.N * (size_t)p.row;
     CH *chan = reinterpret_cast<CH *>(p.chan);
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
+    for (size_t idx = first; idx < total; idx += stride) {
         const int i = (int)(idx / (size_t)p.row);
         const int c = (int)(idx - (size_t)i * p.row);
         const int t = c - p.padl;
@@ -158,6 +157,43 @@ __global__ void __launch_bounds__(256) roots_kernel(const __grid_constant__ Root
             chan[total + idx] = to_ch<CH>(r1);
         }
     }
+}
+
+template <typename CH>
+__global__ void __launch_bounds__(256) roots_kernel(const __grid_constant__ RootsParams p) {
+    roots_body<CH>(p, (size_t)blockIdx.x * blockDim.x + threadIdx.x,
+                   (size_t)gridDim.x * blockDim.x);
+}
+
+// ---------------------------------------------------------------------------
+// Batched launches: up to kBatchMax entries (frames, each with its own plan)
+// in one grid.  Entry k owns blocks [start[k], start[k + 1]); the parameters
+// of every entry travel in the kernel's parameter space.
+// ---------------------------------------------------------------------------
+constexpr int kBatchMax = 64;
+
+__device__ __forceinline__ int batch_entry(const unsigned *start, int count, unsigned block) {
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= block) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct RootsBatch {
+    int count;
+    unsigned start[kBatchMax + 1];
+    RootsParams e[kBatchMax];
+};
+
+template <typename CH>
+__global__ void __launch_bounds__(256) roots_batch_kernel(const __grid_constant__ RootsBatch b) {
+    const int k = batch_entry(b.start, b.count, blockIdx.x);
+    const unsigned nb = b.start[k + 1] - b.start[k];
+    roots_body<CH>(b.e[k], (size_t)(blockIdx.x - b.start[k]) * blockDim.x + threadIdx.x,
+                   (size_t)nb * blockDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -316,8 +352,7 @@ __device__ __forceinline__ void accumulate(float (&a)[SumLayout<ORDER>::kNum], f
 }
 
 template <int ORDER, bool LINEAR, typename CH, int NGP>
-__global__ void __launch_bounds__(kThreads, 2)
-    beamform_kernel(const __grid_constant__ BeamParams p) {
+__device__ __forceinline__ void beamform_body(const BeamParams &p, unsigned block) {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int NA = SumLayout<ORDER>::kNum;
     constexpr int NP = SumLayout<ORDER>::kNumP;
@@ -329,8 +364,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     int *s_rel = reinterpret_cast<int *>(smem + 128 + win_bytes);
     float *s_frac = reinterpret_cast<float *>(s_rel + NC * 8);
 
-    const int tile = (int)(blockIdx.x / (unsigned)p.n_groups);
-    const int g = (int)(blockIdx.x - (unsigned)tile * (unsigned)p.n_groups);
+    const int tile = (int)(block / (unsigned)p.n_groups);
+    const int g = (int)(block - (unsigned)tile * (unsigned)p.n_groups);
     const int t0 = tile * (32 * kPix);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -483,8 +518,7 @@ __device__ __forceinline__ void accumulate2(f32x2_t (&a)[SumLayout<ORDER>::kNum]
 // PAIRS pixel pairs per lane: time tile 64 * PAIRS.  PAIRS = 2 keeps few
 // enough registers and shared memory for four CTAs per SM, PAIRS = 4 two.
 template <int ORDER, bool LINEAR, int NGP, int PAIRS>
-__global__ void __launch_bounds__(kThreads, PAIRS == 2 ? 4 : 2)
-    beamform_x2_kernel(const __grid_constant__ BeamParams p) {
+__device__ __forceinline__ void beamform_x2_body(const BeamParams &p, unsigned block) {
     constexpr int kPairs = PAIRS;
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int NA = SumLayout<ORDER>::kNum;
@@ -498,8 +532,8 @@ __global__ void __launch_bounds__(kThreads, PAIRS == 2 ? 4 : 2)
     int *s_rel = reinterpret_cast<int *>(smem + 128 + 2 * win_bytes);
     float *s_frac = reinterpret_cast<float *>(s_rel + NC * 8);
 
-    const int tile = (int)(blockIdx.x / (unsigned)p.n_groups);
-    const int g = (int)(blockIdx.x - (unsigned)tile * (unsigned)p.n_groups);
+    const int tile = (int)(block / (unsigned)p.n_groups);
+    const int g = (int)(block - (unsigned)tile * (unsigned)p.n_groups);
     const int t0 = tile * (64 * kPairs);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -604,6 +638,41 @@ __global__ void __launch_bounds__(kThreads, PAIRS == 2 ? 4 : 2)
             if (cfrow) cfrow[t] = cf;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// __global__ entry points: one frame, or a batch of frames (BeamBatch)
+// ---------------------------------------------------------------------------
+struct BeamBatch {
+    int count;
+    unsigned start[kBatchMax + 1];
+    BeamParams e[kBatchMax];
+};
+
+template <int ORDER, bool LINEAR, typename CH, int NGP>
+__global__ void __launch_bounds__(kThreads, 2)
+    beamform_kernel(const __grid_constant__ BeamParams p) {
+    beamform_body<ORDER, LINEAR, CH, NGP>(p, blockIdx.x);
+}
+
+template <int ORDER, bool LINEAR, typename CH, int NGP>
+__global__ void __launch_bounds__(kThreads, 2)
+    beamform_batch_kernel(const __grid_constant__ BeamBatch b) {
+    const int k = batch_entry(b.start, b.count, blockIdx.x);
+    beamform_body<ORDER, LINEAR, CH, NGP>(b.e[k], blockIdx.x - b.start[k]);
+}
+
+template <int ORDER, bool LINEAR, int NGP, int PAIRS>
+__global__ void __launch_bounds__(kThreads, PAIRS == 2 ? 4 : 2)
+    beamform_x2_kernel(const __grid_constant__ BeamParams p) {
+    beamform_x2_body<ORDER, LINEAR, NGP, PAIRS>(p, blockIdx.x);
+}
+
+template <int ORDER, bool LINEAR, int NGP, int PAIRS>
+__global__ void __launch_bounds__(kThreads, PAIRS == 2 ? 4 : 2)
+    beamform_x2_batch_kernel(const __grid_constant__ BeamBatch b) {
+    const int k = batch_entry(b.start, b.count, blockIdx.x);
+    beamform_x2_body<ORDER, LINEAR, NGP, PAIRS>(b.e[k], blockIdx.x - b.start[k]);
 }
 
 }  // namespace dmas

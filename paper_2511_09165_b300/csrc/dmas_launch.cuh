@@ -16,9 +16,9 @@ namespace dmas {
 // family's per-CTA opt-in maximum, 227 KB).
 constexpr int kBeamSmemOptIn = 227 * 1024;
 
-template <typename K>
-cudaError_t launch_kernel(K kern, std::once_flag &once, cudaError_t &attr_err,
-                          const BeamParams &p, unsigned grid, size_t smem, cudaStream_t s) {
+template <typename K, typename P>
+cudaError_t launch_kernel(K kern, std::once_flag &once, cudaError_t &attr_err, const P &p,
+                          unsigned grid, size_t smem, cudaStream_t s) {
     std::call_once(once, [&] {
         attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         kBeamSmemOptIn);
@@ -81,5 +81,63 @@ cudaError_t launch_beamform_order(const BeamParams &p, int linear, int chan, int
 
 using BeamLauncher = cudaError_t (*)(const BeamParams &, int, int, int, unsigned, size_t,
                                      cudaStream_t);
+
+// Batched launch of one kernel variant over up to kBatchMax entries.
+template <int ORDER, bool LINEAR, typename CH, int NGP>
+cudaError_t launch_beam_batch_variant(const BeamBatch &b, int pairs, unsigned grid, size_t smem,
+                                      cudaStream_t s) {
+    if constexpr (std::is_same<CH, float>::value && ORDER <= kPairMaxOrder) {
+        if (pairs == 4) {
+            static std::once_flag once;
+            static cudaError_t err = cudaSuccess;
+            return launch_kernel(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, 4>, once, err, b,
+                                 grid, smem, s);
+        }
+        static std::once_flag once;
+        static cudaError_t err = cudaSuccess;
+        return launch_kernel(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, 2>, once, err, b, grid,
+                             smem, s);
+    } else {
+        static std::once_flag once;
+        static cudaError_t err = cudaSuccess;
+        return launch_kernel(beamform_batch_kernel<ORDER, LINEAR, CH, NGP>, once, err, b, grid,
+                             smem, s);
+    }
+}
+
+template <int ORDER, bool LINEAR, typename CH>
+cudaError_t launch_beam_batch_ng(const BeamBatch &b, int ngp, int pairs, unsigned grid,
+                                 size_t smem, cudaStream_t s) {
+    switch (ngp) {
+        case NG_F64:
+            return launch_beam_batch_variant<ORDER, LINEAR, CH, NG_F64>(b, pairs, grid, smem, s);
+        case NG_CF32:
+            return launch_beam_batch_variant<ORDER, LINEAR, CH, NG_CF32>(b, pairs, grid, smem, s);
+        default:
+            return launch_beam_batch_variant<ORDER, LINEAR, CH, NG_F32>(b, pairs, grid, smem, s);
+    }
+}
+
+template <int ORDER>
+cudaError_t launch_beamform_batch_order(const BeamBatch &b, int linear, int chan, int ngp,
+                                        int pairs, unsigned grid, size_t smem, cudaStream_t s) {
+    if (linear) {
+        switch (chan) {
+            case 1: return launch_beam_batch_ng<ORDER, true, __half>(b, ngp, pairs, grid, smem, s);
+            case 2:
+                return launch_beam_batch_ng<ORDER, true, __nv_bfloat16>(b, ngp, pairs, grid, smem, s);
+            default: return launch_beam_batch_ng<ORDER, true, float>(b, ngp, pairs, grid, smem, s);
+        }
+    }
+    switch (chan) {
+        case 1: return launch_beam_batch_ng<ORDER, false, __half>(b, ngp, pairs, grid, smem, s);
+        case 2:
+            return launch_beam_batch_ng<ORDER, false, __nv_bfloat16>(b, ngp, pairs, grid, smem, s);
+        default: return launch_beam_batch_ng<ORDER, false, float>(b, ngp, pairs, grid, smem, s);
+    }
+}
+
+using BeamBatchLauncher = cudaError_t (*)(const BeamBatch &, int, int, int, int, unsigned, size_t,
+                                          cudaStream_t);
 
 }  // namespace dmas

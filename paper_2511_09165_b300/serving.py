@@ -1,0 +1,281 @@
+"""Continuous-batching server for sonar frames from several sensors.
+
+Each sensor has a resident plan (delay tables and taps on the device).  Frames
+arrive on the host at any time; the server
+
+  * admits a frame when the device-memory budget has room for its frame,
+    image and scratch (otherwise it waits in the FIFO queue; a frame that can
+    never fit is rejected),
+  * gathers every admitted frame that is waiting into one batch (up to
+    `max_batch`) and runs it with one `dmas_beamform_batch` call: one launch
+    per kernel stage and variant for the whole batch,
+  * keeps up to `streams` batches in flight on separate CUDA streams, so
+    frames that arrive while earlier batches run are batched and overlap with
+    them on the GPU,
+  * records, per frame, the time from its arrival to the completion of its
+    batch on the device (the image is then resident in device memory; with
+    `copy_back` the image is also copied to host memory first).
+
+The host threads only move pointers and events; every step of the
+beamforming path runs in the library's kernels.  Results do not depend on the
+batch a frame lands in: each entry uses its own scratch, so its image is
+bitwise identical to a `dmas_beamform` of that frame alone.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import beamform_batch, batch_workspace_bytes
+
+
+@dataclass
+class Sensor:
+    """A sensor: its plan and the device bytes one of its frames occupies."""
+    plan: object
+    name: str = ""
+
+    @property
+    def frame_shape(self):
+        return (self.plan.n_mics, self.plan.n_samples)
+
+    @property
+    def image_shape(self):
+        return (self.plan.n_dirs, self.plan.n_samples)
+
+    @property
+    def device_bytes(self) -> int:
+        n, t = self.frame_shape
+        m, _ = self.image_shape
+        return 4 * (n * t + m * t) + self.plan.workspace_bytes()
+
+
+@dataclass
+class Request:
+    sensor: int
+    frame: object                 # host tensor [N][T] float32 (pinned for overlap)
+    t_arrival: float              # time.perf_counter() seconds
+    keep_image: bool = False
+    t_admitted: float = 0.0
+    t_done: float = 0.0
+    batch_size: int = 0
+    image: object = None          # device tensor when keep_image, host tensor with copy_back
+    rejected: bool = False
+    done: threading.Event = field(default_factory=threading.Event)
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_arrival
+
+
+class Server:
+    def __init__(self, sensors, device=None, budget_bytes: int = 32 << 30,
+                 max_batch: int = 64, streams: int = 2, copy_back: bool = False):
+        import torch
+        self.torch = torch
+        self.sensors = list(sensors)
+        self.device = torch.device("cuda") if device is None else torch.device(device)
+        self.budget = int(budget_bytes)
+        self.max_batch = int(max_batch)
+        self.copy_back = bool(copy_back)
+        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(max(1, streams))]
+        self._queue: collections.deque = collections.deque()
+        self._cv = threading.Condition()
+        self._reserved = 0
+        self._in_flight = 0
+        self._next_stream = 0
+        self._inflight_q: collections.deque = collections.deque()
+        self._running = False
+        self._threads = []
+        self.batches = 0
+        self.completed: list[Request] = []
+
+    # -- lifecycle -------------------------------------------------------
+    def start(self):
+        self._running = True
+        self._threads = [threading.Thread(target=self._dispatch, daemon=True),
+                         threading.Thread(target=self._complete, daemon=True)]
+        for t in self._threads:
+            t.start()
+        return self
+
+    def stop(self):
+        with self._cv:
+            self._running = False
+            self._cv.notify_all()
+        for t in self._threads:
+            t.join(timeout=60)
+
+    def __enter__(self):
+        return self.start()
+
+    def __exit__(self, *exc):
+        self.stop()
+
+    def submit(self, sensor: int, frame, t_arrival: float | None = None,
+               keep_image: bool = False) -> Request:
+        req = Request(sensor, frame, time.perf_counter() if t_arrival is None else t_arrival,
+                      keep_image)
+        with self._cv:
+            self._queue.append(req)
+            self._cv.notify_all()
+        return req
+
+    def drain(self, timeout: float = 600.0) -> bool:
+        end = time.perf_counter() + timeout
+        with self._cv:
+            while self._queue or self._in_flight:
+                left = end - time.perf_counter()
+                if left <= 0:
+                    return False
+                self._cv.wait(timeout=min(left, 0.1))
+        return True
+
+    # -- dispatcher: admission and batching -------------------------------
+    def _dispatch(self):
+        while True:
+            with self._cv:
+                while self._running and not self._can_launch():
+                    self._cv.wait(timeout=0.05)
+                if not self._can_launch():
+                    return                          # stopped and nothing launchable
+                batch = []
+                while self._queue and len(batch) < self.max_batch:
+                    req = self._queue[0]
+                    need = self.sensors[req.sensor].device_bytes
+                    if need > self.budget:          # can never fit: reject
+                        self._queue.popleft()
+                        req.rejected = True
+                        req.t_done = time.perf_counter()
+                        req.done.set()
+                        continue
+                    if self._reserved + need > self.budget:
+                        break
+                    self._queue.popleft()
+                    self._reserved += need
+                    batch.append(req)
+                if not batch:
+                    continue
+                self._in_flight += 1
+                stream = self.streams[self._next_stream]
+                self._next_stream = (self._next_stream + 1) % len(self.streams)
+            now = time.perf_counter()
+            for r in batch:
+                r.t_admitted = now
+            self._launch(batch, stream)
+
+    def _can_launch(self) -> bool:
+        if not self._queue or self._in_flight >= len(self.streams):
+            return False
+        head = self.sensors[self._queue[0].sensor].device_bytes
+        return head > self.budget or self._reserved + head <= self.budget
+
+    def _launch(self, batch, stream):
+        torch = self.torch
+        with torch.cuda.stream(stream):
+            plans = [self.sensors[r.sensor].plan for r in batch]
+            frames, images = [], []
+            for r, p in zip(batch, plans):
+                f = torch.empty((p.n_mics, p.n_samples), device=self.device)
+                f.copy_(r.frame, non_blocking=True)
+                frames.append(f)
+                images.append(torch.empty((p.n_dirs, p.n_samples), device=self.device))
+            ws = torch.empty(batch_workspace_bytes(plans), device=self.device, dtype=torch.uint8)
+            beamform_batch(plans, frames, images, workspace=ws, stream=stream)
+            hosts = None
+            if self.copy_back:
+                hosts = [torch.empty(im.shape, dtype=torch.float32, pin_memory=True)
+                         for im in images]
+                for h, im in zip(hosts, images):
+                    h.copy_(im, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+        self.batches += 1
+        with self._cv:
+            self._inflight_q.append((ev, batch, frames, images, ws, hosts))
+            self._cv.notify_all()
+
+    # -- completion: latency and memory release ----------------------------
+    def _complete(self):
+        while True:
+            with self._cv:
+                while self._running and not self._inflight_q:
+                    self._cv.wait(timeout=0.05)
+                if not self._inflight_q:
+                    if not self._running:
+                        return
+                    continue
+                ev, batch, frames, images, ws, hosts = self._inflight_q.popleft()
+            ev.synchronize()
+            t = time.perf_counter()
+            for k, r in enumerate(batch):
+                r.t_done = t
+                r.batch_size = len(batch)
+                if r.keep_image:
+                    r.image = hosts[k] if hosts is not None else images[k]
+            with self._cv:
+                for r in batch:
+                    self._reserved -= self.sensors[r.sensor].device_bytes
+                    self.completed.append(r)
+                    r.done.set()
+                self._in_flight -= 1
+                self._cv.notify_all()
+
+
+def one_frame_per_launch(sensors, requests, device=None):
+    """Baseline: every frame alone through dmas_beamform, in arrival order, on
+    one stream.  Blocks until each frame's arrival time; returns the requests
+    with t_done filled."""
+    import torch
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    stream = torch.cuda.Stream(device=dev)
+    pending = collections.deque()
+    with torch.cuda.stream(stream):
+        for r in requests:
+            while time.perf_counter() < r.t_arrival:
+                while pending and pending[0][0].query():
+                    ev, q = pending.popleft()
+                    q.t_done = time.perf_counter()
+                time.sleep(0.0002)
+            p = sensors[r.sensor].plan
+            f = torch.empty((p.n_mics, p.n_samples), device=dev)
+            f.copy_(r.frame, non_blocking=True)
+            img = p(f, stream=stream)
+            ev = torch.cuda.Event()
+            ev.record(stream)
+            pending.append((ev, r))
+            r.batch_size = 1
+            if r.keep_image:
+                r.image = img
+    while pending:
+        ev, q = pending.popleft()
+        ev.synchronize()
+        q.t_done = time.perf_counter()
+    return requests
+
+
+def poisson_arrivals(rate_hz: float, duration_s: float, n_sensors: int, seed: int):
+    """Scheduled arrival offsets (s) and sensor indices of a Poisson stream."""
+    rng = np.random.default_rng(seed)
+    t, times, which = 0.0, [], []
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t >= duration_s:
+            break
+        times.append(t)
+        which.append(int(rng.integers(n_sensors)))
+    return np.array(times), np.array(which, dtype=np.int64)
+
+
+def latency_summary(reqs, t_from: float = -np.inf) -> dict:
+    """p50/p99/mean latency (ms) of requests that arrived at or after t_from."""
+    lat = np.array([r.latency for r in reqs if not r.rejected and r.t_arrival >= t_from])
+    if lat.size == 0:
+        return {"frames": 0}
+    return {"frames": int(lat.size), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+            "max_ms": float(lat.max() * 1e3)}

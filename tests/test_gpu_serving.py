@@ -1,0 +1,122 @@
+"""Batched launches and the continuous-batching server.
+
+A frame's image must not depend on the batch it runs in: every entry has its
+own scratch and the per-pixel arithmetic is the same, so the comparison with
+dmas_beamform of the frame alone is bitwise.
+"""
+import functools
+import time
+
+import numpy as np
+import pytest
+
+from workloads import scenes
+
+torch = pytest.importorskip("torch")
+dm = pytest.importorskip("paper_2511_09165_b300")
+from paper_2511_09165_b300 import serving  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _plan(sc, order, mode, **kw):
+    return dm.Plan(mic_xyz=sc.mic_xyz, dir_azel=sc.dir_azel, dir_unit=sc.dir_unit,
+                   n_samples=sc.n_samples, fs=sc.fs, c=sc.c, order=order, delay_mode=mode, **kw)
+
+
+def test_batch_of_mixed_variants_is_bitwise_equal_to_single_calls():
+    a = scenes.small_2d(seed=1, n_samples=1500)
+    b = scenes.hemi_3d(seed=2, n_samples=1100, n_dirs=100)
+    c = scenes.passive(seed=4, n_mics=40, n_samples=900, n_az=12, n_el=6)
+    plans = [
+        _plan(a, 5, dm.ROUND), _plan(a, 3, dm.ROUND), _plan(b, 5, dm.LINEAR),
+        _plan(b, 2, dm.LINEAR, ng_prec=dm.NG_CF32), _plan(a, 7, dm.ROUND),
+        _plan(a, 5, dm.ROUND, chan_prec=dm.CH_F16), _plan(c, 4, dm.ROUND, envelope=False),
+        _plan(a, 5, dm.ROUND, env_taps=51), _plan(c, 5, dm.LINEAR, cf=False),
+    ]
+    scs = [a, a, b, b, a, a, c, a, c]
+    frames = [torch.from_numpy(sc.frame).cuda() for sc in scs]
+    alone = [p(f).clone() for p, f in zip(plans, frames)]
+    # every plan twice, interleaved, in one batch
+    order = list(range(len(plans))) * 2
+    imgs = dm.beamform_batch([plans[k] for k in order], [frames[k] for k in order])
+    torch.cuda.synchronize()
+    for k, im in zip(order, imgs):
+        assert torch.equal(im, alone[k]), k
+    for p in plans:
+        p.check()
+        p.close()
+
+
+@functools.lru_cache(maxsize=None)
+def _small_mix():
+    return scenes.serving_mix(seed=7, n_sensors=6, frames_per_sensor=2, mics=(32, 48),
+                              dirs=(91, 2048), samples=(2048, 4096), orders=(3, 5))
+
+
+def _sensors(mix):
+    out = []
+    for s in mix:
+        plan = dm.Plan(mic_xyz=s.mic_xyz, dir_azel=s.dir_azel, dir_unit=s.dir_unit,
+                       n_samples=s.n_samples, fs=s.fs, c=s.c, order=s.order)
+        out.append(serving.Sensor(plan, s.name))
+    return out
+
+
+def test_server_results_equal_alone_and_in_the_mix():
+    mix = _small_mix()
+    sensors = _sensors(mix)
+    host = [[torch.from_numpy(f).pin_memory() for f in s.frames] for s in mix]
+    rng = np.random.default_rng(3)
+    reqs = []
+    with serving.Server(sensors, streams=2, max_batch=16) as srv:
+        for k in range(48):
+            si = int(rng.integers(len(mix)))
+            fi = int(rng.integers(len(host[si])))
+            reqs.append((si, fi, srv.submit(si, host[si][fi], keep_image=True)))
+            if k % 12 == 11:
+                time.sleep(0.002)           # arrivals while batches run
+        assert srv.drain(120.0)
+        assert srv.batches < len(reqs)      # frames were batched together
+    assert max(r.batch_size for _, _, r in reqs) > 1
+    for si, fi, r in reqs:
+        assert not r.rejected and r.latency > 0
+        alone = sensors[si].plan(host[si][fi].cuda())
+        assert torch.equal(r.image, alone)
+    for s in sensors:
+        s.plan.close()
+
+
+def test_server_admission_by_memory_and_rejection():
+    mix = _small_mix()
+    sensors = _sensors(mix)
+    sizes = [s.device_bytes for s in sensors]
+    budget = max(sizes)                     # one frame of the largest sensor at a time
+    host = [torch.from_numpy(s.frames[0]).pin_memory() for s in mix]
+    with serving.Server(sensors, budget_bytes=budget, streams=2) as srv:
+        reqs = [srv.submit(k % len(mix), host[k % len(mix)], keep_image=True) for k in range(12)]
+        assert srv.drain(120.0)
+    assert all(not r.rejected for r in reqs)
+    for k, r in enumerate(reqs):
+        assert torch.equal(r.image, sensors[k % len(mix)].plan(host[k % len(mix)].cuda()))
+    small = serving.Server(sensors, budget_bytes=min(sizes) - 1, streams=1)
+    with small:
+        r = small.submit(0, host[0])
+        assert small.drain(30.0)
+    assert r.rejected
+    for s in sensors:
+        s.plan.close()
+
+
+def test_one_frame_per_launch_baseline_matches():
+    mix = _small_mix()
+    sensors = _sensors(mix)
+    host = [torch.from_numpy(s.frames[0]).pin_memory() for s in mix]
+    t0 = time.perf_counter()
+    reqs = [serving.Request(k, host[k], t0 + 0.001 * k, keep_image=True) for k in range(len(mix))]
+    serving.one_frame_per_launch(sensors, reqs)
+    for k, r in enumerate(reqs):
+        assert r.t_done >= r.t_arrival
+        assert torch.equal(r.image, sensors[k].plan(host[k].cuda()))
+    for s in sensors:
+        s.plan.close()

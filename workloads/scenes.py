@@ -208,6 +208,64 @@ def passive(seed: int = 4, n_mics: int = 64, n_samples: int = 32768,
                  {"seed": seed, "sources": np.array(pos)})
 
 
+@dataclass
+class SensorSpec:
+    """One sensor of the serving mix: its array, direction grid and frames."""
+    name: str
+    mic_xyz: np.ndarray
+    n_samples: int
+    order: int
+    fs: float
+    c: float
+    dir_azel: np.ndarray | None
+    dir_unit: np.ndarray | None
+    frames: list  # seeded frames [N][T] float32
+
+    @property
+    def n_mics(self) -> int:
+        return int(self.mic_xyz.shape[0])
+
+    @property
+    def n_dirs(self) -> int:
+        return int((self.dir_unit if self.dir_unit is not None else self.dir_azel).shape[0])
+
+
+def serving_mix(seed: int = 5, n_sensors: int = 16, frames_per_sensor: int = 4,
+                mics=(32, 64, 128), dirs=(91, 2048, 8192), samples=(4096, 16384, 32768),
+                orders=(3, 5)) -> list:
+    """Sensors of the serving workload: each draws its microphone count, direction
+    grid (the 91-azimuth fan, the 2048-point hemisphere, the 128 x 64 az/el
+    grid), frame length and order; its array is a 12 cm disc of that many
+    microphones and its frames are small_2d-style echo scenes (3 reflectors,
+    20 dB SNR)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for s_i in range(n_sensors):
+        N = int(rng.choice(mics))
+        M = int(rng.choice(dirs))
+        T = int(rng.choice(samples))
+        n = int(rng.choice(orders))
+        fs, c = 450e3, SOUND_SPEED
+        mic = disc_array(rng, N, 0.06)
+        azel = unit = None
+        if M == 91:
+            azel = azimuth_fan()
+        elif M == 2048:
+            unit = fibonacci_hemisphere(2048)
+        else:
+            azel = azel_grid(128, 64)
+        frames = []
+        for _ in range(frames_per_sensor):
+            pos = []
+            for _ in range(3):
+                az = math.radians(rng.uniform(-60.0, 60.0))
+                pos.append(_point(az, 0.0, rng.uniform(0.5, 3.0)))
+            frames.append(_echo_frame(rng, mic, pos, [1.0] * 3, fs, T, c, 40e3, 50e-6,
+                                      0.1).astype(np.float32))
+        out.append(SensorSpec(f"sensor{s_i}", mic, T, n, fs, c, azel, unit, frames))
+    return out
+
+
 def plane_wave(n_mics: int, n_samples: int, az_deg: float, el_deg: float = 0.0,
                fs: float = 450e3, c: float = SOUND_SPEED, seed: int = 7,
                radius: float = 0.06, t0: float = 2e-3) -> Scene:
