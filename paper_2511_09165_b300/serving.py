@@ -12,6 +12,11 @@ arrive on the host at any time; the server
   * keeps up to `streams` batches in flight on separate CUDA streams, so
     frames that arrive while earlier batches run are batched and overlap with
     them on the GPU,
+  * sorts frames into two lanes by their cost N * M * T: small frames go to a
+    fast lane whose streams have high priority (the GPU schedules their CTAs
+    ahead of waiting CTAs of big frames) and are batched generously; big frames
+    go to a bulk lane in small batches, since batching them saves no launch
+    overhead worth having and a batch completes only when its last frame does,
   * records, per frame, the time from its arrival to the completion of its
     batch on the device (the image is then resident in device memory; with
     `copy_back` the image is also copied to host memory first).
@@ -53,6 +58,21 @@ class Sensor:
         m, _ = self.image_shape
         return 4 * (n * t + m * t) + self.plan.workspace_bytes()
 
+    @property
+    def cost(self) -> int:
+        """Work of one frame: microphones x directions x samples."""
+        return self.plan.n_mics * self.plan.n_dirs * self.plan.n_samples
+
+
+class _Lane:
+    def __init__(self, name, streams, max_batch):
+        self.name = name
+        self.streams = streams
+        self.max_batch = max_batch
+        self.queue = collections.deque()
+        self.in_flight = 0
+        self.next_stream = 0
+
 
 @dataclass
 class Request:
@@ -73,26 +93,38 @@ class Request:
 
 
 class Server:
+    """fast_cost: frames with cost <= fast_cost use the fast lane (default:
+    about 1 ms of GPU work, 1.3e9 mic x direction x samples).  Set streams
+    counts per lane; `streams` sets both."""
+
     def __init__(self, sensors, device=None, budget_bytes: int = 32 << 30,
-                 max_batch: int = 64, streams: int = 2, copy_back: bool = False):
+                 max_batch: int = 64, streams: int = 2, copy_back: bool = False,
+                 fast_cost: float = 1.3e9, bulk_batch: int = 2, bulk_streams: int | None = None):
         import torch
         self.torch = torch
         self.sensors = list(sensors)
         self.device = torch.device("cuda") if device is None else torch.device(device)
         self.budget = int(budget_bytes)
-        self.max_batch = int(max_batch)
         self.copy_back = bool(copy_back)
-        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(max(1, streams))]
-        self._queue: collections.deque = collections.deque()
+        self.fast_cost = float(fast_cost)
+        lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream,
+                                                              "priority_range") else (0, -1)
+        n_fast = max(1, streams)
+        n_bulk = max(1, streams if bulk_streams is None else bulk_streams)
+        self.fast = _Lane("fast", [torch.cuda.Stream(device=self.device, priority=hi)
+                                   for _ in range(n_fast)], int(max_batch))
+        self.bulk = _Lane("bulk", [torch.cuda.Stream(device=self.device, priority=lo)
+                                   for _ in range(n_bulk)], max(1, int(bulk_batch)))
         self._cv = threading.Condition()
         self._reserved = 0
-        self._in_flight = 0
-        self._next_stream = 0
         self._inflight_q: collections.deque = collections.deque()
         self._running = False
         self._threads = []
         self.batches = 0
         self.completed: list[Request] = []
+
+    def _lane_of(self, sensor: int) -> _Lane:
+        return self.fast if self.sensors[sensor].cost <= self.fast_cost else self.bulk
 
     # -- lifecycle -------------------------------------------------------
     def start(self):
@@ -121,14 +153,15 @@ class Server:
         req = Request(sensor, frame, time.perf_counter() if t_arrival is None else t_arrival,
                       keep_image)
         with self._cv:
-            self._queue.append(req)
+            self._lane_of(sensor).queue.append(req)
             self._cv.notify_all()
         return req
 
     def drain(self, timeout: float = 600.0) -> bool:
         end = time.perf_counter() + timeout
         with self._cv:
-            while self._queue or self._in_flight:
+            while (self.fast.queue or self.bulk.queue or self.fast.in_flight
+                   or self.bulk.in_flight):
                 left = end - time.perf_counter()
                 if left <= 0:
                     return False
@@ -139,42 +172,47 @@ class Server:
     def _dispatch(self):
         while True:
             with self._cv:
-                while self._running and not self._can_launch():
+                lane = None
+                while True:
+                    lane = next((ln for ln in (self.fast, self.bulk) if self._can_launch(ln)),
+                                None)
+                    if lane is not None or not self._running:
+                        break
                     self._cv.wait(timeout=0.05)
-                if not self._can_launch():
+                if lane is None:
                     return                          # stopped and nothing launchable
                 batch = []
-                while self._queue and len(batch) < self.max_batch:
-                    req = self._queue[0]
+                while lane.queue and len(batch) < lane.max_batch:
+                    req = lane.queue[0]
                     need = self.sensors[req.sensor].device_bytes
                     if need > self.budget:          # can never fit: reject
-                        self._queue.popleft()
+                        lane.queue.popleft()
                         req.rejected = True
                         req.t_done = time.perf_counter()
                         req.done.set()
                         continue
                     if self._reserved + need > self.budget:
                         break
-                    self._queue.popleft()
+                    lane.queue.popleft()
                     self._reserved += need
                     batch.append(req)
                 if not batch:
                     continue
-                self._in_flight += 1
-                stream = self.streams[self._next_stream]
-                self._next_stream = (self._next_stream + 1) % len(self.streams)
+                lane.in_flight += 1
+                stream = lane.streams[lane.next_stream]
+                lane.next_stream = (lane.next_stream + 1) % len(lane.streams)
             now = time.perf_counter()
             for r in batch:
                 r.t_admitted = now
-            self._launch(batch, stream)
+            self._launch(batch, stream, lane)
 
-    def _can_launch(self) -> bool:
-        if not self._queue or self._in_flight >= len(self.streams):
+    def _can_launch(self, lane) -> bool:
+        if not lane.queue or lane.in_flight >= len(lane.streams):
             return False
-        head = self.sensors[self._queue[0].sensor].device_bytes
+        head = self.sensors[lane.queue[0].sensor].device_bytes
         return head > self.budget or self._reserved + head <= self.budget
 
-    def _launch(self, batch, stream):
+    def _launch(self, batch, stream, lane):
         torch = self.torch
         with torch.cuda.stream(stream):
             plans = [self.sensors[r.sensor].plan for r in batch]
@@ -196,7 +234,7 @@ class Server:
             ev.record(stream)
         self.batches += 1
         with self._cv:
-            self._inflight_q.append((ev, batch, frames, images, ws, hosts))
+            self._inflight_q.append((ev, batch, frames, images, ws, hosts, lane))
             self._cv.notify_all()
 
     # -- completion: latency and memory release ----------------------------
@@ -209,8 +247,15 @@ class Server:
                     if not self._running:
                         return
                     continue
-                ev, batch, frames, images, ws, hosts = self._inflight_q.popleft()
-            ev.synchronize()
+                # any batch whose completion event has fired (fast lanes finish
+                # out of order with the bulk lane)
+                item = next((x for x in self._inflight_q if x[0].query()), None)
+                if item is not None:
+                    self._inflight_q.remove(item)
+            if item is None:
+                time.sleep(50e-6)
+                continue
+            ev, batch, frames, images, ws, hosts, lane = item
             t = time.perf_counter()
             for k, r in enumerate(batch):
                 r.t_done = t
@@ -222,7 +267,7 @@ class Server:
                     self._reserved -= self.sensors[r.sensor].device_bytes
                     self.completed.append(r)
                     r.done.set()
-                self._in_flight -= 1
+                lane.in_flight -= 1
                 self._cv.notify_all()
 
 
