@@ -1,0 +1,63 @@
+"""Precision forms on the small 2-D workload (32 mics, 91 azimuths, 4096
+samples): channels stored in FP32, FP16 or BF16, power sums in FP32, and
+Newton-Girard in FP32, FP64 or compensated FP32, for n = 3 and n = 5, each
+compared with the FP64 oracle.  Reported per image: eps_peak of y and of the
+envelope, max and mean per-pixel dB error within 60 dB of the peak, max CF
+error.  The table prints with `pytest -s`."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import scenes
+from parity import db_error, eps_peak, gpu_plan, oracle_run
+
+torch = pytest.importorskip("torch")
+dm = pytest.importorskip("paper_2511_09165_b300")
+
+pytestmark = pytest.mark.gpu
+
+# Bounds on eps_peak (y and envelope) per channel type, from measurement.
+BOUND = {"f32": 1e-5, "f16": 3e-3, "bf16": 3e-2}
+DB_BOUND = {"f32": 0.01, "f16": 0.1, "bf16": 1.0}   # max dB error within 60 dB of the peak
+
+
+@functools.lru_cache(maxsize=None)
+def _scene():
+    return scenes.small_2d(seed=1)
+
+
+@functools.lru_cache(maxsize=None)
+def _ref(order):
+    return oracle_run(_scene(), order, oracle.ROUND)
+
+
+def test_precision_table():
+    sc = _scene()
+    chans = {"f32": dm.CH_F32, "f16": dm.CH_F16, "bf16": dm.CH_BF16}
+    ngs = {"f32": dm.NG_F32, "f64": dm.NG_F64, "cf32": dm.NG_CF32}
+    rows = []
+    x = torch.from_numpy(sc.frame).cuda()
+    for order in (3, 5):
+        ref = _ref(order)
+        for cname, cp in chans.items():
+            for nname, ngp in ngs.items():
+                plan = gpu_plan(dm, sc, order, dm.ROUND, chan_prec=cp, ng_prec=ngp)
+                y = torch.empty((sc.n_dirs, sc.n_samples), device="cuda")
+                cf = torch.empty_like(y)
+                img = plan(x, y=y, cf=cf)
+                torch.cuda.synchronize()
+                plan.check()
+                plan.close()
+                y, cf, img = y.cpu().numpy(), cf.cpu().numpy(), img.cpu().numpy()
+                ey, ei = eps_peak(y, ref["y"]), eps_peak(img, ref["img"])
+                dmax, dmean = db_error(img, ref["img"], 60.0)
+                ecf = float(np.max(np.abs(cf - ref["cf"])))
+                rows.append((order, cname, nname, ey, ei, dmax, dmean, ecf))
+                assert ey <= BOUND[cname] and ei <= BOUND[cname], (order, cname, nname, ey, ei)
+                assert dmax <= DB_BOUND[cname], (order, cname, nname, dmax)
+    print("\n n  channels  NG    eps_peak(y)  eps_peak(img)  dB max  dB mean   CF max err")
+    for r in rows:
+        print(f" {r[0]}  {r[1]:8s}  {r[2]:4s}  {r[3]:11.3e}  {r[4]:13.3e}  {r[5]:6.4f}  "
+              f"{r[6]:7.5f}  {r[7]:10.3e}")
