@@ -1,6 +1,6 @@
 // C ABI of the DMAS-CF beamformer (declared in include/dmas.h): plan
 // lifecycle, device tables and scratch, and the launch sequence of one frame:
-//   roots_kernel -> beamform_kernel -> envelope_kernel.
+//   roots_kernel -> beamform kernel -> envelope_tc_kernel (tensor cores).
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -11,7 +11,7 @@
 
 #include "dmas.h"
 #include "dmas_internal.h"
-#include "dmas_envelope.cuh"
+#include "dmas_envelope_tc.cuh"
 #include "dmas_launch.cuh"
 
 namespace dmas {
@@ -77,7 +77,7 @@ struct dmas_plan {
     size_t chan_bytes = 0, ybuf_bytes = 0, table_bytes = 0;
     float *d_io_frame = nullptr, *d_io_image = nullptr;  // dmas_beamform_host staging
     size_t smem_beam = 0, smem_env = 0;
-    EnvTaps taps{};
+    float *d_taps_tc = nullptr;       // envelope taps as TF32 hi/lo phase arrays [2][4][Z]
     int num_sms = 148;
     cudaStream_t last_stream = nullptr;
     std::string last_error;
@@ -122,6 +122,8 @@ void free_plan_memory(dmas_plan *p) {
     cudaFree(p->d_scratch);
     cudaFree(p->d_io_frame);
     cudaFree(p->d_io_image);
+    cudaFree(p->d_taps_tc);
+    p->d_taps_tc = nullptr;
     for (auto &e : p->ev) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
@@ -154,8 +156,103 @@ size_t beam_smem_bytes(const HostPlan &hp) {
 
 size_t env_smem_bytes(const HostPlan &hp) {
     if (hp.L == 0) return 0;
-    const int HA = env_halo_aligned((hp.L - 1) / 2);
-    return sizeof(float) * ((size_t)kEnvTile + 2 * HA + hp.L);
+    const int Z = tc_Z((hp.L - 1) / 2);
+    return (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023) + (size_t)kTcStages * kTcStageBytes;
+}
+
+// TF32 rounding (nearest, ties away from zero) of a finite float, as cvt.rna.
+float tf32_host(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float y;
+    std::memcpy(&y, &u, 4);
+    return y;
+}
+
+// Phase arrays of the tensor-core envelope: copy r holds, at index z, the tap
+// that multiplies |y[t0 - HA + u]| for output 4q + r where z = u + 4 q' and
+// q' = Nq - 1 - q:  g~[z - 4 (Nq - 1) - r],  g~[w] = h[2H - (w - (HA - H))]
+// (e[t] = sum_k h[k] |y[t - k]|), split into TF32 hi and lo parts.
+std::vector<float> tc_tap_arrays(const HostPlan &hp) {
+    const int H = (hp.L - 1) / 2, HA = tc_halo(H), Z = tc_Z(H);
+    std::vector<float> out((size_t)8 * Z, 0.0f);
+    for (int r = 0; r < 4; ++r) {
+        for (int z = 0; z < Z; ++z) {
+            const int w = z - 4 * (kTcNq - 1) - r;
+            const int x = w - (HA - H);
+            if (x < 0 || x > 2 * H) continue;
+            const float gv = hp.taps[2 * H - x];
+            const float hi = tf32_host(gv);
+            out[(size_t)r * Z + z] = hi;
+            out[(size_t)(4 + r) * Z + z] = gv - hi;
+        }
+    }
+    return out;
+}
+
+cudaError_t launch_env_tc(const EnvTcParams &ep, unsigned grid, size_t smem, cudaStream_t s) {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [&] {
+        // the kernel also has ~1 KB of static shared memory (barriers, TMEM slot)
+        attr = cudaFuncSetAttribute(envelope_tc_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 222 * 1024);
+    });
+    if (attr != cudaSuccess) return attr;
+    envelope_tc_kernel<<<grid, kTcThreadsWS, smem, s>>>(ep);
+    return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime.
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+    static std::once_flag once;
+    static EncodeTiledFn fn = nullptr;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+        cudaGetLastError();
+    });
+    return fn;
+}
+
+EnvTcJob env_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned first) {
+    EnvTcJob j;
+    std::memset(&j, 0, sizeof(j));
+    j.use_tma = 0;
+    if ((p->hp.T & 3) == 0 && ((uintptr_t)ybuf & 15) == 0) {
+        if (EncodeTiledFn enc = encode_tiled()) {
+            cuuint64_t dims[3] = {4, (cuuint64_t)p->hp.M, (cuuint64_t)(p->hp.T / 4)};
+            cuuint64_t strides[2] = {(cuuint64_t)p->hp.T * 4, 16};
+            cuuint32_t box[3] = {4, 8, 16};
+            cuuint32_t es[3] = {1, 1, 1};
+            if (enc(&j.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)ybuf, dims, strides, box,
+                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+                j.use_tma = 1;
+        }
+    }
+    j.y = ybuf;
+    j.img = d_image;
+    j.M = p->hp.M;
+    j.T = p->hp.T;
+    j.t_tiles = (p->hp.T + kTcJ - 1) / kTcJ;
+    j.first = first;
+    return j;
+}
+
+unsigned env_tiles(const dmas_plan *p) {
+    return (unsigned)(((size_t)p->hp.M + kTcRows - 1) / kTcRows *
+                      (((size_t)p->hp.T + kTcJ - 1) / kTcJ));
 }
 
 void mark(dmas_plan *p, int k, cudaStream_t s) {
@@ -220,20 +317,6 @@ unsigned beam_blocks(const dmas_plan *p) {
     return (unsigned)((size_t)p->hp.n_groups * p->hp.n_tiles);
 }
 
-EnvParams env_params(const dmas_plan *p, const float *ybuf, float *d_image) {
-    EnvParams ep;
-    ep.y = ybuf;
-    ep.img = d_image;
-    ep.T = p->hp.T;
-    ep.n_tiles = (p->hp.T + kEnvTile - 1) / kEnvTile;
-    ep.L = p->hp.L;
-    return ep;
-}
-
-unsigned env_blocks(const dmas_plan *p) {
-    return (unsigned)((size_t)p->hp.M * ((p->hp.T + kEnvTile - 1) / kEnvTile));
-}
-
 // Enqueue the whole path for one frame with the given scratch.
 dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, float *d_y,
                           float *d_cf, void *scratch, cudaStream_t s) {
@@ -271,17 +354,16 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
         p->profiled_once = p->profiled_once || p->profiling;
         return DMAS_OK;
     }
-    // K3: envelope
-    const EnvParams ep = env_params(p, ybuf, d_image);
-    const unsigned egrid = env_blocks(p);
-    const int H = (hp.L - 1) / 2;
-    if (H == 90)
-        envelope_kernel<90><<<egrid, kEnvThreads, p->smem_env, s>>>(ep, p->taps);
-    else if (H == 80)
-        envelope_kernel<80><<<egrid, kEnvThreads, p->smem_env, s>>>(ep, p->taps);
-    else
-        envelope_generic_kernel<<<egrid, kEnvThreads, p->smem_env, s>>>(ep, p->taps);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(p, e, "envelope_kernel launch");
+    // K3: envelope on the tensor cores
+    EnvTcParams ep{};
+    ep.count = 1;
+    ep.job[0] = env_job(p, ybuf, d_image, 0);
+    ep.total_tiles = env_tiles(p);
+    ep.H = (hp.L - 1) / 2;
+    ep.taps = p->d_taps_tc;
+    ep.err = p->d_err;
+    e = launch_env_tc(ep, std::min<unsigned>(ep.total_tiles, (unsigned)p->num_sms), p->smem_env, s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "envelope_tc_kernel launch");
     mark(p, 3, s);
     p->env_ran = true;
     p->profiled_once = p->profiled_once || p->profiling;
@@ -368,27 +450,22 @@ dmas_status enqueue_batch(const std::vector<BatchEntry> &v, cudaStream_t s) {
                 done[j] = true;
             }
         }
-        const int H = (a.L - 1) / 2;
         for (size_t b0 = 0; b0 < cls.size(); b0 += kBatchMax) {
-            EnvBatch eb{};
-            eb.count = (int)std::min<size_t>(kBatchMax, cls.size() - b0);
-            unsigned blocks = 0;
-            for (int k = 0; k < eb.count; ++k) {
+            EnvTcParams ep{};
+            ep.count = (int)std::min<size_t>(kBatchMax, cls.size() - b0);
+            unsigned tiles = 0;
+            for (int k = 0; k < ep.count; ++k) {
                 const BatchEntry &x = v[cls[b0 + k]];
-                eb.start[k] = blocks;
-                eb.e[k] = env_params(x.plan, x.ybuf, x.image);
-                blocks += env_blocks(x.plan);
+                ep.job[k] = env_job(x.plan, x.ybuf, x.image, tiles);
+                tiles += env_tiles(x.plan);
             }
-            eb.start[eb.count] = blocks;
             const dmas_plan *pa = v[cls[b0]].plan;
-            if (H == 90)
-                envelope_batch_kernel<90><<<blocks, kEnvThreads, pa->smem_env, s>>>(eb, pa->taps);
-            else if (H == 80)
-                envelope_batch_kernel<80><<<blocks, kEnvThreads, pa->smem_env, s>>>(eb, pa->taps);
-            else
-                envelope_batch_kernel<-1><<<blocks, kEnvThreads, pa->smem_env, s>>>(eb, pa->taps);
-            if ((e = cudaGetLastError()) != cudaSuccess)
-                return cuda_fail(v[cls[b0]].plan, e, "envelope batch");
+            ep.total_tiles = tiles;
+            ep.H = (a.L - 1) / 2;
+            ep.taps = pa->d_taps_tc;
+            ep.err = pa->d_err;
+            e = launch_env_tc(ep, std::min<unsigned>(tiles, (unsigned)pa->num_sms), pa->smem_env, s);
+            if (e != cudaSuccess) return cuda_fail(v[cls[b0]].plan, e, "envelope batch");
         }
     }
     return DMAS_OK;
@@ -439,7 +516,6 @@ dmas_status dmas_plan_create(const dmas_plan_desc *desc, dmas_plan **out) {
     cudaGetLastError();
     p->smem_beam = beam_smem_bytes(hp);
     p->smem_env = env_smem_bytes(hp);
-    for (int k = 0; k < hp.L; ++k) p->taps.h[k] = hp.taps[k];
     cudaError_t e;
     if ((e = upload(&p->d_gdir, hp.gdir)) != cudaSuccess ||
         (e = upload(&p->d_gws, hp.gws)) != cudaSuccess ||
@@ -449,6 +525,22 @@ dmas_status dmas_plan_create(const dmas_plan_desc *desc, dmas_plan **out) {
         delete p;
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? DMAS_ENOMEM : DMAS_ECUDA;
+    }
+    if (hp.L > 0) {
+        std::vector<float> tc;
+        try {
+            tc = tc_tap_arrays(hp);
+        } catch (const std::bad_alloc &) {
+            free_plan_memory(p);
+            delete p;
+            return DMAS_ENOMEM;
+        }
+        if ((e = upload(&p->d_taps_tc, tc)) != cudaSuccess) {
+            free_plan_memory(p);
+            delete p;
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? DMAS_ENOMEM : DMAS_ECUDA;
+        }
     }
     p->table_bytes = (hp.gdir.size() + hp.gws.size() + hp.rel.size()) * 4 + hp.gfrac.size() * 4;
     // the pair kernel also reads every root row shifted by one sample

@@ -1,0 +1,404 @@
+// Envelope low-pass on the tensor cores (tcgen05, kind::tf32).
+//
+// The FIR  e[d][t] = sum_x g[x] |y[d][t - H + x]|  (g the symmetric taps,
+// x = 0..2H) is, for a tile of 128 direction rows and J = 256 output samples
+// starting at t0, the product  E[128][J] = A[128][K] . B[K][J]  with
+//   A[m][u] = |y[d0 + m][t0 - HA + u]|        (u = 0..K-1, K = J + 2 HA)
+//   B[u][j] = g~[u - j]                        (a band: the taps slid by j)
+// where HA = H rounded up to 4 (so every load starts 16-byte aligned) and g~ is
+// g shifted by HA - H and zero outside the taps.  A is K-major (rows of y are
+// contiguous in t).  B is K-major too, but its rows are the tap vector slid by
+// one sample each, and a shared-memory matrix descriptor can only step rows by
+// 16 bytes (4 samples): so the J outputs are taken as 4 phases r (j = 4q + r),
+// and phase r's 64 columns, in reverse order of q, are rows of a tap array
+// that step by exactly 16 bytes -- one descriptor over one array per phase, no
+// Toeplitz matrix materialised.  Phase r accumulates into TMEM columns
+// [64 r, 64 r + 64).
+//
+// FP32 accuracy from TF32 products: A = A_hi + A_lo and g = g_hi + g_lo with
+// the _hi parts rounded to TF32; each k-step issues A_hi.B_hi + A_hi.B_lo +
+// A_lo.B_hi (the dropped A_lo.B_lo term is ~2^-22 relative).
+//
+// CTA: 256 threads, two per direction row of the tile, persistent over tiles
+// (and over the frames of a batch).  Per k-block of 64 samples: each thread
+// issues all eight of its 16-byte loads before using any (enough bytes in
+// flight to cover the memory latency), takes |y|, splits it and stores
+// A_hi/A_lo into one of two shared-memory buffers
+// in the canonical K-major no-swizzle layout (core matrix = 8 rows x 16 bytes);
+// thread 0 issues 8 k-steps x 4 phases x 3 MMAs and commits them to that
+// buffer's mbarrier, which the threads wait on (bounded) before refilling the
+// buffer two k-blocks later.  After a tile's last k-block the threads read
+// their row of the accumulator from TMEM and store 4 consecutive outputs at a
+// time.
+#pragma once
+
+#include <cuda.h>
+
+#include "dmas_kernels.cuh"
+
+namespace dmas {
+
+constexpr int kTcRows = 128;         // direction rows per tile (MMA M)
+constexpr int kTcJ = 256;            // output samples per tile
+constexpr int kTcNq = kTcJ / 4;      // columns per phase (MMA N)
+constexpr int kTcKB = 64;            // samples per k-block
+constexpr int kTcThreads = 256;   // (unused by the warp-specialised kernel)
+constexpr int kTcBufBytes = kTcRows * kTcKB * 4;  // one of A_hi / A_lo for a k-block
+
+__host__ __device__ inline int tc_halo(int H) { return (H + 3) & ~3; }
+__host__ __device__ inline int tc_K(int H) { return kTcJ + 2 * tc_halo(H); }
+// length of one phase tap array (floats), a multiple of 8
+__host__ __device__ inline int tc_Z(int H) { return (tc_K(H) + 4 * (kTcNq - 1) + 7) & ~7; }
+
+struct EnvTcJob {
+    // 3-D view of y for the TMA engine when T % 4 == 0: dims (4 samples, M rows,
+    // T/4 chunks), strides (T*4 B, 16 B); a box {4, 8, 16} lands as the 16 core
+    // matrices (8 rows x 16 B) of one 8-row group of a k-block, out-of-range
+    // coordinates filled with zeros.
+    CUtensorMap tmap;
+    const float *y;   // [M][T]
+    float *img;       // [M][T]
+    int M, T;
+    int t_tiles;      // ceil(T / kTcJ)
+    int use_tma;      // T % 4 == 0 and the map was encoded
+    unsigned first;   // first tile of this job in the launch
+};
+
+struct EnvTcParams {
+    int count;
+    unsigned total_tiles;
+    int H;
+    const float *taps;  // [2][4][Z]: hi then lo, phase r = 0..3 (device)
+    unsigned *err;
+    EnvTcJob job[kBatchMax];
+};
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
+    d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for sm_100-family tcgen05
+    return d;                // base offset 0, no swizzle
+}
+
+// kind::tf32 instruction descriptor: D f32, A/B tf32, both K-major, N and M.
+__host__ __device__ constexpr uint32_t tc_idesc(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_addr(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+// make `bar`'s phase wait for this thread's earlier cp.async copies (adds a
+// pending arrival now, completes it when the copies have landed)
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::
+                     "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Tile -> (job, row block, time tile).
+struct TcTile {
+    const EnvTcJob *job;
+    int row0, t0;
+};
+__device__ __forceinline__ TcTile tc_tile(const EnvTcParams &p, unsigned tile) {
+    int k = 0;
+    while (k + 1 < p.count && p.job[k + 1].first <= tile) ++k;
+    const EnvTcJob &jb = p.job[k];
+    const unsigned local = tile - jb.first;
+    const int rb = (int)(local / (unsigned)jb.t_tiles);
+    const int tt = (int)(local - (unsigned)rb * (unsigned)jb.t_tiles);
+    return {&jb, rb * kTcRows, tt * kTcJ};
+}
+
+// Warp roles: 0-3 split (one row each), 4-7 epilogue (TMEM lane quarters),
+// 8 producer (cp.async), 9 MMA issue (lane 0) and TMEM allocation.
+constexpr int kTcStages = 3;
+constexpr int kTcWarps = 10;
+constexpr int kTcThreadsWS = kTcWarps * 32;
+constexpr int kTcStageBytes = 2 * kTcBufBytes;  // A_hi (loaded raw, split in place) + A_lo
+
+__global__ void __launch_bounds__(kTcThreadsWS, 1)
+    envelope_tc_kernel(const __grid_constant__ EnvTcParams p) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t full[kTcStages], split_done[kTcStages], empty[kTcStages];
+    __shared__ uint64_t acc_full[2], acc_empty[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int H = p.H, HA = tc_halo(H), K = tc_K(H), Z = tc_Z(H);
+    const int n_kb = (K + kTcKB - 1) / kTcKB;
+    float *s_taps = reinterpret_cast<float *>(smem);                               // [2][4][Z]
+    unsigned char *stages = smem + (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023);  // [S][hi,lo]
+    const unsigned n_tiles = (blockIdx.x < p.total_tiles)
+                                 ? (p.total_tiles - 1 - blockIdx.x) / gridDim.x + 1
+                                 : 0;
+
+    for (int i = tid; i < 8 * Z; i += kTcThreadsWS) s_taps[i] = p.taps[i];
+    if (warp == 9) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(&full[s], 1);         // producer lane 0 (+ bytes or cp.async arrivals)
+            mbar_init(&split_done[s], 128); // split threads
+            mbar_init(&empty[s], 1);        // MMA commit
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);     // MMA commit after a tile's last k-block
+            mbar_init(&acc_empty[a], 128);  // epilogue threads
+        }
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+
+    auto wait = [&](uint64_t *bar, uint32_t parity) -> bool {
+        if (abort_flag) return false;
+        if (mbar_wait_bounded(bar, parity)) return true;
+        abort_flag = 1;
+        atomicOr(p.err, kErrTimeout);
+        return false;
+    };
+
+    if (warp == 8) {
+        // ------------------------------ producer -----------------------------
+        unsigned g = 0;
+        for (unsigned i = 0; i < n_tiles; ++i) {
+            const TcTile tl = tc_tile(p, blockIdx.x + i * gridDim.x);
+            const EnvTcJob &jb = *tl.job;
+            for (int kb = 0; kb < n_kb; ++kb, ++g) {
+                const int s = (int)(g % kTcStages);
+                const unsigned use = g / kTcStages;
+                if (use > 0 && !wait(&empty[s], (use - 1) & 1u)) goto done;
+                float *ahi = reinterpret_cast<float *>(stages + (size_t)s * kTcStageBytes);
+                const int u0 = kb * kTcKB;
+                const int nc4 = min(kTcKB, K - u0) / 4;
+                if (jb.use_tma) {
+                    // 16 boxes of 8 rows x 16 chunks (32 KB); chunks past K land in
+                    // the unused tail of the buffer
+                    if (lane == 0) {
+                        mbar_arrive_expect_tx(&full[s], 16u * 2048u);
+                        const int chunk0 = (tl.t0 - HA + u0) / 4;  // exact: all terms % 4 == 0
+                        for (int a = 0; a < kTcRows / 8; ++a)
+                            tma_load_3d(ahi + a * 512, &jb.tmap, 0, tl.row0 + 8 * a, chunk0,
+                                        &full[s]);
+                    }
+                    continue;
+                }
+                // fallback (T % 4 != 0): chunk (m, c), 4 samples of row m at
+                // t = t0 - HA + u0 + 4c, copied to the canonical K-major position of
+                // A (core matrix 8 rows x 16 B) by 4-byte cp.async with zero fill
+                for (int idx = lane; idx < kTcRows * nc4; idx += 32) {
+                    const int m = idx % kTcRows, c = idx / kTcRows;
+                    const int row = tl.row0 + m;
+                    const int t = tl.t0 - HA + u0 + 4 * c;
+                    float *dst = ahi + (((m & 7) * 16 + (m >> 3) * 2048 + c * 128) >> 2);
+                    const float *rowp = jb.y + (size_t)(row < jb.M ? row : 0) * jb.T;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const bool in = row < jb.M && t + e >= 0 && t + e < jb.T;
+                        cp_async4(dst + e, in ? rowp + t + e : jb.y, in ? 4u : 0u);
+                    }
+                }
+                cp_async_arrive(&full[s]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[s]);
+            }
+        }
+    } else if (warp < 4) {
+        // -------------------------- split |y| -> hi, lo ---------------------
+        const int m = tid;  // row of the tile
+        const int rowoff = (m & 7) * 16 + (m >> 3) * 2048;
+        unsigned g = 0;
+        for (unsigned i = 0; i < n_tiles; ++i) {
+            for (int kb = 0; kb < n_kb; ++kb, ++g) {
+                const int s = (int)(g % kTcStages);
+                if (!wait(&full[s], (g / kTcStages) & 1u)) goto done;
+                float *ahi = reinterpret_cast<float *>(stages + (size_t)s * kTcStageBytes);
+                float *alo = ahi + kTcBufBytes / 4;
+                const int nc4 = min(kTcKB, K - kb * kTcKB) / 4;
+#pragma unroll 4
+                for (int c = 0; c < nc4; ++c) {
+                    const int off = (rowoff + c * 128) >> 2;
+                    const float4 v = *reinterpret_cast<const float4 *>(ahi + off);
+                    float4 h, l;
+                    h.x = tf32_round(fabsf(v.x)); l.x = fabsf(v.x) - h.x;
+                    h.y = tf32_round(fabsf(v.y)); l.y = fabsf(v.y) - h.y;
+                    h.z = tf32_round(fabsf(v.z)); l.z = fabsf(v.z) - h.z;
+                    h.w = tf32_round(fabsf(v.w)); l.w = fabsf(v.w) - h.w;
+                    *reinterpret_cast<float4 *>(ahi + off) = h;
+                    *reinterpret_cast<float4 *>(alo + off) = l;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(&split_done[s]);
+            }
+        }
+    } else if (warp == 9) {
+        // ------------------------------ MMA issue ----------------------------
+        const uint32_t idesc = tc_idesc(kTcRows, kTcNq);
+        const uint32_t taps_base = smem_addr(s_taps);
+        unsigned g = 0;
+        for (unsigned i = 0; i < n_tiles; ++i) {
+            const int a = (int)(i & 1u);
+            // the epilogue must have drained this accumulator (tile i - 2)
+            if (i >= 2 && !wait(&acc_empty[a], ((i >> 1) - 1) & 1u)) goto done;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dacc = tmem + (uint32_t)(a * 256);
+            for (int kb = 0; kb < n_kb; ++kb, ++g) {
+                const int s = (int)(g % kTcStages);
+                if (!wait(&split_done[s], (g / kTcStages) & 1u)) goto done;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (lane == 0) {
+                    const uint32_t a_hi = smem_addr(stages + (size_t)s * kTcStageBytes);
+                    const int u0 = kb * kTcKB;
+                    const int nks = min(kTcKB, K - u0) / 8;
+                    // descriptors of the k-block's first k-step; a k-step advances A by
+                    // two core matrices (256 B) and B by 8 samples (32 B): +16 and +2
+                    // in the descriptors' 16-byte address field
+                    const uint64_t dah0 = smem_desc(a_hi, 128, 2048);
+                    const uint64_t dal0 = smem_desc(a_hi + kTcBufBytes, 128, 2048);
+                    uint64_t dbh0[4], dbl0[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        dbh0[r] = smem_desc(taps_base + (uint32_t)(r * Z * 4 + u0 * 4), 16, 128);
+                        dbl0[r] = smem_desc(taps_base + (uint32_t)((4 + r) * Z * 4 + u0 * 4), 16, 128);
+                    }
+                    const uint32_t acc0 = kb > 0 ? 1u : 0u;
+#pragma unroll
+                    for (int ks = 0; ks < kTcKB / 8; ++ks) {
+                        if (ks < nks) {
+                            const uint64_t dah = dah0 + (uint64_t)(16 * ks);
+                            const uint64_t dal = dal0 + (uint64_t)(16 * ks);
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) {
+                                const uint32_t d = dacc + (uint32_t)(r * kTcNq);
+                                const uint64_t dbh = dbh0[r] + (uint64_t)(2 * ks);
+                                const uint64_t dbl = dbl0[r] + (uint64_t)(2 * ks);
+                                tc_mma(d, dah, dbh, idesc, (ks > 0) ? 1u : acc0);
+                                tc_mma(d, dah, dbl, idesc, 1u);
+                                tc_mma(d, dal, dbh, idesc, 1u);
+                            }
+                        }
+                    }
+                    tc_commit(&empty[s]);                     // stage s may be refilled
+                    if (kb == n_kb - 1) tc_commit(&acc_full[a]);  // the tile is complete
+                }
+                __syncwarp();
+            }
+        }
+    } else {
+        // ------------------------------ epilogue -----------------------------
+        const int m = (warp & 3) * 32 + lane;  // TMEM lane = row of the tile
+        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        for (unsigned i = 0; i < n_tiles; ++i) {
+            const int a = (int)(i & 1u);
+            const TcTile tl = tc_tile(p, blockIdx.x + i * gridDim.x);
+            const EnvTcJob &jb = *tl.job;
+            const bool vec = (jb.T & 3) == 0;
+            if (!wait(&acc_full[a], (i >> 1) & 1u)) goto done;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int row = tl.row0 + m;
+            const bool row_ok = row < jb.M;
+            float *irow = jb.img + (size_t)(row_ok ? row : 0) * jb.T;
+#pragma unroll 1
+            for (int qc = 0; qc < kTcNq; qc += 16) {
+                float v[4][16];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    tmem_ld16(lane_base + (uint32_t)(a * 256 + r * kTcNq + qc), v[r]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row_ok) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        // column qc + k of phase r holds output j = 4 (Nq - 1 - qc - k) + r
+                        const int t = tl.t0 + 4 * (kTcNq - 1 - qc - k);
+                        if (vec && t + 3 < jb.T) {
+                            *reinterpret_cast<float4 *>(irow + t) =
+                                make_float4(v[0][k], v[1][k], v[2][k], v[3][k]);
+                        } else {
+#pragma unroll
+                            for (int r = 0; r < 4; ++r)
+                                if (t + r < jb.T) irow[t + r] = v[r][k];
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(&acc_empty[a]);
+        }
+    }
+done:
+    // on an abort, give MMAs and copies in flight time to land before the
+    // shared memory and TMEM are released
+    if (abort_flag) {
+        const unsigned long long t0 = global_ns();
+        while (global_ns() - t0 < 100000000ull) {
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 9)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                     : "memory");
+}
+
+}  // namespace dmas
