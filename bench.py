@@ -72,6 +72,23 @@ WORKLOADS = {
 }
 
 
+# DRAM bytes (read + write) of one beamform launch on the default workload, from
+# one ncu capture (profiles/beamform_x2_hemi3d_n5.md), valid while the kernel
+# source is the one that was measured.
+TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "kernel_src_sha256_16": "6055555d481262c1",
+                  "bytes": 4868096 + 74967040}
+
+
+def beam_traffic(workload: str):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2511_09165_b300", "csrc", "dmas_kernels.cuh")
+    with open(src, "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    if workload == TRAFFIC_RECORD["workload"] and sha == TRAFFIC_RECORD["kernel_src_sha256_16"]:
+        return TRAFFIC_RECORD["bytes"]
+    return None
+
+
 def algorithmic_ops_per_pixel(N: int, n: int, linear: bool) -> dict:
     """FP32 operations one output pixel needs (FADD, FMUL and FFMA each count 1):
     N(n+2) channel accumulations (twice with interpolation), ~n(n+1)/2 + n
@@ -339,7 +356,8 @@ def run_ours(args, wl, scene) -> None:
                      "peak": peak, "unit": "Top/s", "frac": achieved / peak,
                      "ops_per_pixel": ops, "pixels_per_launch": px,
                      "peak_source": "148 SMs x 128 FP32 lanes x 2032 MHz (unit counts)",
-                     "traffic": None},
+                     "traffic": beam_traffic(args.workload),
+                     "algorithmic_bytes": px * 4 + 2 * N * T * 4},
         "e2e": {"value": px * world * e2e_steps / e2e_total, "unit": UNIT,
                 "h2d_bytes_per_step": N * T * 4, "d2h_bytes_per_step": M * T * 4},
         "gpu_launches": 3 * args.steps,
