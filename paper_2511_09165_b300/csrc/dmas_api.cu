@@ -70,8 +70,8 @@ using namespace dmas;
 struct dmas_plan {
     HostPlan hp;
     int device = 0;
-    int *d_gdir = nullptr, *d_gws = nullptr, *d_rel = nullptr;
-    float *d_frac = nullptr;
+    int *d_gdir = nullptr, *d_gws = nullptr, *d_rel = nullptr, *d_sel = nullptr;
+    float *d_frac = nullptr, *d_w4 = nullptr;
     unsigned *d_err = nullptr;
     void *d_scratch = nullptr;        // root channels (+ y buffer with the envelope)
     size_t chan_bytes = 0, ybuf_bytes = 0, table_bytes = 0;
@@ -118,6 +118,8 @@ void free_plan_memory(dmas_plan *p) {
     cudaFree(p->d_gws);
     cudaFree(p->d_rel);
     cudaFree(p->d_frac);
+    cudaFree(p->d_sel);
+    cudaFree(p->d_w4);
     cudaFree(p->d_err);
     cudaFree(p->d_scratch);
     cudaFree(p->d_io_frame);
@@ -128,8 +130,8 @@ void free_plan_memory(dmas_plan *p) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
     }
-    p->d_gdir = p->d_gws = p->d_rel = nullptr;
-    p->d_frac = nullptr;
+    p->d_gdir = p->d_gws = p->d_rel = p->d_sel = nullptr;
+    p->d_frac = p->d_w4 = nullptr;
     p->d_err = nullptr;
     p->d_scratch = nullptr;
     p->d_io_frame = p->d_io_image = nullptr;
@@ -149,8 +151,10 @@ size_t beam_smem_bytes(const HostPlan &hp) {
     const size_t eb = chan_elem_bytes(hp.chan_prec);
     const size_t win = ((size_t)hp.mic_chunk * hp.window * eb + 127) & ~(size_t)127;
     const size_t tabs = (size_t)hp.mic_chunk * kGroup * 4 * (hp.delay_mode ? 2 : 1);
-    if (uses_pair_kernel(hp.chan_prec, hp.order))  // pair kernel: window and shifted window
-        return 128 + 2 * win + tabs;
+    if (uses_shifted_rows(hp.chan_prec, hp.order, hp.delay_mode))  // window and shifted window
+        return lin_pair_smem_bytes(hp.mic_chunk, hp.window);
+    if (uses_pair_kernel(hp.chan_prec, hp.order))  // persistent: two staging buffers
+        return 128 + 2 * pair_stage_bytes(hp.mic_chunk, hp.window);
     return 128 + win + tabs;
 }
 
@@ -259,18 +263,28 @@ void mark(dmas_plan *p, int k, cudaStream_t s) {
     if (p->profiling) cudaEventRecord(p->ev[k], s);
 }
 
+// Per-frame scratch: root channels, y buffer (with the envelope), and a
+// 256-byte slot for the beamform launch's work counter.
+size_t scratch_bytes(const dmas_plan *p) {
+    return align256(p->chan_bytes) + align256(p->ybuf_bytes) + 256;
+}
+unsigned *work_counter(const dmas_plan *p, void *scratch) {
+    return (unsigned *)((char *)scratch + align256(p->chan_bytes) + align256(p->ybuf_bytes));
+}
+
 // ---- per-stage launch parameters of one frame ----------------------------
 RootsParams roots_params(const dmas_plan *p, const float *d_frame, void *scratch) {
     const HostPlan &hp = p->hp;
     RootsParams rp;
     rp.frame = d_frame;
     rp.chan = scratch;
+    rp.work = work_counter(p, scratch);
+    rp.shifted = uses_shifted_rows(hp.chan_prec, hp.order, hp.delay_mode) ? 1 : 0;
     rp.N = hp.N;
     rp.T = hp.T;
     rp.row = hp.row;
     rp.padl = hp.padl;
     rp.order = hp.order;
-    rp.shifted = uses_pair_kernel(hp.chan_prec, hp.order) ? 1 : 0;
     rp.inv_order = 1.0f / (float)hp.order;
     return rp;
 }
@@ -291,10 +305,13 @@ BeamParams beam_params(const dmas_plan *p, void *scratch, float *ybuf, float *d_
     const HostPlan &hp = p->hp;
     BeamParams bp;
     bp.chan = scratch;
+    bp.work = work_counter(p, scratch);
     bp.gdir = p->d_gdir;
     bp.gws = p->d_gws;
     bp.rel = p->d_rel;
     bp.frac = p->d_frac;
+    bp.sel = p->d_sel;
+    bp.w4 = p->d_w4;
     bp.y = ybuf;
     bp.cf = d_cf;
     bp.err = p->d_err;
@@ -310,6 +327,8 @@ BeamParams beam_params(const dmas_plan *p, void *scratch, float *ybuf, float *d_
     bp.cf_eps = (float)hp.cf_eps;
     bp.use_cf = (hp.flags & DMAS_F_CF) ? 1 : 0;
     bp.pairs = hp.pairs;
+    bp.stage_bytes = hp.pairs && !hp.delay_mode ? (int)pair_stage_bytes(hp.mic_chunk, hp.window)
+                                                : 0;
     return bp;
 }
 
@@ -432,6 +451,12 @@ dmas_status enqueue_batch(const std::vector<BatchEntry> &v, cudaStream_t s) {
                 smem = std::max(smem, x.plan->smem_beam);
             }
             bb.start[bb.count] = blocks;
+            if (a.pairs && !a.delay_mode) {  // one staging-buffer size: the largest
+                int sb = 0;
+                for (int k = 0; k < bb.count; ++k) sb = std::max(sb, bb.e[k].stage_bytes);
+                for (int k = 0; k < bb.count; ++k) bb.e[k].stage_bytes = sb;
+                smem = 128 + 2 * (size_t)sb;
+            }
             e = kBeamBatchLaunchers[a.order](bb, a.delay_mode, a.chan_prec, a.ng_prec, a.pairs,
                                              blocks, smem, s);
             if (e != cudaSuccess) return cuda_fail(v[cls[b0]].plan, e, "beamform batch");
@@ -520,7 +545,9 @@ dmas_status dmas_plan_create(const dmas_plan_desc *desc, dmas_plan **out) {
     if ((e = upload(&p->d_gdir, hp.gdir)) != cudaSuccess ||
         (e = upload(&p->d_gws, hp.gws)) != cudaSuccess ||
         (e = upload(&p->d_rel, hp.rel)) != cudaSuccess ||
-        (e = upload(&p->d_frac, hp.gfrac)) != cudaSuccess) {
+        (e = upload(&p->d_frac, hp.gfrac)) != cudaSuccess ||
+        (e = upload(&p->d_sel, hp.gsel)) != cudaSuccess ||
+        (e = upload(&p->d_w4, hp.gw4)) != cudaSuccess) {
         free_plan_memory(p);
         delete p;
         cudaGetLastError();
@@ -542,14 +569,16 @@ dmas_status dmas_plan_create(const dmas_plan_desc *desc, dmas_plan **out) {
             return e == cudaErrorMemoryAllocation ? DMAS_ENOMEM : DMAS_ECUDA;
         }
     }
-    p->table_bytes = (hp.gdir.size() + hp.gws.size() + hp.rel.size()) * 4 + hp.gfrac.size() * 4;
-    // the pair kernel also reads every root row shifted by one sample
+    p->table_bytes = (hp.gdir.size() + hp.gws.size() + hp.rel.size() + hp.gfrac.size() +
+                      hp.gsel.size() + hp.gw4.size()) * 4;
+    // the interpolated-delay pair kernel also reads every root row shifted by
+    // one sample
     p->chan_bytes = (size_t)hp.N * hp.row * chan_elem_bytes(hp.chan_prec) *
-                    (uses_pair_kernel(hp.chan_prec, hp.order) ? 2 : 1);
+                    (uses_shifted_rows(hp.chan_prec, hp.order, hp.delay_mode) ? 2 : 1);
     p->ybuf_bytes = hp.L > 0 ? sizeof(float) * (size_t)hp.M * hp.T : 0;
     if ((e = cudaMalloc((void **)&p->d_err, 256)) != cudaSuccess ||
         (e = cudaMemset(p->d_err, 0, 256)) != cudaSuccess ||
-        (e = cudaMalloc(&p->d_scratch, align256(p->chan_bytes) + align256(p->ybuf_bytes))) !=
+        (e = cudaMalloc(&p->d_scratch, scratch_bytes(p))) !=
             cudaSuccess) {
         free_plan_memory(p);
         delete p;
@@ -570,7 +599,7 @@ dmas_status dmas_destroy(dmas_plan *p) {
 
 size_t dmas_plan_workspace_bytes(const dmas_plan *p) {
     if (!p) return 0;
-    return align256(p->chan_bytes) + align256(p->ybuf_bytes);
+    return scratch_bytes(p);
 }
 
 dmas_status dmas_beamform(dmas_plan *p, const float *d_frame, float *d_image, float *d_y,

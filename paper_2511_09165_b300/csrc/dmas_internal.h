@@ -21,8 +21,11 @@ constexpr int kTimeTile = 256;
 constexpr int kAlign = 8;
 // Largest envelope FIR.
 constexpr int kMaxTaps = 1023;
-// Shared memory a beamform CTA may use for its staged windows (two CTAs per SM).
+// Shared memory a beamform CTA may use for its staged windows: the scalar and
+// interpolated-delay pair kernels (one buffer), and the persistent pair
+// kernel's two staging buffers together (three or more CTAs per SM).
 constexpr size_t kWindowSmemBudget = 96 * 1024;
+constexpr size_t kPairSmemBudget = 72 * 1024;
 
 // Host-side result of planning: everything the device needs, before upload.
 struct HostPlan {
@@ -42,6 +45,11 @@ struct HostPlan {
     std::vector<int32_t> gws;   // [n_groups * N] window start relative to t0
     std::vector<int32_t> rel;   // [n_groups][N][kGroup] shift - window start
     std::vector<float> gfrac;   // [n_groups][N][kGroup] interpolation weight f
+    // interpolated-delay pair kernel: byte offset, from the staged windows'
+    // base, of lane 0's first pixel pair (window as is for an even shift, the
+    // shifted window for an odd one), and the weights {1 - f, 1 - f, f, f}
+    std::vector<int32_t> gsel;  // [n_groups][N][kGroup]
+    std::vector<float> gw4;     // [n_groups][N][kGroup][4]
 
     int window = 0;      // staged samples per microphone row (multiple of kAlign)
     int mic_chunk = 0;   // microphones staged per pass
@@ -62,11 +70,36 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
 // (too many running sums for its registers) and FP16/BF16 channels run the
 // scalar beamform kernel.
 constexpr int kPairMaxOrder = 5;
+
 inline bool uses_pair_kernel(int chan_prec, int order) {
     return chan_prec == DMAS_CH_F32 && order <= kPairMaxOrder;
 }
 
 // Bytes of one element of the root channel for a dmas_chan_prec.
 inline size_t chan_elem_bytes(int chan_prec) { return chan_prec == DMAS_CH_F32 ? 4 : 2; }
+
+// Persistent pair kernel (nearest-sample delays): one of its two staging
+// buffers holds mic_chunk FP32 window rows (padded to 128 bytes), then the
+// chunk's shift table.
+inline size_t pair_window_bytes(int mic_chunk, int window) {
+    return ((size_t)mic_chunk * window * 4 + 127) & ~(size_t)127;
+}
+inline size_t pair_stage_bytes(int mic_chunk, int window) {
+    return (pair_window_bytes(mic_chunk, window) + (size_t)mic_chunk * kGroup * 4 + 127) &
+           ~(size_t)127;
+}
+// Pair kernel with interpolated delays: its root rows are also stored shifted
+// by one sample; its CTA stages mic_chunk window rows as is, the same rows
+// shifted (each block padded to 128 bytes), and per microphone and direction
+// the shift (int), the pair offset (int) and the weights (4 floats).
+inline bool uses_shifted_rows(int chan_prec, int order, int delay_mode) {
+    return uses_pair_kernel(chan_prec, order) && delay_mode == DMAS_DELAY_LINEAR;
+}
+// The CTA also keeps per-lane partial sums of the sample past its tile
+// (8 warps x up to 6 sums x 32 lanes).
+inline size_t lin_pair_smem_bytes(int mic_chunk, int window) {
+    return 128 + 2 * pair_window_bytes(mic_chunk, window) + (size_t)mic_chunk * kGroup * 24 +
+           8 * 6 * 32 * 4;
+}
 
 }  // namespace dmas

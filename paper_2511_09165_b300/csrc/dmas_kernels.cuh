@@ -62,6 +62,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t by
                  : "memory");
 }
 
+// Orders this thread's earlier shared-memory accesses before later async-proxy
+// (bulk copy) writes to shared memory.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
@@ -124,6 +130,7 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_ch<__nv_bfloat16>(float 
 struct RootsParams {
     const float *frame;  // [N][T]
     void *chan;          // [N][row] CH, then (shifted != 0) [N][row] shifted by one sample
+    unsigned *work;      // the beamform launch's work counter: set to zero
     int N, T, row, padl, order;
     int shifted;         // also write chan1[i][c] = chan0[i][c + 1] after the first block
     float inv_order;
@@ -142,6 +149,7 @@ template <typename CH>
 __device__ __forceinline__ void roots_body(const RootsParams &p, size_t first, size_t stride) {
     const size_t total = (size_t)p.N * (size_t)p.row;
     CH *chan = reinterpret_cast<CH *>(p.chan);
+    if (first == 0 && p.work) *p.work = 0u;
     for (size_t idx = first; idx < total; idx += stride) {
         const int i = (int)(idx / (size_t)p.row);
         const int c = (int)(idx - (size_t)i * p.row);
@@ -316,6 +324,8 @@ struct BeamParams {
     const int *gws;      // [n_groups][N] window start relative to t0
     const int *rel;      // [n_groups][N][8] shift relative to window start
     const float *frac;   // [n_groups][N][8] interpolation weight (LINEAR)
+    const int *sel;      // LINEAR pair kernel: [n_groups][N][8] byte offset of lane 0's pair
+    const float *w4;     // LINEAR pair kernel: [n_groups][N][8][4] {1-f, 1-f, f, f}
     float *y;            // [M][T] E_n (x CF)
     float *cf;           // [M][T] or nullptr
     unsigned *err;       // error word
@@ -323,6 +333,9 @@ struct BeamParams {
     float n_mics_f, cf_eps;
     int use_cf;
     int pairs;           // pair kernel: pixel pairs per lane (time tile 64 * pairs)
+    int stage_bytes;     // persistent pair kernel: bytes of one staging buffer (same for a
+                         // whole launch)
+    unsigned *work;      // persistent pair kernel: the launch's work counter, zero at launch
 };
 
 // Running sums per pixel: P_1..P_n, sum x, sum x^2, where for odd n
@@ -458,15 +471,18 @@ __device__ __forceinline__ void beamform_body(const BeamParams &p, unsigned bloc
 
 // ---------------------------------------------------------------------------
 // K2 (FP32 channels up to 5th order): the same gather + power sums on PAIRS of
-// neighbouring output samples (t, t+1) with packed f32x2 arithmetic: one
-// FFMA2/FMUL2/FADD2 does two FP32 operations in one issue slot, and one 8-byte
-// shared load fetches the pair of delayed roots straight into the 64-bit
-// register the packed instructions read.  A pair load must be 8-byte aligned
-// but t + shift may be odd, so the roots kernel also writes every channel row
-// shifted by one sample (chan1[x] = chan0[x + 1]); both windows are staged by
-// bulk copy, and each pair is read from the copy in which it starts at an even
-// index.
-//   lane l, pair k (0..PAIRS-1): samples t = t0 + 2l + 64k and t + 1.
+// output samples per lane with packed f32x2 arithmetic: one FFMA2/FMUL2/FADD2
+// does two FP32 operations in one issue slot.  Two kernels:
+//  * nearest-sample delays (beamform_x2_run): persistent, lane l and pair k
+//    take samples t0 + l + 64k and t0 + l + 32 + 64k, each half loaded by a
+//    conflict-free 32-lane shared load;
+//  * interpolated delays (beamform_x2_lin_body): one work item per CTA, lane l
+//    and pair k take the neighbours t = t0 + 2l + 64k and t + 1, fetched by
+//    one 8-byte shared load straight into the 64-bit register the packed
+//    instructions read.  That load must be 8-byte aligned but t + shift may be
+//    odd, so the roots kernel also writes every channel row shifted by one
+//    sample (chan1[x] = chan0[x + 1]); both windows are staged, and each pair
+//    is read from the copy in which it starts at an even index.
 // ---------------------------------------------------------------------------
 typedef unsigned long long f32x2_t;
 
@@ -515,11 +531,60 @@ __device__ __forceinline__ void accumulate2(f32x2_t (&a)[SumLayout<ORDER>::kNum]
     a[NP + 1] = f2_fma(wx, x, a[NP + 1]);
 }
 
-// PAIRS pixel pairs per lane: time tile 64 * PAIRS.  PAIRS = 2 keeps few
-// enough registers and shared memory for four CTAs per SM, PAIRS = 4 two.
-template <int ORDER, bool LINEAR, int NGP, int PAIRS>
-__device__ __forceinline__ void beamform_x2_body(const BeamParams &p, unsigned block) {
+// Interpolated delays without recomputing powers.  Pixel t takes
+// (1 - f) p(x) + f p(x + 1) per channel, with x = t + shift; pixel t + 1 takes
+// x + 1 and x + 2, so every sample's powers are needed by two pixels.  With
+//   U[t] = sum_i (1 - f_i) p(x_i(t)),   V[t] = sum_i f_i p(x_i(t)),
+// both summed over the SAME samples, the interpolated sum is U[t] + V[t + 1]:
+// each staged sample's powers are formed once and accumulated twice.
+template <int ORDER>
+__device__ __forceinline__ void accumulate2_split(f32x2_t (&u)[SumLayout<ORDER>::kNum],
+                                                  f32x2_t (&v)[SumLayout<ORDER>::kNum],
+                                                  f32x2_t s, f32x2_t w0, f32x2_t w1) {
+    constexpr int NP = SumLayout<ORDER>::kNumP;
+    f32x2_t pw = s;
+    if constexpr (NP >= 1) {
+        u[0] = f2_fma(w0, s, u[0]);
+        v[0] = f2_fma(w1, s, v[0]);
+    }
+#pragma unroll
+    for (int q = 2; q <= ORDER; ++q) {
+        pw = f2_mul(pw, s);
+        if (q <= NP) {
+            u[q - 1] = f2_fma(w0, pw, u[q - 1]);
+            v[q - 1] = f2_fma(w1, pw, v[q - 1]);
+        }
+    }
+    const f32x2_t x = (ORDER & 1) ? pw : f2_copysign(pw, s);
+    u[NP] = f2_fma(w0, x, u[NP]);
+    v[NP] = f2_fma(w1, x, v[NP]);
+    const f32x2_t xx = f2_mul(x, x);
+    u[NP + 1] = f2_fma(w0, xx, u[NP + 1]);
+    v[NP + 1] = f2_fma(w1, xx, v[NP + 1]);
+}
+
+// The same for one sample in scalar arithmetic, f-weighted part only.
+template <int ORDER>
+__device__ __forceinline__ void accumulate_v(float (&v)[SumLayout<ORDER>::kNum], float s,
+                                             float w1) {
+    constexpr int NP = SumLayout<ORDER>::kNumP;
+    float pw = s;
+    if constexpr (NP >= 1) v[0] = fmaf(w1, s, v[0]);
+#pragma unroll
+    for (int q = 2; q <= ORDER; ++q) {
+        pw *= s;
+        if (q <= NP) v[q - 1] = fmaf(w1, pw, v[q - 1]);
+    }
+    const float x = (ORDER & 1) ? pw : copysignf(pw, s);
+    v[NP] = fmaf(w1, x, v[NP]);
+    v[NP + 1] = fmaf(w1, x * x, v[NP + 1]);
+}
+
+// Interpolated delays, one work item (time tile, direction group) per CTA.
+template <int ORDER, int NGP, int PAIRS>
+__device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsigned block) {
     constexpr int kPairs = PAIRS;
+    constexpr int kTile = 64 * kPairs;
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr int NA = SumLayout<ORDER>::kNum;
     constexpr int NP = SumLayout<ORDER>::kNumP;
@@ -530,11 +595,14 @@ __device__ __forceinline__ void beamform_x2_body(const BeamParams &p, unsigned b
     float *copy0 = reinterpret_cast<float *>(smem + 128);
     float *copy1 = reinterpret_cast<float *>(smem + 128 + win_bytes);
     int *s_rel = reinterpret_cast<int *>(smem + 128 + 2 * win_bytes);
-    float *s_frac = reinterpret_cast<float *>(s_rel + NC * 8);
+    int *s_sel = s_rel + NC * 8;
+    float *s_w4 = reinterpret_cast<float *>(s_sel + NC * 8);
+    // per-lane partial sums of the sample past the tile: [warp][q][lane]
+    float *s_vext = s_w4 + NC * 32 + ((threadIdx.x >> 5) * NA * 32 + (threadIdx.x & 31));
 
     const int tile = (int)(block / (unsigned)p.n_groups);
     const int g = (int)(block - (unsigned)tile * (unsigned)p.n_groups);
-    const int t0 = tile * (64 * kPairs);
+    const int t0 = tile * kTile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -543,11 +611,15 @@ __device__ __forceinline__ void beamform_x2_body(const BeamParams &p, unsigned b
     }
     __syncthreads();
 
-    f32x2_t acc[kPairs][NA];
+    // U (acc) and V (vac) of the lane's pairs; s_vext: V at t0 + 64 PAIRS, the
+    // sample past the tile, one microphone per lane
+    f32x2_t acc[kPairs][NA], vac[kPairs][NA];
 #pragma unroll
-    for (int k = 0; k < kPairs; ++k)
+    for (int q = 0; q < NA; ++q) {
 #pragma unroll
-        for (int q = 0; q < NA; ++q) acc[k][q] = 0ull;
+        for (int k = 0; k < kPairs; ++k) acc[k][q] = vac[k][q] = 0ull;
+        s_vext[q * 32] = 0.0f;
+    }
 
     const float *chan0 = reinterpret_cast<const float *>(p.chan);
     const float *chan1 = chan0 + (size_t)p.N * p.row;
@@ -558,8 +630,7 @@ __device__ __forceinline__ void beamform_x2_body(const BeamParams &p, unsigned b
         if (warp == 0) {
             const uint32_t row_bytes = (uint32_t)(WS * 4);
             const uint32_t tab_bytes = (uint32_t)(nc * 8 * 4);
-            if (lane == 0)
-                mbar_arrive_expect_tx(bar, 2 * nc * row_bytes + tab_bytes * (LINEAR ? 2u : 1u));
+            if (lane == 0) mbar_arrive_expect_tx(bar, 2 * nc * row_bytes + 6 * tab_bytes);
             __syncwarp();
             const int *gws = p.gws + (size_t)g * p.N;
             for (int il = lane; il < nc; il += 32) {
@@ -569,8 +640,10 @@ __device__ __forceinline__ void beamform_x2_body(const BeamParams &p, unsigned b
                 bulk_g2s(copy1 + il * WS, chan1 + o, row_bytes, bar);
             }
             if (lane == 0) {
-                bulk_g2s(s_rel, p.rel + ((size_t)g * p.N + c0) * 8, tab_bytes, bar);
-                if (LINEAR) bulk_g2s(s_frac, p.frac + ((size_t)g * p.N + c0) * 8, tab_bytes, bar);
+                const size_t to = ((size_t)g * p.N + c0) * 8;
+                bulk_g2s(s_rel, p.rel + to, tab_bytes, bar);
+                bulk_g2s(s_sel, p.sel + to, tab_bytes, bar);
+                bulk_g2s(s_w4, p.w4 + to * 4, 4 * tab_bytes, bar);
             }
         }
         const bool ok = mbar_wait_bounded(bar, parity);
@@ -583,40 +656,64 @@ __device__ __forceinline__ void beamform_x2_body(const BeamParams &p, unsigned b
         }
         parity ^= 1u;
 
-#pragma unroll 2
+        // (x, x+1), x = off + 2l + 64k: at x in copy 0 (even off) or at x - 1
+        // in copy 1 (odd off); s_sel holds that byte offset for lane 0, k = 0
+        const unsigned char *base = reinterpret_cast<const unsigned char *>(copy0) + 8 * lane;
+        const ulonglong2 *wq = reinterpret_cast<const ulonglong2 *>(s_w4) + warp;
+#pragma unroll 4
         for (int il = 0; il < nc; ++il) {
-            const int off = s_rel[il * 8 + warp];
-            const float *r0 = copy0 + il * WS;
-            const float *r1 = copy1 + il * WS;
-            const bool odd = (off & 1) != 0;
-            // (x, x+1), x = off + 2l + 64k: at x in copy 0 (even off) or at
-            // x - 1 in copy 1 (odd off)
-            const float *lp = (odd ? r1 + off - 1 : r0 + off) + 2 * lane;
-            if constexpr (LINEAR) {
-                // (x+1, x+2): at x in copy 1 (even off) or at x + 1 in copy 0 (odd off)
-                const float *rp = (odd ? r0 + off + 1 : r1 + off) + 2 * lane;
-                const float f = s_frac[il * 8 + warp];
-                const f32x2_t w0 = f2_pack(1.0f - f, 1.0f - f);
-                const f32x2_t w1 = f2_pack(f, f);
+            const f32x2_t *lp = reinterpret_cast<const f32x2_t *>(base + s_sel[il * 8 + warp]);
+            const ulonglong2 w = wq[il * 8];  // {1-f, 1-f}, {f, f}
 #pragma unroll
-                for (int k = 0; k < kPairs; ++k) {
-                    const f32x2_t a = *reinterpret_cast<const f32x2_t *>(lp + 64 * k);
-                    const f32x2_t b = *reinterpret_cast<const f32x2_t *>(rp + 64 * k);
-                    accumulate2<ORDER, true>(acc[k], a, w0);
-                    accumulate2<ORDER, true>(acc[k], b, w1);
-                }
-            } else {
+            for (int k = 0; k < kPairs; ++k)
+                accumulate2_split<ORDER>(acc[k], vac[k], lp[32 * k], w.x, w.y);
+        }
+        // the sample past the tile lies inside the window (its span covers the
+        // last pixel's x + 1)
+        if (lane < nc) {
+            float ve[NA];
 #pragma unroll
-                for (int k = 0; k < kPairs; ++k) {
-                    const f32x2_t a = *reinterpret_cast<const f32x2_t *>(lp + 64 * k);
-                    accumulate2<ORDER, false>(acc[k], a, 0ull);
-                }
-            }
+            for (int q = 0; q < NA; ++q) ve[q] = s_vext[q * 32];
+            for (int il = lane; il < nc; il += 32)
+                accumulate_v<ORDER>(ve, copy0[il * WS + s_rel[il * 8 + warp] + kTile],
+                                    s_w4[(il * 8 + warp) * 4 + 2]);
+#pragma unroll
+            for (int q = 0; q < NA; ++q) s_vext[q * 32] = ve[q];
         }
     }
 
     const int dir = p.gdir[(size_t)g * 8 + warp];
     if (dir < 0) return;
+    // sum[t] = U[t] + V[t + 1].  For the pair (t, t+1): V[t+1] is the pair's
+    // own second half; V[t+2] the next lane's first half (lane 31: lane 0's of
+    // the next pair, or vext after the last).
+    float vext[NA];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+        vext[q] = s_vext[q * 32];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vext[q] += __shfl_xor_sync(0xffffffffu, vext[q], o);
+    }
+    float nxt[kPairs][NA];
+#pragma unroll
+    for (int k = 0; k < kPairs; ++k)
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+            float lo, hi;
+            f2_unpack(vac[k][q], lo, hi);
+            nxt[k][q] = __shfl_sync(0xffffffffu, lo, (lane + 1) & 31);
+        }
+#pragma unroll
+    for (int k = 0; k < kPairs; ++k)
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+            float ulo, uhi, vlo, vhi;
+            f2_unpack(acc[k][q], ulo, uhi);
+            f2_unpack(vac[k][q], vlo, vhi);
+            const float vn =
+                lane < 31 ? nxt[k][q] : (k + 1 < kPairs ? nxt[(k + 1) % kPairs][q] : vext[q]);
+            acc[k][q] = f2_pack(ulo + vhi, uhi + vn);
+        }
     float *yrow = p.y + (size_t)dir * p.T;
     float *cfrow = p.cf ? p.cf + (size_t)dir * p.T : nullptr;
 #pragma unroll
@@ -637,6 +734,225 @@ __device__ __forceinline__ void beamform_x2_body(const BeamParams &p, unsigned b
             yrow[t] = p.use_cf ? E * cf : E;
             if (cfrow) cfrow[t] = cf;
         }
+    }
+}
+
+// Nearest-sample delays.  PAIRS pixel pairs per lane: time tile 64 * PAIRS.
+// The kernel is persistent: a CTA starts with work item (tile, direction
+// group) blockIdx.x and then takes items from a counter shared by the launch,
+// one stage per (item, microphone chunk), through two staging buffers.  Its
+// warps run free of each other: a warp waits only for the bulk copy of the
+// stage it is about to compute, and the last warp to finish with a buffer
+// (counted in shared memory) stages the stage after next into it.  Measured
+// on B300 against a static item stride and against CTA-wide barriers per
+// stage, both of which left SMs idle at the end or between stages.
+//
+// Src supplies the items: total(), entry(u) (batch entry of item u), par(e)
+// (its parameters) and first(e) (its first item).
+struct OneFrame {
+    const BeamParams &p;
+    __device__ unsigned total() const { return (unsigned)p.n_groups * (unsigned)p.n_tiles; }
+    __device__ int entry(unsigned) const { return 0; }
+    __device__ const BeamParams &par(int) const { return p; }
+    __device__ unsigned first(int) const { return 0; }
+};
+
+__device__ __forceinline__ int stage_window_bytes(const BeamParams &p) {
+    return (p.mic_chunk * p.window * 4 + 127) & ~127;
+}
+
+template <int ORDER, int NGP, int PAIRS, class Src>
+__device__ __forceinline__ void beamform_x2_run(const Src &src) {
+    constexpr int kPairs = PAIRS;
+    constexpr int kTile = 64 * kPairs;
+    constexpr int kWarps = kThreads / 32;
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int NA = SumLayout<ORDER>::kNum;
+    constexpr int NP = SumLayout<ORDER>::kNumP;
+    // smem[0, 128): per buffer b: full barrier, finished-warp count, the item
+    // and first microphone of the stage it holds, the last stage staged into
+    // it; the last staged (item, microphone); abort flag
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    int *done_cnt = reinterpret_cast<int *>(smem + 16);
+    unsigned *st_item = reinterpret_cast<unsigned *>(smem + 24);
+    int *st_c0 = reinterpret_cast<int *>(smem + 32);
+    int *last_staged = reinterpret_cast<int *>(smem + 40);
+    unsigned *cur_item = reinterpret_cast<unsigned *>(smem + 48);
+    int *cur_c0 = reinterpret_cast<int *>(smem + 52);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 56);
+    const unsigned total = src.total();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (blockIdx.x >= total) return;
+    // every entry of a launch carries the same stage_bytes (the largest) and
+    // the launch's work counter (zeroed by the roots kernel before)
+    const unsigned stage_bytes = (unsigned)src.par(0).stage_bytes;
+    unsigned *work = src.par(0).work;
+
+    // Stage the next stage into buffer bf: the next microphone chunk of the
+    // last staged item, else a new item (the CTA's own first, then from the
+    // launch's counter); with no work left, complete the buffer's phase
+    // empty.  Called by a whole warp, one at a time per CTA.
+    auto stage_next = [&](int bf, int stage, bool first) {
+        unsigned uu;
+        int cc;
+        if (first) {
+            uu = blockIdx.x;
+            cc = 0;
+        } else {
+            uu = *cur_item;
+            cc = *cur_c0;
+            const BeamParams &q = src.par(src.entry(uu));
+            cc += q.mic_chunk;
+            if (cc >= q.N) {
+                cc = 0;
+                unsigned nxt = 0;
+                if (lane == 0) nxt = gridDim.x + atomicAdd(work, 1u);
+                uu = __shfl_sync(0xffffffffu, nxt, 0);
+            }
+        }
+        if (uu >= total || *abort_flag) {
+            if (lane == 0) {
+                st_item[bf] = total;
+                mbar_arrive(&bar[bf]);
+            }
+            return;
+        }
+        const int e = src.entry(uu);
+        const BeamParams &q = src.par(e);
+        const unsigned loc = uu - src.first(e);
+        const int tile = (int)(loc / (unsigned)q.n_groups);
+        const int g = (int)(loc - (unsigned)tile * (unsigned)q.n_groups);
+        const int nc = min(q.mic_chunk, q.N - cc);
+        unsigned char *buf = smem + 128 + (size_t)bf * stage_bytes;
+        float *w = reinterpret_cast<float *>(buf);
+        int *rel = reinterpret_cast<int *>(buf + stage_window_bytes(q));
+        const uint32_t row_bytes = (uint32_t)(q.window * 4);
+        const uint32_t tab_bytes = (uint32_t)(nc * 8 * 4);
+        if (lane == 0) {
+            *cur_item = uu;
+            *cur_c0 = cc;
+            st_item[bf] = uu;
+            st_c0[bf] = cc;
+            last_staged[bf] = stage;
+            mbar_arrive_expect_tx(&bar[bf], nc * row_bytes + tab_bytes);
+        }
+        __syncwarp();
+        const float *chan = reinterpret_cast<const float *>(q.chan);
+        const int *gws = q.gws + (size_t)g * q.N;
+        const int t0 = tile * kTile;
+        for (int il = lane; il < nc; il += 32) {
+            const int i = cc + il;
+            bulk_g2s(w + il * q.window, chan + (size_t)i * q.row + q.padl + t0 + gws[i],
+                     row_bytes, &bar[bf]);
+        }
+        if (lane == 0) bulk_g2s(rel, q.rel + ((size_t)g * q.N + cc) * 8, tab_bytes, &bar[bf]);
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        done_cnt[0] = done_cnt[1] = 0;
+        last_staged[0] = last_staged[1] = -1;
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == 0) {  // the first two stages
+        stage_next(0, 0, true);
+        __syncwarp();
+        stage_next(1, 1, false);
+    }
+
+    f32x2_t acc[kPairs][NA];
+
+    for (int stage = 0;; ++stage) {
+        const int bf = stage & 1;
+        const bool ok = __all_sync(0xffffffffu,
+                                   mbar_wait_bounded(&bar[bf], (uint32_t)(stage >> 1) & 1u));
+        if (!ok) {
+            if (lane == 0) {
+                atomicOr(src.par(0).err, kErrTimeout);
+                *abort_flag = 1;
+            }
+            break;
+        }
+        const unsigned u = st_item[bf];
+        if (u >= total) break;  // no work left
+        const int c0 = st_c0[bf];
+        const int e = src.entry(u);
+        const BeamParams &p = src.par(e);
+        const unsigned loc = u - src.first(e);
+        const int tile = (int)(loc / (unsigned)p.n_groups);
+        const int g = (int)(loc - (unsigned)tile * (unsigned)p.n_groups);
+        const int t0 = tile * kTile;
+        const int WS = p.window;
+        const int nc = min(p.mic_chunk, p.N - c0);
+        const bool last_chunk = c0 + p.mic_chunk >= p.N;
+        if (c0 == 0) {
+#pragma unroll
+            for (int k = 0; k < kPairs; ++k)
+#pragma unroll
+                for (int q = 0; q < NA; ++q) acc[k][q] = 0ull;
+        }
+
+        const unsigned char *buf = smem + 128 + (size_t)bf * stage_bytes;
+        const float *w = reinterpret_cast<const float *>(buf);
+        const int *s_rel = reinterpret_cast<const int *>(buf + stage_window_bytes(p));
+#pragma unroll 2
+        for (int il = 0; il < nc; ++il) {
+            const float *r = w + il * WS + s_rel[il * 8 + warp] + lane;
+#pragma unroll
+            for (int k = 0; k < kPairs; ++k)
+                accumulate2<ORDER, false>(acc[k], f2_pack(r[64 * k], r[64 * k + 32]), 0ull);
+        }
+
+        const int dir = last_chunk ? p.gdir[(size_t)g * 8 + warp] : -1;
+        if (dir >= 0) {
+            float *yrow = p.y + (size_t)dir * p.T;
+            float *cfrow = p.cf ? p.cf + (size_t)dir * p.T : nullptr;
+#pragma unroll
+            for (int k = 0; k < kPairs; ++k) {
+                float P[2][ORDER + 1], A[2], B[2];
+                P[0][0] = P[1][0] = 0.0f;
+#pragma unroll
+                for (int q = 1; q <= NP; ++q) f2_unpack(acc[k][q - 1], P[0][q], P[1][q]);
+                f2_unpack(acc[k][NP], A[0], A[1]);
+                f2_unpack(acc[k][NP + 1], B[0], B[1]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int t = t0 + lane + 32 * h + 64 * k;
+                    if (t >= p.T) continue;
+                    if constexpr (SumLayout<ORDER>::kPnIsA) P[h][ORDER] = A[h];
+                    const float E = esym_from_power_sums<ORDER, NGP>(P[h]);
+                    const float cf = (A[h] * A[h]) / fmaf(p.n_mics_f, B[h], p.cf_eps);
+                    yrow[t] = p.use_cf ? E * cf : E;
+                    if (cfrow) cfrow[t] = cf;
+                }
+            }
+        }
+        // hand the buffer back; the last warp out stages the stage after next
+        __syncwarp();
+        int before = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            before = atomicAdd(&done_cnt[bf], 1);
+            __threadfence_block();
+        }
+        __syncwarp();
+        before = __shfl_sync(0xffffffffu, before, 0);
+        if (before == kWarps - 1) {
+            if (lane == 0) done_cnt[bf] = 0;
+            __threadfence_block();
+            fence_proxy_async_smem();  // the warps' reads before the copy's writes
+            stage_next(bf, stage + 2, false);
+        }
+        if (*abort_flag) break;
+    }
+    // After an abort, let the copies in flight land before the CTA exits.
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) {
+        for (int b = 0; b < 2; ++b)
+            if (last_staged[b] >= 0) mbar_wait_bounded(&bar[b], (uint32_t)(last_staged[b] >> 1) & 1u);
     }
 }
 
@@ -662,17 +978,32 @@ __global__ void __launch_bounds__(kThreads, 2)
     beamform_body<ORDER, LINEAR, CH, NGP>(b.e[k], blockIdx.x - b.start[k]);
 }
 
+struct ManyFrames {
+    const BeamBatch &b;
+    __device__ unsigned total() const { return b.start[b.count]; }
+    __device__ int entry(unsigned u) const { return batch_entry(b.start, b.count, u); }
+    __device__ const BeamParams &par(int e) const { return b.e[e]; }
+    __device__ unsigned first(int e) const { return b.start[e]; }
+};
+
+// Four CTAs per SM for nearest-sample delays, three for interpolated ones
+// (twice the accumulators).
 template <int ORDER, bool LINEAR, int NGP, int PAIRS>
-__global__ void __launch_bounds__(kThreads, PAIRS == 2 ? 4 : 2)
+__global__ void __launch_bounds__(kThreads, LINEAR ? 3 : 4)
     beamform_x2_kernel(const __grid_constant__ BeamParams p) {
-    beamform_x2_body<ORDER, LINEAR, NGP, PAIRS>(p, blockIdx.x);
+    if constexpr (LINEAR) beamform_x2_lin_body<ORDER, NGP, PAIRS>(p, blockIdx.x);
+    else beamform_x2_run<ORDER, NGP, PAIRS>(OneFrame{p});
 }
 
 template <int ORDER, bool LINEAR, int NGP, int PAIRS>
-__global__ void __launch_bounds__(kThreads, PAIRS == 2 ? 4 : 2)
+__global__ void __launch_bounds__(kThreads, LINEAR ? 3 : 4)
     beamform_x2_batch_kernel(const __grid_constant__ BeamBatch b) {
-    const int k = batch_entry(b.start, b.count, blockIdx.x);
-    beamform_x2_body<ORDER, LINEAR, NGP, PAIRS>(b.e[k], blockIdx.x - b.start[k]);
+    if constexpr (LINEAR) {
+        const int k = batch_entry(b.start, b.count, blockIdx.x);
+        beamform_x2_lin_body<ORDER, NGP, PAIRS>(b.e[k], blockIdx.x - b.start[k]);
+    } else {
+        beamform_x2_run<ORDER, NGP, PAIRS>(ManyFrames{b});
+    }
 }
 
 }  // namespace dmas

@@ -28,22 +28,59 @@ cudaError_t launch_kernel(K kern, std::once_flag &once, cudaError_t &attr_err, c
     return cudaGetLastError();
 }
 
-// FP32 channels up to kPairMaxOrder: the pair kernel (p.pairs pairs per lane);
+// Persistent launch: `items` work items over at most as many CTAs as fit on
+// the device at once (occupancy for this kernel and shared-memory size, cached
+// per device).
+template <typename K, typename P>
+cudaError_t launch_persistent(K kern, std::once_flag &once, cudaError_t &attr_err, const P &p,
+                              unsigned items, size_t smem, cudaStream_t s) {
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kBeamSmemOptIn);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    struct Slot { int dev = -1; size_t smem = 0; unsigned ctas = 0; };
+    static std::mutex mu;
+    static Slot cache[4];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    unsigned ctas = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const Slot &c : cache)
+            if (c.dev == dev && c.smem == smem) ctas = c.ctas;
+        if (ctas == 0) {
+            int per_sm = 0, sms = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads,
+                                                                   smem)) != cudaSuccess ||
+                (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
+                    cudaSuccess)
+                return e;
+            ctas = (unsigned)std::max(1, per_sm) * (unsigned)sms;
+            std::rotate(cache, cache + 3, cache + 4);
+            cache[0] = Slot{dev, smem, ctas};
+        }
+    }
+    kern<<<std::min(items, ctas), kThreads, smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+// FP32 channels up to kPairMaxOrder: the pair kernel (2 pairs per lane;
+// persistent for nearest-sample delays, `grid` then counting its work items);
 // otherwise the scalar one (the same choice as uses_pair_kernel on the host).
 template <int ORDER, bool LINEAR, typename CH, int NGP>
 cudaError_t launch_beam_variant(const BeamParams &p, unsigned grid, size_t smem,
                                 cudaStream_t s) {
     if constexpr (std::is_same<CH, float>::value && ORDER <= kPairMaxOrder) {
-        if (p.pairs == 4) {
-            static std::once_flag once;
-            static cudaError_t err = cudaSuccess;
-            return launch_kernel(beamform_x2_kernel<ORDER, LINEAR, NGP, 4>, once, err, p, grid,
-                                 smem, s);
-        }
         static std::once_flag once;
         static cudaError_t err = cudaSuccess;
-        return launch_kernel(beamform_x2_kernel<ORDER, LINEAR, NGP, 2>, once, err, p, grid, smem,
-                             s);
+        if constexpr (LINEAR)
+            return launch_kernel(beamform_x2_kernel<ORDER, LINEAR, NGP, 2>, once, err, p, grid,
+                                 smem, s);
+        else
+            return launch_persistent(beamform_x2_kernel<ORDER, LINEAR, NGP, 2>, once, err, p,
+                                     grid, smem, s);
     } else {
         static std::once_flag once;
         static cudaError_t err = cudaSuccess;
@@ -87,16 +124,14 @@ template <int ORDER, bool LINEAR, typename CH, int NGP>
 cudaError_t launch_beam_batch_variant(const BeamBatch &b, int pairs, unsigned grid, size_t smem,
                                       cudaStream_t s) {
     if constexpr (std::is_same<CH, float>::value && ORDER <= kPairMaxOrder) {
-        if (pairs == 4) {
-            static std::once_flag once;
-            static cudaError_t err = cudaSuccess;
-            return launch_kernel(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, 4>, once, err, b,
-                                 grid, smem, s);
-        }
         static std::once_flag once;
         static cudaError_t err = cudaSuccess;
-        return launch_kernel(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, 2>, once, err, b, grid,
-                             smem, s);
+        if constexpr (LINEAR)
+            return launch_kernel(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, 2>, once, err, b,
+                                 grid, smem, s);
+        else
+            return launch_persistent(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, 2>, once, err,
+                                     b, grid, smem, s);
     } else {
         static std::once_flag once;
         static cudaError_t err = cudaSuccess;

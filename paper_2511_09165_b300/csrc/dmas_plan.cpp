@@ -276,25 +276,51 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
     }
     const size_t eb = chan_elem_bytes(d.chan_prec);
     if (uses_pair_kernel(d.chan_prec, d.order)) {
-        // Measured on B300 (hemisphere scene, n = 5): nearest-sample delays run
-        // best with 2 pairs per lane (128-sample tiles, four CTAs per SM hide
-        // the staging), interpolated delays, with twice the arithmetic per
-        // staged sample, with 4 pairs (256-sample tiles, less halo).
-        hp.pairs = lin ? 4 : 2;
+        hp.pairs = 2;  // pixel pairs per lane (time tile 64 x pairs)
         hp.tile = 64 * hp.pairs;
     } else {
         hp.pairs = 0;
         hp.tile = kTimeTile;
     }
     long long window = round_up(hp.tile + spread, kAlign);
-    // The pair kernel stages each window twice (as is and shifted by one sample).
-    const size_t copies = uses_pair_kernel(d.chan_prec, d.order) ? 2 : 1;
-    const size_t budget = kWindowSmemBudget;
-    const size_t per_mic = copies * (size_t)window * eb + (size_t)kGroup * 4 * (lin ? 2 : 1);
+    // The persistent pair kernel (nearest-sample delays) double-buffers its
+    // staged windows; the interpolated-delay pair kernel stages each window
+    // as is and shifted by one sample.
+    const bool pair = uses_pair_kernel(d.chan_prec, d.order);
+    const bool persistent = pair && !lin;
+    const size_t budget = persistent ? kPairSmemBudget - 2 * 256
+                                     : kWindowSmemBudget - (pair ? 8 * 6 * 32 * 4 : 0);
+    const size_t tab = (size_t)kGroup * 4 * (lin ? 2 : 1);
+    const size_t per_mic = persistent ? 2 * ((size_t)window * eb + tab)
+                                      : (pair ? 2 * (size_t)window * eb + (size_t)kGroup * 24
+                                              : (size_t)window * eb + tab);
     if (per_mic > budget)
         return fail("a direction group's delay spread does not fit in shared memory");
     hp.window = (int)window;
     hp.mic_chunk = (int)std::min<size_t>((size_t)N, budget / per_mic);
+    if (persistent) {  // balanced chunks
+        const int n_chunks = (N + hp.mic_chunk - 1) / hp.mic_chunk;
+        hp.mic_chunk = (N + n_chunks - 1) / n_chunks;
+    }
+    if (pair && lin) {
+        const size_t wb = pair_window_bytes(hp.mic_chunk, hp.window);
+        hp.gsel.assign(hp.rel.size(), 0);
+        hp.gw4.assign(hp.rel.size() * 4, 0.0f);
+        for (int g = 0; g < G; ++g)
+            for (int i = 0; i < N; ++i)
+                for (int s = 0; s < kGroup; ++s) {
+                    const size_t o = ((size_t)g * N + i) * kGroup + s;
+                    const int off = hp.rel[o];
+                    const size_t row = (size_t)(i % hp.mic_chunk) * hp.window * 4;
+                    hp.gsel[o] = (int32_t)(row + ((off & 1) ? wb + (size_t)(off - 1) * 4
+                                                            : (size_t)off * 4));
+                    const float f = hp.gfrac[o];
+                    hp.gw4[o * 4 + 0] = 1.0f - f;
+                    hp.gw4[o * 4 + 1] = 1.0f - f;
+                    hp.gw4[o * 4 + 2] = f;
+                    hp.gw4[o * 4 + 3] = f;
+                }
+    }
     hp.n_tiles = (T + hp.tile - 1) / hp.tile;
     hp.padl = (int)round_up(std::max(0, -ws_min), kAlign);
     long long read_end = (long long)hp.padl + (long long)(hp.n_tiles - 1) * hp.tile +
