@@ -75,8 +75,8 @@ WORKLOADS = {
 # DRAM bytes (read + write) of one beamform launch on the default workload, from
 # one ncu capture (profiles/beamform_x2_hemi3d_n5.md), valid while the kernel
 # source is the one that was measured.
-TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "kernel_src_sha256_16": "6055555d481262c1",
-                  "bytes": 4868096 + 74967040}
+TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "kernel_src_sha256_16": "ae7dfaae35d605d5",
+                  "bytes": 5886464 + 75518720}
 
 
 def beam_traffic(workload: str):
