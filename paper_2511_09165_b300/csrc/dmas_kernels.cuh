@@ -740,7 +740,10 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
 // Nearest-sample delays.  PAIRS pixel pairs per lane: time tile 64 * PAIRS.
 // The kernel is persistent: a CTA starts with work item (tile, direction
 // group) blockIdx.x and then takes items from a counter shared by the launch,
-// one stage per (item, microphone chunk), through two staging buffers.  Its
+// at most kPersistItems in all (so its CTAs retire every few tens of
+// microseconds and kernels on higher-priority streams get SMs; the grid has
+// ceil(items / kPersistItems) CTAs), one stage per (item, microphone chunk),
+// through two staging buffers.  Its
 // warps run free of each other: a warp waits only for the bulk copy of the
 // stage it is about to compute, and the last warp to finish with a buffer
 // (counted in shared memory) stages the stage after next into it.  Measured
@@ -749,6 +752,8 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
 //
 // Src supplies the items: total(), entry(u) (batch entry of item u), par(e)
 // (its parameters) and first(e) (its first item).
+constexpr int kPersistItems = 8;  // work items per CTA of the persistent kernel
+
 struct OneFrame {
     const BeamParams &p;
     __device__ unsigned total() const { return (unsigned)p.n_groups * (unsigned)p.n_tiles; }
@@ -780,6 +785,7 @@ __device__ __forceinline__ void beamform_x2_run(const Src &src) {
     unsigned *cur_item = reinterpret_cast<unsigned *>(smem + 48);
     int *cur_c0 = reinterpret_cast<int *>(smem + 52);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 56);
+    int *n_items = reinterpret_cast<int *>(smem + 60);
     const unsigned total = src.total();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (blockIdx.x >= total) return;
@@ -805,8 +811,11 @@ __device__ __forceinline__ void beamform_x2_run(const Src &src) {
             cc += q.mic_chunk;
             if (cc >= q.N) {
                 cc = 0;
-                unsigned nxt = 0;
-                if (lane == 0) nxt = gridDim.x + atomicAdd(work, 1u);
+                unsigned nxt = total;  // this CTA has had its share
+                if (lane == 0 && *n_items < kPersistItems) {
+                    nxt = gridDim.x + atomicAdd(work, 1u);
+                    ++*n_items;
+                }
                 uu = __shfl_sync(0xffffffffu, nxt, 0);
             }
         }
@@ -854,6 +863,7 @@ __device__ __forceinline__ void beamform_x2_run(const Src &src) {
         done_cnt[0] = done_cnt[1] = 0;
         last_staged[0] = last_staged[1] = -1;
         *abort_flag = 0;
+        *n_items = 1;
         fence_mbar_init();
     }
     __syncthreads();

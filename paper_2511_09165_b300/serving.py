@@ -94,12 +94,15 @@ class Request:
 
 class Server:
     """fast_cost: frames with cost <= fast_cost use the fast lane (default:
-    about 1 ms of GPU work, 1.3e9 mic x direction x samples).  Set streams
-    counts per lane; `streams` sets both."""
+    about 0.5 ms of GPU work, 1.3e9 mic x direction x samples).  `streams`
+    is the fast lane's stream count, `bulk_streams` the bulk lane's (None:
+    the same); `bulk_batch` frames per bulk batch.  Defaults measured on B300
+    with the 16-sensor mix at 200 frames/s: one big frame per batch on three
+    low-priority streams kept the small frames' p99 lowest."""
 
     def __init__(self, sensors, device=None, budget_bytes: int = 32 << 30,
                  max_batch: int = 64, streams: int = 2, copy_back: bool = False,
-                 fast_cost: float = 1.3e9, bulk_batch: int = 2, bulk_streams: int | None = None):
+                 fast_cost: float = 1.3e9, bulk_batch: int = 1, bulk_streams: int | None = 3):
         import torch
         self.torch = torch
         self.sensors = list(sensors)
