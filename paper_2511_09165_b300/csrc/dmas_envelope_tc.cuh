@@ -19,17 +19,17 @@
 // the _hi parts rounded to TF32; each k-step issues A_hi.B_hi + A_hi.B_lo +
 // A_lo.B_hi (the dropped A_lo.B_lo term is ~2^-22 relative).
 //
-// CTA: 256 threads, two per direction row of the tile, persistent over tiles
-// (and over the frames of a batch).  Per k-block of 64 samples: each thread
-// issues all eight of its 16-byte loads before using any (enough bytes in
-// flight to cover the memory latency), takes |y|, splits it and stores
-// A_hi/A_lo into one of two shared-memory buffers
-// in the canonical K-major no-swizzle layout (core matrix = 8 rows x 16 bytes);
-// thread 0 issues 8 k-steps x 4 phases x 3 MMAs and commits them to that
-// buffer's mbarrier, which the threads wait on (bounded) before refilling the
-// buffer two k-blocks later.  After a tile's last k-block the threads read
-// their row of the accumulator from TMEM and store 4 consecutive outputs at a
-// time.
+// CTA: 10 warps, persistent over tiles (and over the frames of a batch), with
+// warp roles: a producer stages each k-block of 64 samples of y by TMA (3-D
+// tensor map whose boxes land in the canonical K-major no-swizzle layout, core
+// matrix = 8 rows x 16 bytes; cp.async when T % 4 != 0) into one of 3 stages;
+// 4 split warps (one row per thread) replace it by |y| rounded to TF32 and
+// write the remainder as A_lo; one thread issues the k-block's 8 k-steps x 4
+// phases x 3 MMAs into one of two TMEM accumulators (2 x 256 columns) and
+// commits them to the stage's and, after a tile's last k-block, the
+// accumulator's mbarrier; 4 epilogue warps read their row of the finished
+// accumulator (TMEM lane = row) while the next tile accumulates, and store 8
+// consecutive outputs (one 32-byte sector) at a time.  Every wait is bounded.
 #pragma once
 
 #include <cuda.h>
@@ -42,7 +42,6 @@ constexpr int kTcRows = 128;         // direction rows per tile (MMA M)
 constexpr int kTcJ = 256;            // output samples per tile
 constexpr int kTcNq = kTcJ / 4;      // columns per phase (MMA N)
 constexpr int kTcKB = 64;            // samples per k-block
-constexpr int kTcThreads = 256;   // (unused by the warp-specialised kernel)
 constexpr int kTcBufBytes = kTcRows * kTcKB * 4;  // one of A_hi / A_lo for a k-block
 
 __host__ __device__ inline int tc_halo(int H) { return (H + 3) & ~3; }
@@ -139,6 +138,14 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
         : "memory");
 }
+// one 32-byte store (a whole L2 sector; p 32-byte aligned)
+__device__ __forceinline__ void st_global_v8(float *p, float a, float b, float c, float d,
+                                             float e, float f, float g, float h) {
+    asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a),
+                 "f"(b), "f"(c), "f"(d), "f"(e), "f"(f), "f"(g), "f"(h)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tc_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::
                      "r"(smem_addr(bar))
@@ -353,6 +360,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
             const TcTile tl = tc_tile(p, blockIdx.x + i * gridDim.x);
             const EnvTcJob &jb = *tl.job;
             const bool vec = (jb.T & 3) == 0;
+            const bool vec8 = (jb.T & 7) == 0 && (reinterpret_cast<uintptr_t>(jb.img) & 31) == 0;
             if (!wait(&acc_full[a], (i >> 1) & 1u)) goto done;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int row = tl.row0 + m;
@@ -365,7 +373,16 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                 for (int r = 0; r < 4; ++r)
                     tmem_ld16(lane_base + (uint32_t)(a * 256 + r * kTcNq + qc), v[r]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (row_ok) {
+                if (row_ok && vec8 && tl.t0 + 4 * (kTcNq - qc) <= jb.T) {
+                    // the 64 outputs are whole: 8 aligned sectors, columns k + 1 and k
+                    // holding outputs t .. t + 7
+#pragma unroll
+                    for (int k = 0; k < 16; k += 2) {
+                        const int t = tl.t0 + 4 * (kTcNq - 2 - qc - k);
+                        st_global_v8(irow + t, v[0][k + 1], v[1][k + 1], v[2][k + 1], v[3][k + 1],
+                                     v[0][k], v[1][k], v[2][k], v[3][k]);
+                    }
+                } else if (row_ok) {
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
                         // column qc + k of phase r holds output j = 4 (Nq - 1 - qc - k) + r
