@@ -161,7 +161,8 @@ size_t beam_smem_bytes(const HostPlan &hp) {
 size_t env_smem_bytes(const HostPlan &hp) {
     if (hp.L == 0) return 0;
     const int Z = tc_Z((hp.L - 1) / 2);
-    return (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023) + (size_t)kTcStages * kTcStageBytes;
+    // + 1 KB: the kernel aligns its stages to 1024 bytes (the 128-byte swizzle period)
+    return 1024 + (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023) + (size_t)kTcStages * kTcStageBytes;
 }
 
 // TF32 rounding (nearest, ties away from zero) of a finite float, as cvt.rna.
@@ -234,12 +235,12 @@ EnvTcJob env_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned
     j.use_tma = 0;
     if ((p->hp.T & 3) == 0 && ((uintptr_t)ybuf & 15) == 0) {
         if (EncodeTiledFn enc = encode_tiled()) {
-            cuuint64_t dims[3] = {4, (cuuint64_t)p->hp.M, (cuuint64_t)(p->hp.T / 4)};
-            cuuint64_t strides[2] = {(cuuint64_t)p->hp.T * 4, 16};
-            cuuint32_t box[3] = {4, 8, 16};
-            cuuint32_t es[3] = {1, 1, 1};
-            if (enc(&j.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)ybuf, dims, strides, box,
-                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            cuuint64_t dims[2] = {(cuuint64_t)p->hp.T, (cuuint64_t)p->hp.M};
+            cuuint64_t strides[1] = {(cuuint64_t)p->hp.T * 4};
+            cuuint32_t box[2] = {kTcAtomK, kTcRows};
+            cuuint32_t es[2] = {1, 1};
+            if (enc(&j.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ybuf, dims, strides, box,
+                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
                 j.use_tma = 1;

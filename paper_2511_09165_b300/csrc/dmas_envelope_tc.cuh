@@ -19,10 +19,18 @@
 // the _hi parts rounded to TF32; each k-step issues A_hi.B_hi + A_hi.B_lo +
 // A_lo.B_hi (the dropped A_lo.B_lo term is ~2^-22 relative).
 //
+// A is held in the K-major layout with the 128-byte swizzle: for each 32-sample
+// column of a k-block ("atom"), row m occupies bytes [128 m, 128 m + 128) and
+// its 16-byte chunk c (samples 4c..4c+3) sits at chunk position c ^ (m & 7);
+// the pattern repeats every 8 rows (1024 bytes, so atoms are 1024-aligned).
+// TMA writes it directly from 128-byte rows of y, the split pass reads and
+// writes it without bank conflicts, and a k-step's descriptor starts 32 bytes
+// further into the atom.
+//
 // CTA: 10 warps, persistent over tiles (and over the frames of a batch), with
-// warp roles: a producer stages each k-block of 64 samples of y by TMA (3-D
-// tensor map whose boxes land in the canonical K-major no-swizzle layout, core
-// matrix = 8 rows x 16 bytes; cp.async when T % 4 != 0) into one of 3 stages;
+// warp roles: a producer stages each k-block of 64 samples of y by TMA (2-D
+// tensor map, two boxes of 32 samples x 128 rows; cp.async to the same layout
+// when T % 4 != 0) into one of 3 stages;
 // 4 split warps (one row per thread) replace it by |y| rounded to TF32 and
 // write the remainder as A_lo; one thread issues the k-block's 8 k-steps x 4
 // phases x 3 MMAs into one of two TMEM accumulators (2 x 256 columns) and
@@ -42,6 +50,8 @@ constexpr int kTcRows = 128;         // direction rows per tile (MMA M)
 constexpr int kTcJ = 256;            // output samples per tile
 constexpr int kTcNq = kTcJ / 4;      // columns per phase (MMA N)
 constexpr int kTcKB = 64;            // samples per k-block
+constexpr int kTcAtomK = 32;         // samples per 128-byte swizzle atom column
+constexpr int kTcAtomBytes = kTcRows * 128;  // one atom column of 128 rows
 constexpr int kTcBufBytes = kTcRows * kTcKB * 4;  // one of A_hi / A_lo for a k-block
 
 __host__ __device__ inline int tc_halo(int H) { return (H + 3) & ~3; }
@@ -50,10 +60,9 @@ __host__ __device__ inline int tc_K(int H) { return kTcJ + 2 * tc_halo(H); }
 __host__ __device__ inline int tc_Z(int H) { return (tc_K(H) + 4 * (kTcNq - 1) + 7) & ~7; }
 
 struct EnvTcJob {
-    // 3-D view of y for the TMA engine when T % 4 == 0: dims (4 samples, M rows,
-    // T/4 chunks), strides (T*4 B, 16 B); a box {4, 8, 16} lands as the 16 core
-    // matrices (8 rows x 16 B) of one 8-row group of a k-block, out-of-range
-    // coordinates filled with zeros.
+    // 2-D view of y for the TMA engine when T % 4 == 0: dims (T, M), box
+    // {32 samples, 128 rows} with the 128-byte swizzle, landing as one atom
+    // column of A; out-of-range coordinates filled with zeros.
     CUtensorMap tmap;
     const float *y;   // [M][T]
     float *img;       // [M][T]
@@ -72,12 +81,23 @@ struct EnvTcParams {
     EnvTcJob job[kBatchMax];
 };
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// Shared-memory matrix descriptor: start, leading and stride byte offsets,
+// version 1 (sm_100 family), base offset 0, layout (0 = no swizzle, 2 = the
+// 128-byte swizzle).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo,
+                                              uint32_t layout = 0) {
     uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
     d |= (uint64_t)((lbo & 0x3FFFF) >> 4) << 16;
     d |= (uint64_t)((sbo & 0x3FFFF) >> 4) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version for sm_100-family tcgen05
-    return d;                // base offset 0, no swizzle
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)layout << 61;
+    return d;
+}
+
+// byte offset of row m's 16-byte chunk c (c = 0..15 over a k-block) in the
+// swizzled A buffer of a stage
+__device__ __forceinline__ int sw128_off(int m, int c) {
+    return (c >> 3) * kTcAtomBytes + m * 128 + (((c & 7) ^ (m & 7)) << 4);
 }
 
 // kind::tf32 instruction descriptor: D f32, A/B tf32, both K-major, N and M.
@@ -130,12 +150,12 @@ __device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
     asm volatile("cp.async.mbarrier.arrive.shared::cta.b64 [%0];" ::"r"(smem_addr(bar))
                  : "memory");
 }
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1,
-                                            int c2, uint64_t *bar) {
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                            uint64_t *bar) {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
-        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(smem_addr(bar))
         : "memory");
 }
 // one 32-byte store (a whole L2 sector; p 32-byte aligned)
@@ -168,9 +188,14 @@ __device__ __forceinline__ TcTile tc_tile(const EnvTcParams &p, unsigned tile) {
 }
 
 // Warp roles: 0-3 split (one row each), 4-7 epilogue (TMEM lane quarters),
-// 8 producer (cp.async), 9 MMA issue (lane 0) and TMEM allocation.
+// 8 producer, 9.. MMA issue (lane 0 of each; warp 9 also allocates TMEM).  A
+// tcgen05.mma costs its issuing thread tens of cycles (measured: ~70 per
+// M=128 N=64 K=8 instruction), more than the tensor core needs to run it, so
+// the phases are spread over kTcMmaWarps issuing warps.
 constexpr int kTcStages = 3;
-constexpr int kTcWarps = 10;
+constexpr int kTcMmaWarps = 2;
+constexpr int kTcPhasesPerWarp = 4 / kTcMmaWarps;
+constexpr int kTcWarps = 9 + kTcMmaWarps;
 constexpr int kTcThreadsWS = kTcWarps * 32;
 constexpr int kTcStageBytes = 2 * kTcBufBytes;  // A_hi (loaded raw, split in place) + A_lo
 
@@ -184,8 +209,10 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int H = p.H, HA = tc_halo(H), K = tc_K(H), Z = tc_Z(H);
     const int n_kb = (K + kTcKB - 1) / kTcKB;
-    float *s_taps = reinterpret_cast<float *>(smem);                               // [2][4][Z]
-    unsigned char *stages = smem + (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023);  // [S][hi,lo]
+    // the dynamic window starts 1024-aligned (its size has 1 KB to spare)
+    unsigned char *base = smem + ((1024u - (smem_addr(smem) & 1023u)) & 1023u);
+    float *s_taps = reinterpret_cast<float *>(base);                               // [2][4][Z]
+    unsigned char *stages = base + (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023);  // [S][hi,lo]
     const unsigned n_tiles = (blockIdx.x < p.total_tiles)
                                  ? (p.total_tiles - 1 - blockIdx.x) / gridDim.x + 1
                                  : 0;
@@ -202,10 +229,10 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
         for (int s = 0; s < kTcStages; ++s) {
             mbar_init(&full[s], 1);         // producer lane 0 (+ bytes or cp.async arrivals)
             mbar_init(&split_done[s], 128); // split threads
-            mbar_init(&empty[s], 1);        // MMA commit
+            mbar_init(&empty[s], kTcMmaWarps);  // MMA commits
         }
         for (int a = 0; a < 2; ++a) {
-            mbar_init(&acc_full[a], 1);     // MMA commit after a tile's last k-block
+            mbar_init(&acc_full[a], kTcMmaWarps);  // MMA commits after a tile's last k-block
             mbar_init(&acc_empty[a], 128);  // epilogue threads
         }
         abort_flag = 0;
@@ -239,25 +266,26 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                 const int u0 = kb * kTcKB;
                 const int nc4 = min(kTcKB, K - u0) / 4;
                 if (jb.use_tma) {
-                    // 16 boxes of 8 rows x 16 chunks (32 KB); chunks past K land in
-                    // the unused tail of the buffer
+                    // two atom columns of 32 samples x 128 rows (32 KB); samples past
+                    // K are loaded but never read by the MMAs
                     if (lane == 0) {
-                        mbar_arrive_expect_tx(&full[s], 16u * 2048u);
-                        const int chunk0 = (tl.t0 - HA + u0) / 4;  // exact: all terms % 4 == 0
-                        for (int a = 0; a < kTcRows / 8; ++a)
-                            tma_load_3d(ahi + a * 512, &jb.tmap, 0, tl.row0 + 8 * a, chunk0,
+                        mbar_arrive_expect_tx(&full[s], (uint32_t)(kTcKB / kTcAtomK) * kTcAtomBytes);
+                        // x = t0 - HA + u0 (+ 32): a multiple of 4 samples (16 bytes)
+                        for (int a = 0; a < kTcKB / kTcAtomK; ++a)
+                            tma_load_2d(reinterpret_cast<unsigned char *>(ahi) + a * kTcAtomBytes,
+                                        &jb.tmap, tl.t0 - HA + u0 + kTcAtomK * a, tl.row0,
                                         &full[s]);
                     }
                     continue;
                 }
                 // fallback (T % 4 != 0): chunk (m, c), 4 samples of row m at
-                // t = t0 - HA + u0 + 4c, copied to the canonical K-major position of
-                // A (core matrix 8 rows x 16 B) by 4-byte cp.async with zero fill
+                // t = t0 - HA + u0 + 4c, copied to its swizzled position by 4-byte
+                // cp.async with zero fill
                 for (int idx = lane; idx < kTcRows * nc4; idx += 32) {
                     const int m = idx % kTcRows, c = idx / kTcRows;
                     const int row = tl.row0 + m;
                     const int t = tl.t0 - HA + u0 + 4 * c;
-                    float *dst = ahi + (((m & 7) * 16 + (m >> 3) * 2048 + c * 128) >> 2);
+                    float *dst = ahi + (sw128_off(m, c) >> 2);
                     const float *rowp = jb.y + (size_t)(row < jb.M ? row : 0) * jb.T;
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
@@ -273,7 +301,6 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
     } else if (warp < 4) {
         // -------------------------- split |y| -> hi, lo ---------------------
         const int m = tid;  // row of the tile
-        const int rowoff = (m & 7) * 16 + (m >> 3) * 2048;
         unsigned g = 0;
         for (unsigned i = 0; i < n_tiles; ++i) {
             for (int kb = 0; kb < n_kb; ++kb, ++g) {
@@ -284,7 +311,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                 const int nc4 = min(kTcKB, K - kb * kTcKB) / 4;
 #pragma unroll 4
                 for (int c = 0; c < nc4; ++c) {
-                    const int off = (rowoff + c * 128) >> 2;
+                    const int off = sw128_off(m, c) >> 2;
                     const float4 v = *reinterpret_cast<const float4 *>(ahi + off);
                     float4 h, l;
                     h.x = tf32_round(fabsf(v.x)); l.x = fabsf(v.x) - h.x;
@@ -298,8 +325,9 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                 mbar_arrive(&split_done[s]);
             }
         }
-    } else if (warp == 9) {
+    } else if (warp >= 9) {
         // ------------------------------ MMA issue ----------------------------
+        const int r0 = (warp - 9) * kTcPhasesPerWarp;  // this warp's phases
         const uint32_t idesc = tc_idesc(kTcRows, kTcNq);
         const uint32_t taps_base = smem_addr(s_taps);
         unsigned g = 0;
@@ -317,28 +345,32 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                     const uint32_t a_hi = smem_addr(stages + (size_t)s * kTcStageBytes);
                     const int u0 = kb * kTcKB;
                     const int nks = min(kTcKB, K - u0) / 8;
-                    // descriptors of the k-block's first k-step; a k-step advances A by
-                    // two core matrices (256 B) and B by 8 samples (32 B): +16 and +2
-                    // in the descriptors' 16-byte address field
-                    const uint64_t dah0 = smem_desc(a_hi, 128, 2048);
-                    const uint64_t dal0 = smem_desc(a_hi + kTcBufBytes, 128, 2048);
-                    uint64_t dbh0[4], dbl0[4];
+                    // descriptors of the k-block's first k-step.  A (128-byte swizzle,
+                    // 8-row groups 1024 B apart): a k-step of 8 samples advances 32 B
+                    // within an atom column, the fifth starts the next atom column.
+                    // B advances 8 samples (32 B).  Both in 16-byte address units.
+                    const uint64_t dah0 = smem_desc(a_hi, 16, 1024, 2);
+                    const uint64_t dal0 = smem_desc(a_hi + kTcBufBytes, 16, 1024, 2);
+                    uint64_t dbh0[kTcPhasesPerWarp], dbl0[kTcPhasesPerWarp];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        dbh0[r] = smem_desc(taps_base + (uint32_t)(r * Z * 4 + u0 * 4), 16, 128);
-                        dbl0[r] = smem_desc(taps_base + (uint32_t)((4 + r) * Z * 4 + u0 * 4), 16, 128);
+                    for (int rr = 0; rr < kTcPhasesPerWarp; ++rr) {
+                        const int r = r0 + rr;
+                        dbh0[rr] = smem_desc(taps_base + (uint32_t)(r * Z * 4 + u0 * 4), 16, 128);
+                        dbl0[rr] = smem_desc(taps_base + (uint32_t)((4 + r) * Z * 4 + u0 * 4), 16, 128);
                     }
                     const uint32_t acc0 = kb > 0 ? 1u : 0u;
 #pragma unroll
                     for (int ks = 0; ks < kTcKB / 8; ++ks) {
                         if (ks < nks) {
-                            const uint64_t dah = dah0 + (uint64_t)(16 * ks);
-                            const uint64_t dal = dal0 + (uint64_t)(16 * ks);
+                            const uint64_t da =
+                                (uint64_t)((ks >> 2) * (kTcAtomBytes >> 4) + (ks & 3) * 2);
+                            const uint64_t dah = dah0 + da;
+                            const uint64_t dal = dal0 + da;
 #pragma unroll
-                            for (int r = 0; r < 4; ++r) {
-                                const uint32_t d = dacc + (uint32_t)(r * kTcNq);
-                                const uint64_t dbh = dbh0[r] + (uint64_t)(2 * ks);
-                                const uint64_t dbl = dbl0[r] + (uint64_t)(2 * ks);
+                            for (int rr = 0; rr < kTcPhasesPerWarp; ++rr) {
+                                const uint32_t d = dacc + (uint32_t)((r0 + rr) * kTcNq);
+                                const uint64_t dbh = dbh0[rr] + (uint64_t)(2 * ks);
+                                const uint64_t dbl = dbl0[rr] + (uint64_t)(2 * ks);
                                 tc_mma(d, dah, dbh, idesc, (ks > 0) ? 1u : acc0);
                                 tc_mma(d, dah, dbl, idesc, 1u);
                                 tc_mma(d, dal, dbh, idesc, 1u);
@@ -351,7 +383,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                 __syncwarp();
             }
         }
-    } else {
+    } else if (warp >= 4 && warp < 8) {
         // ------------------------------ epilogue -----------------------------
         const int m = (warp & 3) * 32 + lane;  // TMEM lane = row of the tile
         const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
