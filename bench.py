@@ -75,8 +75,9 @@ WORKLOADS = {
 # DRAM bytes (read + write) of one beamform launch on the default workload, from
 # one ncu capture (profiles/beamform_x2_hemi3d_n5.md), valid while the kernel
 # source is the one that was measured.
-TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "kernel_src_sha256_16": "ae7dfaae35d605d5",
-                  "bytes": 5886464 + 75518720}
+TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "kernel_src_sha256_16": "082c1683f2e8c29a",
+                  # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (MB, 2 decimals)
+                  "bytes": 5_890_000 + 74_920_000}
 
 
 def beam_traffic(workload: str):
@@ -337,8 +338,12 @@ def run_ours(args, wl, scene) -> None:
         return
     ops = algorithmic_ops_per_pixel(N, order, linear)
     beam_ms = float(np.mean(stage[:, 1]))
+    env_ms = float(np.mean(stage[:, 2]))
     peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12   # T op/s
     achieved = ops["beam_total"] * px / (beam_ms * 1e-3) / 1e12
+    # the whole per-pixel path (beamform + envelope, L taps), as one roofline
+    path_ops = ops["beam_total"] + info.env_taps
+    path_achieved = path_ops * px / ((beam_ms + env_ms) * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -352,12 +357,14 @@ def run_ours(args, wl, scene) -> None:
                        "p99": float(np.percentile(step_ms, 99))},
         "stage_ms": {"roots": float(np.mean(stage[:, 0])), "beamform": beam_ms,
                      "envelope": float(np.mean(stage[:, 2]))},
-        "roofline": {"bound": "alu", "kernel": "beamform_kernel", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": "beamform_x2_kernel", "achieved": achieved,
                      "peak": peak, "unit": "Top/s", "frac": achieved / peak,
                      "ops_per_pixel": ops, "pixels_per_launch": px,
                      "peak_source": "148 SMs x 128 FP32 lanes x 2032 MHz (unit counts)",
                      "traffic": beam_traffic(args.workload),
-                     "algorithmic_bytes": px * 4 + 2 * N * T * 4},
+                     "algorithmic_bytes": px * 4 + N * T * 4 * (2 if linear else 1),
+                     "path": {"stages": "beamform + envelope", "ops_per_pixel": path_ops,
+                              "achieved": path_achieved, "frac": path_achieved / peak}},
         "e2e": {"value": px * world * e2e_steps / e2e_total, "unit": UNIT,
                 "h2d_bytes_per_step": N * T * 4, "d2h_bytes_per_step": M * T * 4},
         "gpu_launches": 3 * args.steps,
