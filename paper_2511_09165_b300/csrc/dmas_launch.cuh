@@ -29,12 +29,43 @@ cudaError_t launch_kernel(K kern, std::once_flag &once, cudaError_t &attr_err, c
 }
 
 // Launch of the persistent kernel: `items` work items, at most kPersistItems
-// per CTA.
+// per CTA, and never fewer CTAs than fit on the device at once (occupancy for
+// this kernel and shared-memory size, cached per device), so small frames
+// still spread over every SM.
 template <typename K, typename P>
 cudaError_t launch_persistent(K kern, std::once_flag &once, cudaError_t &attr_err, const P &p,
                               unsigned items, size_t smem, cudaStream_t s) {
-    return launch_kernel(kern, once, attr_err, p, (items + kPersistItems - 1) / kPersistItems,
-                         smem, s);
+    std::call_once(once, [&] {
+        attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        kBeamSmemOptIn);
+    });
+    if (attr_err != cudaSuccess) return attr_err;
+    struct Slot { int dev = -1; size_t smem = 0; unsigned ctas = 0; };
+    static std::mutex mu;
+    static Slot cache[4];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    unsigned resident = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const Slot &c : cache)
+            if (c.dev == dev && c.smem == smem) resident = c.ctas;
+        if (resident == 0) {
+            int per_sm = 0, sms = 0;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads,
+                                                                   smem)) != cudaSuccess ||
+                (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) !=
+                    cudaSuccess)
+                return e;
+            resident = (unsigned)std::max(1, per_sm) * (unsigned)sms;
+            std::rotate(cache, cache + 3, cache + 4);
+            cache[0] = Slot{dev, smem, resident};
+        }
+    }
+    const unsigned capped = (items + kPersistItems - 1) / kPersistItems;
+    kern<<<std::min(items, std::max(capped, resident)), kThreads, smem, s>>>(p);
+    return cudaGetLastError();
 }
 
 // FP32 channels up to kPairMaxOrder: the pair kernel (2 pairs per lane;
