@@ -157,12 +157,9 @@ __device__ __forceinline__ void roots_body(const RootsParams &p, size_t first, s
         float r = 0.0f;
         if (t >= 0 && t < p.T) r = signed_root(p.frame[(size_t)i * p.T + t], p.order, p.inv_order);
         chan[idx] = to_ch<CH>(r);
-        if (p.shifted) {
-            const int t1 = t + 1;
-            float r1 = 0.0f;
-            if (t1 >= 0 && t1 < p.T)
-                r1 = signed_root(p.frame[(size_t)i * p.T + t1], p.order, p.inv_order);
-            chan[total + idx] = to_ch<CH>(r1);
+        if (p.shifted) {  // chan1[i][c - 1] = chan0[i][c]; the row's last sample is 0
+            if (c > 0) chan[total + idx - 1] = to_ch<CH>(r);
+            if (c == p.row - 1) chan[total + idx] = to_ch<CH>(0.0f);
         }
     }
 }
@@ -318,6 +315,12 @@ __device__ __forceinline__ float esym_from_power_sums(const float (&P)[ORDER + 1
 // ---------------------------------------------------------------------------
 // K2: gather + power sums + Newton-Girard + CF
 // ---------------------------------------------------------------------------
+// CF = A^2 / (N B + eps) with CUDA's fast division (__fdividef: within 2 ulp
+// for denominators up to 2^126; N B + eps >= eps > 0).
+__device__ __forceinline__ float cf_ratio(float A, float B, float n_mics, float eps) {
+    return __fdividef(A * A, fmaf(n_mics, B, eps));
+}
+
 struct BeamParams {
     const void *chan;    // [N][row] roots, zero padded
     const int *gdir;     // [n_groups * 8] direction index or -1
@@ -463,7 +466,7 @@ __device__ __forceinline__ void beamform_body(const BeamParams &p, unsigned bloc
         const float A = acc[k][NP], B = acc[k][NP + 1];
         if constexpr (SumLayout<ORDER>::kPnIsA) P[ORDER] = A;
         const float E = esym_from_power_sums<ORDER, NGP>(P);
-        const float cf = (A * A) / fmaf(p.n_mics_f, B, p.cf_eps);
+        const float cf = cf_ratio(A, B, p.n_mics_f, p.cf_eps);
         yrow[t] = p.use_cf ? E * cf : E;
         if (cfrow) cfrow[t] = cf;
     }
@@ -730,7 +733,7 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
             if (t >= p.T) continue;
             if constexpr (SumLayout<ORDER>::kPnIsA) P[h][ORDER] = A[h];
             const float E = esym_from_power_sums<ORDER, NGP>(P[h]);
-            const float cf = (A[h] * A[h]) / fmaf(p.n_mics_f, B[h], p.cf_eps);
+            const float cf = cf_ratio(A[h], B[h], p.n_mics_f, p.cf_eps);
             yrow[t] = p.use_cf ? E * cf : E;
             if (cfrow) cfrow[t] = cf;
         }
@@ -934,7 +937,7 @@ __device__ __forceinline__ void beamform_x2_run(const Src &src) {
                     if (t >= p.T) continue;
                     if constexpr (SumLayout<ORDER>::kPnIsA) P[h][ORDER] = A[h];
                     const float E = esym_from_power_sums<ORDER, NGP>(P[h]);
-                    const float cf = (A[h] * A[h]) / fmaf(p.n_mics_f, B[h], p.cf_eps);
+                    const float cf = cf_ratio(A[h], B[h], p.n_mics_f, p.cf_eps);
                     yrow[t] = p.use_cf ? E * cf : E;
                     if (cfrow) cfrow[t] = cf;
                 }
