@@ -243,8 +243,9 @@ dmas_status dmas_selftest_wait_timeout(double limit_ms, void *stream);
  * allocator so that a new cudaMalloc would fail.
  *
  * It runs the same kernels as dmas_beamform with the same results, but its
- * scratch (the root channels and, with DMAS_F_ENVELOPE, the pre-envelope
- * image) lives in one static device array of DMAS_NOALLOC_SCRATCH_BYTES that
+ * scratch (the root channels, with DMAS_F_ENVELOPE the pre-envelope image,
+ * and the beamform kernel's work counter) lives in one static device array of
+ * DMAS_NOALLOC_SCRATCH_BYTES that
  * the library holds on every GPU it is loaded on until the process exits.
  * The plan itself is created beforehand with dmas_plan_create, which does
  * allocate (once, at set-up).
