@@ -11,6 +11,7 @@
 
 #include "dmas.h"
 #include "dmas_internal.h"
+#include "dmas_envelope_fir.cuh"
 #include "dmas_envelope_tc.cuh"
 #include "dmas_launch.cuh"
 
@@ -78,6 +79,7 @@ struct dmas_plan {
     float *d_io_frame = nullptr, *d_io_image = nullptr;  // dmas_beamform_host staging
     size_t smem_beam = 0, smem_env = 0;
     float *d_taps_tc = nullptr;       // envelope taps as TF32 hi/lo phase arrays [2][4][Z]
+    float *d_taps = nullptr;          // envelope taps [L] (CUDA-core FIR for small frames)
     int num_sms = 148;
     cudaStream_t last_stream = nullptr;
     std::string last_error;
@@ -125,7 +127,9 @@ void free_plan_memory(dmas_plan *p) {
     cudaFree(p->d_io_frame);
     cudaFree(p->d_io_image);
     cudaFree(p->d_taps_tc);
+    cudaFree(p->d_taps);
     p->d_taps_tc = nullptr;
+    p->d_taps = nullptr;
     for (auto &e : p->ev) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
@@ -260,6 +264,25 @@ unsigned env_tiles(const dmas_plan *p) {
                       (((size_t)p->hp.T + kTcJ - 1) / kTcJ));
 }
 
+// Frames with fewer tensor-core tiles than SMs take the CUDA-core FIR (a
+// property of the plan, so a frame gets the same kernel alone and in a batch).
+bool env_on_cuda_cores(const dmas_plan *p) { return env_tiles(p) < (unsigned)p->num_sms; }
+
+EnvFirJob fir_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned first) {
+    EnvFirJob j;
+    j.y = ybuf;
+    j.img = d_image;
+    j.M = p->hp.M;
+    j.T = p->hp.T;
+    j.t_tiles = (p->hp.T + kFirTile - 1) / kFirTile;
+    j.first = first;
+    return j;
+}
+
+unsigned fir_ctas(const dmas_plan *p) {
+    return (unsigned)((size_t)p->hp.M * ((p->hp.T + kFirTile - 1) / kFirTile));
+}
+
 void mark(dmas_plan *p, int k, cudaStream_t s) {
     if (p->profiling) cudaEventRecord(p->ev[k], s);
 }
@@ -374,7 +397,21 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
         p->profiled_once = p->profiled_once || p->profiling;
         return DMAS_OK;
     }
-    // K3: envelope on the tensor cores
+    // K3: envelope, on the CUDA cores for small frames, else on the tensor cores
+    if (env_on_cuda_cores(p)) {
+        EnvFirParams fp{};
+        fp.count = 1;
+        fp.H = (hp.L - 1) / 2;
+        fp.taps = p->d_taps;
+        fp.job[0] = fir_job(p, ybuf, d_image, 0);
+        envelope_fir_kernel<<<fir_ctas(p), kFirTile, 0, s>>>(fp);
+        if ((e = cudaGetLastError()) != cudaSuccess)
+            return cuda_fail(p, e, "envelope_fir_kernel launch");
+        mark(p, 3, s);
+        p->env_ran = true;
+        p->profiled_once = p->profiled_once || p->profiling;
+        return DMAS_OK;
+    }
     EnvTcParams ep{};
     ep.count = 1;
     ep.job[0] = env_job(p, ybuf, d_image, 0);
@@ -463,20 +500,38 @@ dmas_status enqueue_batch(const std::vector<BatchEntry> &v, cudaStream_t s) {
             if (e != cudaSuccess) return cuda_fail(v[cls[b0]].plan, e, "beamform batch");
         }
     }
-    // K3: envelope, grouped by identical taps
+    // K3: envelope, grouped by identical taps and by engine (CUDA-core FIR for
+    // small frames, tensor cores otherwise)
     std::fill(done.begin(), done.end(), false);
     for (size_t i = 0; i < v.size(); ++i) {
         if (done[i] || v[i].plan->hp.L == 0) continue;
         const HostPlan &a = v[i].plan->hp;
+        const bool fir = env_on_cuda_cores(v[i].plan);
         std::vector<size_t> cls;
         for (size_t j = i; j < v.size(); ++j) {
             const HostPlan &b = v[j].plan->hp;
-            if (!done[j] && b.L == a.L && b.taps == a.taps) {
+            if (!done[j] && b.L == a.L && b.taps == a.taps &&
+                env_on_cuda_cores(v[j].plan) == fir) {
                 cls.push_back(j);
                 done[j] = true;
             }
         }
-        for (size_t b0 = 0; b0 < cls.size(); b0 += kBatchMax) {
+        for (size_t b0 = 0; fir && b0 < cls.size(); b0 += kBatchMax) {
+            EnvFirParams fp{};
+            fp.count = (int)std::min<size_t>(kBatchMax, cls.size() - b0);
+            unsigned ctas = 0;
+            for (int k = 0; k < fp.count; ++k) {
+                const BatchEntry &x = v[cls[b0 + k]];
+                fp.job[k] = fir_job(x.plan, x.ybuf, x.image, ctas);
+                ctas += fir_ctas(x.plan);
+            }
+            fp.H = (a.L - 1) / 2;
+            fp.taps = v[cls[b0]].plan->d_taps;
+            envelope_fir_kernel<<<ctas, kFirTile, 0, s>>>(fp);
+            if ((e = cudaGetLastError()) != cudaSuccess)
+                return cuda_fail(v[cls[b0]].plan, e, "envelope fir batch");
+        }
+        for (size_t b0 = 0; !fir && b0 < cls.size(); b0 += kBatchMax) {
             EnvTcParams ep{};
             ep.count = (int)std::min<size_t>(kBatchMax, cls.size() - b0);
             unsigned tiles = 0;
@@ -563,7 +618,8 @@ dmas_status dmas_plan_create(const dmas_plan_desc *desc, dmas_plan **out) {
             delete p;
             return DMAS_ENOMEM;
         }
-        if ((e = upload(&p->d_taps_tc, tc)) != cudaSuccess) {
+        if ((e = upload(&p->d_taps_tc, tc)) != cudaSuccess ||
+            (e = upload(&p->d_taps, hp.taps)) != cudaSuccess) {
             free_plan_memory(p);
             delete p;
             cudaGetLastError();

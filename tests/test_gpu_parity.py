@@ -195,6 +195,18 @@ def test_generic_envelope_length():
     assert_parity(g, r)
 
 
+@pytest.mark.parametrize("T,M,taps", [(6001, 1200, None), (6000, 1201, None), (6004, 1200, 33)])
+def test_tensor_core_envelope_ragged_tiles(T, M, taps):
+    """Frames with more 128 x 256 envelope tiles than SMs take the tensor-core
+    FIR (smaller ones the CUDA-core FIR): ragged last row block and time tile,
+    T % 4 != 0 (copy fallback) and T % 4 == 0 (TMA), another tap count."""
+    sc = hemi(T, M)
+    kw = {} if taps is None else {"env_cutoff_hz": 20000.0, "env_taps": taps}
+    g = run_gpu(sc, 3, dm.LINEAR, **kw)
+    r = oracle_run(sc, 3, oracle.LINEAR, **kw)
+    assert_parity(g, r)
+
+
 # ---------------------------------------------------------------------------
 # reduced-precision channels (measured bounds)
 # ---------------------------------------------------------------------------

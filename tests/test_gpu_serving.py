@@ -28,13 +28,16 @@ def test_batch_of_mixed_variants_is_bitwise_equal_to_single_calls():
     a = scenes.small_2d(seed=1, n_samples=1500)
     b = scenes.hemi_3d(seed=2, n_samples=1100, n_dirs=100)
     c = scenes.passive(seed=4, n_mics=40, n_samples=900, n_az=12, n_el=6)
+    # large enough for the tensor-core envelope (more 128 x 256 tiles than SMs)
+    d = scenes.hemi_3d(seed=2, n_samples=4100, n_dirs=1200)
     plans = [
         _plan(a, 5, dm.ROUND), _plan(a, 3, dm.ROUND), _plan(b, 5, dm.LINEAR),
         _plan(b, 2, dm.LINEAR, ng_prec=dm.NG_CF32), _plan(a, 7, dm.ROUND),
         _plan(a, 5, dm.ROUND, chan_prec=dm.CH_F16), _plan(c, 4, dm.ROUND, envelope=False),
         _plan(a, 5, dm.ROUND, env_taps=51), _plan(c, 5, dm.LINEAR, cf=False),
+        _plan(d, 3, dm.LINEAR), _plan(d, 5, dm.ROUND),
     ]
-    scs = [a, a, b, b, a, a, c, a, c]
+    scs = [a, a, b, b, a, a, c, a, c, d, d]
     frames = [torch.from_numpy(sc.frame).cuda() for sc in scs]
     alone = [p(f).clone() for p, f in zip(plans, frames)]
     # every plan twice, interleaved, in one batch
