@@ -64,6 +64,17 @@ WORKLOADS = {
         text="passive: 64 mics in a 0.4 m square, 8192 az/el directions, 32768 samples "
              "at 400 kHz, 4 broadband sources, 0 dB SNR, n=5, nearest-sample delays, "
              "CF, 161-tap envelope"),
+    # the paper's timing workload (Table II): N = 32, 1000 directions, 163840
+    # samples (the reading in which the stated sample count is processed),
+    # DMAS5 without CF; delay mode unstated (nearest sample here), envelope
+    # included here.  The paper's fastest GPU, an RTX 3090, took 40 ms.
+    "paper_2d_1000_n5": dict(
+        scene=lambda: scenes.small_2d(seed=1, n_samples=163840, n_dirs=1000), order=5,
+        mode="round", cf=False, paper_rate=1000 * 163840 / 40e-3,
+        text="the paper's timing configuration: 32 mics in a 12 cm disc, 1000 azimuths "
+             "over -90..90 deg, 163840 samples at 450 kHz, n=5 without CF, "
+             "nearest-sample delays, 181-tap envelope; vs_baseline against the paper's "
+             "RTX 3090 (40 ms per frame, Table II)"),
     "passive256_n5": dict(
         scene=lambda: scenes.passive(seed=4, n_mics=256), order=5, mode="round",
         text="passive: 256 mics in a 0.4 m square, 8192 az/el directions, 32768 samples "
@@ -195,7 +206,7 @@ def dist_barrier(td):
 # ---------------------------------------------------------------------------
 # CPU oracle timing
 # ---------------------------------------------------------------------------
-def oracle_sample(scene, order, linear, n_dirs):
+def oracle_sample(scene, order, linear, n_dirs, cf=True):
     import oracle
     u = scene.dir_unit if scene.dir_unit is not None else oracle.unit_vectors(scene.dir_azel)
     tau = oracle.geometric_delays(scene.mic_xyz, u, scene.c)
@@ -204,22 +215,22 @@ def oracle_sample(scene, order, linear, n_dirs):
     D = min(n_dirs, scene.n_dirs)
     t0 = time.perf_counter()
     oracle.dmas(frame, tau, scene.fs, order, oracle.LINEAR if linear else oracle.ROUND,
-                use_cf=True, taps=taps, dir_range=(0, D))
+                use_cf=cf, taps=taps, dir_range=(0, D))
     dt = time.perf_counter() - t0
     return D * scene.n_samples, dt
 
 
-def cpu_baseline(scene, order, linear, min_s=10.0) -> dict:
+def cpu_baseline(scene, order, linear, cf=True, min_s=10.0) -> dict:
     """The oracle as it stands, on all host cores: whole frames of the workload
     (or a direction subset if a frame takes longer than min_s), repeated until
     at least min_s seconds of CPU work."""
     import oracle
     cores = oracle.set_threads(os.cpu_count() or 1)
-    px, dt = oracle_sample(scene, order, linear, 64)
+    px, dt = oracle_sample(scene, order, linear, 64, cf)
     D = int(max(64, min(scene.n_dirs, min_s * px / dt / scene.n_samples)))
     total_px, total_s, reps = 0, 0.0, 0
     while total_s < min_s:
-        px, dt = oracle_sample(scene, order, linear, D)
+        px, dt = oracle_sample(scene, order, linear, D, cf)
         total_px += px
         total_s += dt
         reps += 1
@@ -235,15 +246,16 @@ def run_reference(args, wl, scene) -> None:
         return
     import oracle
     linear = wl["mode"] == "linear"
+    cf = wl.get("cf", True)
     cores = oracle.set_threads(os.cpu_count() or 1)
-    px, dt = oracle_sample(scene, wl["order"], linear, 16)
+    px, dt = oracle_sample(scene, wl["order"], linear, 16, cf)
     rate = px / dt
     D = int(max(8, min(scene.n_dirs, 0.4 * rate / scene.n_samples)))  # ~0.4 s a step
     for _ in range(args.warmup):
-        oracle_sample(scene, wl["order"], linear, D)
+        oracle_sample(scene, wl["order"], linear, D, cf)
     times = []
     for _ in range(args.steps):
-        px, dt = oracle_sample(scene, wl["order"], linear, D)
+        px, dt = oracle_sample(scene, wl["order"], linear, D, cf)
         times.append(dt)
     value = px * len(times) / sum(times)
     line = {
@@ -275,9 +287,10 @@ def run_ours(args, wl, scene) -> None:
     td = dist_init(world, "nccl")
     linear = wl["mode"] == "linear"
     order = wl["order"]
+    cf = wl.get("cf", True)
     plan = dm.Plan(mic_xyz=scene.mic_xyz, dir_azel=scene.dir_azel, dir_unit=scene.dir_unit,
                    n_samples=scene.n_samples, fs=scene.fs, c=scene.c, order=order,
-                   delay_mode=dm.LINEAR if linear else dm.ROUND)
+                   delay_mode=dm.LINEAR if linear else dm.ROUND, cf=cf)
     info = plan.info()
     N, M, T = scene.n_mics, scene.n_dirs, scene.n_samples
     px = M * T
@@ -347,11 +360,13 @@ def run_ours(args, wl, scene) -> None:
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
+        "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": (value / wl["paper_rate"]) if "paper_rate" in wl else None,
+        "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "description": wl["text"],
                    "n_mics": N, "n_dirs": M, "n_samples": T, "order": order,
-                   "delays": wl["mode"], "l2": "flushed (256 MB write) before every step",
+                   "delays": wl["mode"], "cf": cf,
+                   "l2": "flushed (256 MB write) before every step",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
@@ -373,7 +388,7 @@ def run_ours(args, wl, scene) -> None:
                  "groups": info.n_groups},
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(scene, order, linear)
+        line["cpu_baseline"] = cpu_baseline(scene, order, linear, cf)
     print(json.dumps(line), flush=True)
 
 
@@ -476,13 +491,76 @@ def run_serving(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# direction sweep: frame time against the number of directions (the paper's
+# Fig. 7 shape), 2-D fan, 16384 samples, n=5 with CF
+# ---------------------------------------------------------------------------
+SWEEP_DIRS = [2, 10, 50, 100, 250, 500, 1000, 2000, 4000]
+
+
+def run_sweep(args) -> None:
+    import torch
+    import paper_2511_09165_b300 as dm
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+    steps = max(5, min(args.steps, 50))
+    clocks = ClockSampler(local)
+    clocks.start()
+    wall0 = time.time()
+    rows = []
+    for M in SWEEP_DIRS:
+        sc = scenes.small_2d(seed=1, n_samples=16384, n_dirs=M)
+        plan = dm.Plan(mic_xyz=sc.mic_xyz, dir_azel=sc.dir_azel, n_samples=sc.n_samples,
+                       fs=sc.fs, c=sc.c, order=5, delay_mode=dm.ROUND)
+        frame = torch.from_numpy(sc.frame).to(dev)
+        image = torch.empty((M, sc.n_samples), device=dev)
+        for _ in range(args.warmup):
+            flush.zero_()
+            plan(frame, out=image, stream=stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            plan(frame, out=image, stream=stream)
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        plan.check()
+        plan.close()
+        ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+        rows.append({"n_dirs": M, "ms_p50": ms, "dir_samples_per_s": M * sc.n_samples / ms * 1e3})
+    wall1 = time.time()
+    clocks.stop()
+    if rank != 0:
+        return
+    top = rows[-1]
+    print(json.dumps({
+        "metric": METRIC, "value": top["dir_samples_per_s"], "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": top["ms_p50"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "sweep", "description":
+                   "2-D fan (32 mics, 12 cm disc), 16384 samples at 450 kHz, n=5 with CF, "
+                   "nearest-sample delays, envelope; frame time per direction count "
+                   "(median of CUDA-event steps, L2 flushed before each)",
+                   "n_dirs": SWEEP_DIRS},
+        "sweep": rows,
+        "clocks": clocks.summary(wall0, wall1),
+    }), flush=True)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving"], default="hemi_3d_n5")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving", "sweep"],
+                    default="hemi_3d_n5")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 1000.0])
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-budget-gb", type=int, default=48)
@@ -496,6 +574,13 @@ def main() -> None:
                               "the serving workload has no CPU reference arm"}))
             return
         run_serving(args)
+        return
+    if args.workload == "sweep":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the direction sweep has no CPU reference arm"}))
+            return
+        run_sweep(args)
         return
     wl = WORKLOADS[args.workload]
     scene = wl["scene"]()

@@ -264,9 +264,14 @@ unsigned env_tiles(const dmas_plan *p) {
                       (((size_t)p->hp.T + kTcJ - 1) / kTcJ));
 }
 
-// Frames with fewer tensor-core tiles than SMs take the CUDA-core FIR (a
-// property of the plan, so a frame gets the same kernel alone and in a batch).
-bool env_on_cuda_cores(const dmas_plan *p) { return env_tiles(p) < (unsigned)p->num_sms; }
+// Small frames take the CUDA-core FIR: at most 1.5e8 tap products (M T L), about
+// what one wave of tensor-core tiles costs (measured on B300: the 2-D frame,
+// 91 x 4096 x 181 = 6.7e7, runs 23 us there against ~50 us on the tensor
+// cores; 250 x 16384 x 181 = 7.4e8 runs faster on the tensor cores).  A
+// property of the plan, so a frame gets the same kernel alone and in a batch.
+bool env_on_cuda_cores(const dmas_plan *p) {
+    return (double)p->hp.M * (double)p->hp.T * (double)p->hp.L <= 1.5e8;
+}
 
 EnvFirJob fir_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned first) {
     EnvFirJob j;

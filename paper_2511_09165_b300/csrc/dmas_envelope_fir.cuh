@@ -1,5 +1,5 @@
 // Envelope low-pass on the CUDA cores, for frames too small to fill the GPU
-// with tensor-core tiles (fewer 128 x 256 tiles than SMs).
+// with tensor-core tiles (at most 1.5e8 tap products M T L).
 //
 //   e[d][t] = sum_{x=0..2H} g[x] |y[d][t - H + x]|,  y = 0 outside [0, T)
 //

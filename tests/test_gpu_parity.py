@@ -197,8 +197,8 @@ def test_generic_envelope_length():
 
 @pytest.mark.parametrize("T,M,taps", [(6001, 1200, None), (6000, 1201, None), (6004, 1200, 33)])
 def test_tensor_core_envelope_ragged_tiles(T, M, taps):
-    """Frames with more 128 x 256 envelope tiles than SMs take the tensor-core
-    FIR (smaller ones the CUDA-core FIR): ragged last row block and time tile,
+    """Frames beyond 1.5e8 tap products (M T L) take the tensor-core FIR
+    (smaller ones the CUDA-core FIR): ragged last row block and time tile,
     T % 4 != 0 (copy fallback) and T % 4 == 0 (TMA), another tap count."""
     sc = hemi(T, M)
     kw = {} if taps is None else {"env_cutoff_hz": 20000.0, "env_taps": taps}
@@ -328,11 +328,11 @@ def test_host_buffers_and_batch_equal_device_path():
     p2.close()
 
 
-def sampled_rows_parity(sc, order, gpu_mode, oracle_mode):
+def sampled_rows_parity(sc, order, gpu_mode, oracle_mode, cf=True):
     """Whole frame on the GPU in the benchmark's launch configuration; blocks
     of 8 rows sampled across the direction range, plus the rows around the
     image peak, compared with the oracle."""
-    plan = gpu_plan(dm, sc, order, gpu_mode)
+    plan = gpu_plan(dm, sc, order, gpu_mode, cf=cf)
     x = torch.from_numpy(sc.frame).cuda()
     y = torch.empty((sc.n_dirs, sc.n_samples), device="cuda")
     img = plan(x, y=y)
@@ -347,7 +347,7 @@ def sampled_rows_parity(sc, order, gpu_mode, oracle_mode):
     tau = scene_tau(sc)
     peak_y = peak_i = err_y = err_i = 0.0
     for b in starts:
-        r = oracle_run(sc, order, oracle_mode, dir_range=(b, b + 8), tau=tau)
+        r = oracle_run(sc, order, oracle_mode, cf=cf, dir_range=(b, b + 8), tau=tau)
         gy, gi = y[b:b + 8].cpu().numpy(), img[b:b + 8].cpu().numpy()
         peak_y = max(peak_y, np.max(np.abs(r["y"])))
         peak_i = max(peak_i, np.max(np.abs(r["img"])))
@@ -368,6 +368,13 @@ def test_full_size_hemisphere_nearest_sampled_rows():
     """The same frame with nearest-sample delays (the persistent kernel: 32768
     work items over 4096 CTAs drawing on one counter)."""
     sampled_rows_parity(scenes.hemi_3d(seed=2), 5, dm.ROUND, oracle.ROUND)
+
+
+def test_full_size_paper_timing_configuration_sampled_rows():
+    """The paper's timing configuration: 1000 azimuths x 163840 samples, n = 5
+    without CF."""
+    sampled_rows_parity(scenes.small_2d(seed=1, n_samples=163840, n_dirs=1000), 5,
+                        dm.ROUND, oracle.ROUND, cf=False)
 
 
 @pytest.mark.parametrize("n_mics,order,mode", [(64, 5, "round"), (64, 3, "linear"),

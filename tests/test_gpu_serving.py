@@ -28,7 +28,7 @@ def test_batch_of_mixed_variants_is_bitwise_equal_to_single_calls():
     a = scenes.small_2d(seed=1, n_samples=1500)
     b = scenes.hemi_3d(seed=2, n_samples=1100, n_dirs=100)
     c = scenes.passive(seed=4, n_mics=40, n_samples=900, n_az=12, n_el=6)
-    # large enough for the tensor-core envelope (more 128 x 256 tiles than SMs)
+    # large enough for the tensor-core envelope (more than 1.5e8 tap products)
     d = scenes.hemi_3d(seed=2, n_samples=4100, n_dirs=1200)
     plans = [
         _plan(a, 5, dm.ROUND), _plan(a, 3, dm.ROUND), _plan(b, 5, dm.LINEAR),

@@ -133,8 +133,9 @@ def _echo_frame(rng, mic_xyz, positions, amps, fs, T, c, f0, sigma, noise_eta):
 
 
 def small_2d(seed: int = 1, n_mics: int = 32, n_samples: int = 4096,
-             n_reflectors: int = 3, snr_db: float = 20.0) -> Scene:
-    """2-D scene: 12 cm disc, 91 azimuths at elevation 0."""
+             n_reflectors: int = 3, snr_db: float = 20.0, n_dirs: int = 91) -> Scene:
+    """2-D scene: 12 cm disc, n_dirs azimuths evenly spaced over -90..90 degrees
+    at elevation 0 (91: every 2 degrees)."""
     rng = np.random.default_rng(seed)
     fs, c = 450e3, SOUND_SPEED
     mic = disc_array(rng, n_mics, 0.06)
@@ -146,8 +147,10 @@ def small_2d(seed: int = 1, n_mics: int = 32, n_samples: int = 4096,
         amps.append(1.0)
     eta = 10.0 ** (-snr_db / 20.0)
     frame = _echo_frame(rng, mic, pos, amps, fs, n_samples, c, 40e3, 50e-6, eta)
+    dirs = azimuth_fan() if n_dirs == 91 else np.stack(
+        [np.deg2rad(np.linspace(-90.0, 90.0, n_dirs)), np.zeros(n_dirs)], axis=1)
     return Scene("small_2d", mic, frame.astype(np.float32), fs, c,
-                 azimuth_fan(), None,
+                 dirs, None,
                  {"seed": seed, "reflectors": np.array(pos), "snr_db": snr_db})
 
 
