@@ -68,6 +68,10 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 using namespace dmas;
 
+// dmas_beamform_host pipelines a large frame in this many time chunks: each
+// chunk's image columns download while the next chunk computes.
+constexpr int kHostChunks = 4;
+
 struct dmas_plan {
     HostPlan hp;
     int device = 0;
@@ -88,6 +92,9 @@ struct dmas_plan {
     bool profiled_once = false;
     bool env_ran = false;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // dmas_beamform_host: the image download stream and one event per chunk
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t chunk_ev[kHostChunks] = {};
 };
 
 namespace {
@@ -134,6 +141,12 @@ void free_plan_memory(dmas_plan *p) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
     }
+    for (auto &e : p->chunk_ev) {
+        if (e) cudaEventDestroy(e);
+        e = nullptr;
+    }
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    p->copy_stream = nullptr;
     p->d_gdir = p->d_gws = p->d_rel = p->d_sel = nullptr;
     p->d_frac = p->d_w4 = nullptr;
     p->d_err = nullptr;
@@ -254,6 +267,7 @@ EnvTcJob env_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned
     j.img = d_image;
     j.M = p->hp.M;
     j.T = p->hp.T;
+    j.tt0 = 0;
     j.t_tiles = (p->hp.T + kTcJ - 1) / kTcJ;
     j.first = first;
     return j;
@@ -279,6 +293,7 @@ EnvFirJob fir_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigne
     j.img = d_image;
     j.M = p->hp.M;
     j.T = p->hp.T;
+    j.tt0 = 0;
     j.t_tiles = (p->hp.T + kFirTile - 1) / kFirTile;
     j.first = first;
     return j;
@@ -352,6 +367,8 @@ BeamParams beam_params(const dmas_plan *p, void *scratch, float *ybuf, float *d_
     bp.mic_chunk = hp.mic_chunk;
     bp.n_groups = hp.n_groups;
     bp.n_tiles = hp.n_tiles;
+    bp.item0 = 0;
+    bp.n_items = (unsigned)((size_t)hp.n_groups * hp.n_tiles);
     bp.n_mics_f = (float)hp.N;
     bp.cf_eps = (float)hp.cf_eps;
     bp.use_cf = (hp.flags & DMAS_F_CF) ? 1 : 0;
@@ -366,20 +383,26 @@ unsigned beam_blocks(const dmas_plan *p) {
 }
 
 // Enqueue the whole path for one frame with the given scratch.
+dmas_status enqueue_roots(dmas_plan *p, const float *d_frame, void *scratch, cudaStream_t s) {
+    const RootsParams rp = roots_params(p, d_frame, scratch);
+    const unsigned rgrid = roots_blocks(p);
+    switch (p->hp.chan_prec) {
+        case DMAS_CH_F16: roots_kernel<__half><<<rgrid, 256, 0, s>>>(rp); break;
+        case DMAS_CH_BF16: roots_kernel<__nv_bfloat16><<<rgrid, 256, 0, s>>>(rp); break;
+        default: roots_kernel<float><<<rgrid, 256, 0, s>>>(rp); break;
+    }
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DMAS_OK : cuda_fail(p, e, "roots_kernel launch");
+}
+
 dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, float *d_y,
                           float *d_cf, void *scratch, cudaStream_t s) {
     const HostPlan &hp = p->hp;
     cudaError_t e;
     mark(p, 0, s);
     // K1: roots
-    const RootsParams rp = roots_params(p, d_frame, scratch);
-    const unsigned rgrid = roots_blocks(p);
-    switch (hp.chan_prec) {
-        case DMAS_CH_F16: roots_kernel<__half><<<rgrid, 256, 0, s>>>(rp); break;
-        case DMAS_CH_BF16: roots_kernel<__nv_bfloat16><<<rgrid, 256, 0, s>>>(rp); break;
-        default: roots_kernel<float><<<rgrid, 256, 0, s>>>(rp); break;
-    }
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(p, e, "roots_kernel launch");
+    dmas_status st = enqueue_roots(p, d_frame, scratch, s);
+    if (st != DMAS_OK) return st;
     mark(p, 1, s);
 
     // K2: beamform into y (the image itself without the envelope)
@@ -428,6 +451,86 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
     if (e != cudaSuccess) return cuda_fail(p, e, "envelope_tc_kernel launch");
     mark(p, 3, s);
     p->env_ran = true;
+    p->profiled_once = p->profiled_once || p->profiling;
+    return DMAS_OK;
+}
+
+// The host-buffer path for one frame, in time chunks: chunk c beamforms the
+// work items of its time tiles (plus the envelope's halo ahead), filters the
+// outputs whose input window is complete, and its image columns download on
+// the copy stream while chunk c + 1 computes.  Small frames run in one chunk.
+dmas_status enqueue_host_chunks(dmas_plan *p, const float *d_frame, float *d_image,
+                                float *h_image, void *scratch, cudaStream_t s) {
+    static_assert(kTcJ == kFirTile, "both envelope kernels tile time by the same length");
+    const HostPlan &hp = p->hp;
+    cudaError_t e;
+    mark(p, 0, s);
+    dmas_status st = enqueue_roots(p, d_frame, scratch, s);
+    if (st != DMAS_OK) return st;
+    mark(p, 1, s);
+    const bool env = hp.L > 0;
+    const int H = env ? (hp.L - 1) / 2 : 0;
+    const int bt = hp.tile;                     // beamform time tile
+    const int n_et = (hp.T + kTcJ - 1) / kTcJ;  // envelope time tiles
+    const int units = env ? n_et : hp.n_tiles;
+    const int K = (units >= 2 * kHostChunks && (size_t)hp.M * hp.T >= ((size_t)1 << 22))
+                      ? kHostChunks : 1;
+    const unsigned G = (unsigned)hp.n_groups;
+    float *ybuf = y_target(p, d_image, nullptr, scratch);
+    const bool fir = env && env_on_cuda_cores(p);
+    int beam_done = 0;
+    for (int c = 0; c < K; ++c) {
+        const int u_lo = units * c / K, u_hi = units * (c + 1) / K;
+        const int unit = env ? kTcJ : bt;
+        const int out_lo = u_lo * unit, out_hi = std::min(hp.T, u_hi * unit);
+        const int need = (c == K - 1) ? hp.n_tiles
+                                      : std::min(hp.n_tiles, (out_hi + H + bt - 1) / bt);
+        if (need > beam_done) {
+            BeamParams bp = beam_params(p, scratch, ybuf, nullptr);
+            bp.item0 = (unsigned)beam_done * G;
+            bp.n_items = (unsigned)(need - beam_done) * G;
+            bp.work = work_counter(p, scratch) + c;
+            e = kBeamLaunchers[hp.order](bp, hp.delay_mode, hp.chan_prec, hp.ng_prec,
+                                         bp.n_items, p->smem_beam, s);
+            if (e != cudaSuccess) return cuda_fail(p, e, "beamform_kernel launch");
+            beam_done = need;
+        }
+        if (env && fir) {
+            EnvFirParams fp{};
+            fp.count = 1;
+            fp.H = H;
+            fp.taps = p->d_taps;
+            fp.job[0] = fir_job(p, ybuf, d_image, 0);
+            fp.job[0].tt0 = u_lo;
+            fp.job[0].t_tiles = u_hi - u_lo;
+            envelope_fir_kernel<<<(unsigned)hp.M * (unsigned)(u_hi - u_lo), kFirTile, 0, s>>>(fp);
+            if ((e = cudaGetLastError()) != cudaSuccess)
+                return cuda_fail(p, e, "envelope_fir_kernel launch");
+        } else if (env) {
+            EnvTcParams ep{};
+            ep.count = 1;
+            ep.job[0] = env_job(p, ybuf, d_image, 0);
+            ep.job[0].tt0 = u_lo;
+            ep.job[0].t_tiles = u_hi - u_lo;
+            ep.total_tiles = (unsigned)((hp.M + kTcRows - 1) / kTcRows) * (unsigned)(u_hi - u_lo);
+            ep.H = H;
+            ep.taps = p->d_taps_tc;
+            ep.err = p->d_err;
+            e = launch_env_tc(ep, std::min<unsigned>(ep.total_tiles, (unsigned)p->num_sms),
+                              p->smem_env, s);
+            if (e != cudaSuccess) return cuda_fail(p, e, "envelope_tc_kernel launch");
+        }
+        if ((e = cudaEventRecord(p->chunk_ev[c], s)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(p->copy_stream, p->chunk_ev[c], 0)) != cudaSuccess ||
+            (e = cudaMemcpy2DAsync(h_image + out_lo, sizeof(float) * hp.T, d_image + out_lo,
+                                   sizeof(float) * hp.T, sizeof(float) * (out_hi - out_lo),
+                                   hp.M, cudaMemcpyDeviceToHost, p->copy_stream)) != cudaSuccess)
+            return cuda_fail(p, e, "image download");
+    }
+    // the stages interleave: the profile shows the whole frame as the beamform
+    mark(p, 2, s);
+    mark(p, 3, s);
+    p->env_ran = false;
     p->profiled_once = p->profiled_once || p->profiling;
     return DMAS_OK;
 }
@@ -690,17 +793,28 @@ dmas_status dmas_beamform_host(dmas_plan *p, const float *h_frame, float *h_imag
         cudaGetLastError();
         return DMAS_ENOMEM;
     }
+    if (!p->copy_stream) {
+        if ((e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking)) !=
+            cudaSuccess) {
+            p->copy_stream = nullptr;
+            return cuda_fail(p, e, "copy stream");
+        }
+        for (auto &ev : p->chunk_ev)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+                ev = nullptr;
+                return cuda_fail(p, e, "chunk events");
+            }
+    }
     p->last_stream = s;
     if ((e = cudaMemcpyAsync(p->d_io_frame, h_frame, fbytes, cudaMemcpyHostToDevice, s)) !=
         cudaSuccess)
         return cuda_fail(p, e, "frame upload");
     dmas_status st =
-        enqueue_frame(p, p->d_io_frame, p->d_io_image, nullptr, nullptr, p->d_scratch, s);
+        enqueue_host_chunks(p, p->d_io_frame, p->d_io_image, h_image, p->d_scratch, s);
     if (st != DMAS_OK) return st;
-    if ((e = cudaMemcpyAsync(h_image, p->d_io_image, ibytes, cudaMemcpyDeviceToHost, s)) !=
-        cudaSuccess)
-        return cuda_fail(p, e, "image download");
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(p, e, "synchronise");
+    if ((e = cudaStreamSynchronize(p->copy_stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_fail(p, e, "synchronise");
     return DMAS_OK;
 }
 

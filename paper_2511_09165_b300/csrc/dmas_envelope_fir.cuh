@@ -19,7 +19,8 @@ struct EnvFirJob {
     const float *y;  // [M][T]
     float *img;      // [M][T]
     int M, T;
-    int t_tiles;     // ceil(T / kFirTile)
+    int tt0;         // first time tile (kFirTile outputs) of this job
+    int t_tiles;     // time tiles of this job (all: ceil(T / kFirTile))
     unsigned first;  // first CTA of this job in the launch
 };
 
@@ -38,7 +39,7 @@ __global__ void __launch_bounds__(kFirTile) envelope_fir_kernel(const __grid_con
     const EnvFirJob &jb = p.job[k];
     const unsigned local = blockIdx.x - jb.first;
     const int row = (int)(local / (unsigned)jb.t_tiles);
-    const int t0 = (int)(local - (unsigned)row * (unsigned)jb.t_tiles) * kFirTile;
+    const int t0 = (jb.tt0 + (int)(local - (unsigned)row * (unsigned)jb.t_tiles)) * kFirTile;
     const int H = p.H, L = 2 * H + 1;
     const float *yrow = jb.y + (size_t)row * jb.T;
     for (int i = threadIdx.x; i < L; i += kFirTile) s_h[i] = p.taps[i];

@@ -67,7 +67,8 @@ struct EnvTcJob {
     const float *y;   // [M][T]
     float *img;       // [M][T]
     int M, T;
-    int t_tiles;      // ceil(T / kTcJ)
+    int tt0;          // first time tile (kTcJ outputs) of this job
+    int t_tiles;      // time tiles of this job (all: ceil(T / kTcJ))
     int use_tma;      // T % 4 == 0 and the map was encoded
     unsigned first;   // first tile of this job in the launch
 };
@@ -184,7 +185,7 @@ __device__ __forceinline__ TcTile tc_tile(const EnvTcParams &p, unsigned tile) {
     const unsigned local = tile - jb.first;
     const int rb = (int)(local / (unsigned)jb.t_tiles);
     const int tt = (int)(local - (unsigned)rb * (unsigned)jb.t_tiles);
-    return {&jb, rb * kTcRows, tt * kTcJ};
+    return {&jb, rb * kTcRows, (jb.tt0 + tt) * kTcJ};
 }
 
 // Warp roles: 0-3 split (one row each), 4-7 epilogue (TMEM lane quarters),

@@ -32,6 +32,7 @@ constexpr int kThreads = 256;      // 8 warps, one direction each
 constexpr int kPix = 8;            // output samples per lane (kTimeTile / 32)
 constexpr int kTimeTileDev = 32 * kPix;  // output samples per work item
 constexpr unsigned kErrTimeout = 1u;
+constexpr unsigned kWorkSlots = 64;  // beamform work counters per frame (one per launch)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
 // ---------------------------------------------------------------------------
@@ -130,7 +131,7 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_ch<__nv_bfloat16>(float 
 struct RootsParams {
     const float *frame;  // [N][T]
     void *chan;          // [N][row] CH, then (shifted != 0) [N][row] shifted by one sample
-    unsigned *work;      // the beamform launch's work counter: set to zero
+    unsigned *work;      // the frame's beamform work counters [kWorkSlots]: set to zero
     int N, T, row, padl, order;
     int shifted;         // also write chan1[i][c] = chan0[i][c + 1] after the first block
     float inv_order;
@@ -149,7 +150,7 @@ template <typename CH>
 __device__ __forceinline__ void roots_body(const RootsParams &p, size_t first, size_t stride) {
     const size_t total = (size_t)p.N * (size_t)p.row;
     CH *chan = reinterpret_cast<CH *>(p.chan);
-    if (first == 0 && p.work) *p.work = 0u;
+    if (first < kWorkSlots && p.work) p.work[first] = 0u;
     for (size_t idx = first; idx < total; idx += stride) {
         const int i = (int)(idx / (size_t)p.row);
         const int c = (int)(idx - (size_t)i * p.row);
@@ -333,12 +334,14 @@ struct BeamParams {
     float *cf;           // [M][T] or nullptr
     unsigned *err;       // error word
     int N, T, row, padl, window, mic_chunk, n_groups, n_tiles;
+    unsigned item0;      // first work item (time tile x n_groups + group) of this launch
+    unsigned n_items;    // work items of this launch
     float n_mics_f, cf_eps;
     int use_cf;
     int pairs;           // pair kernel: pixel pairs per lane (time tile 64 * pairs)
     int stage_bytes;     // persistent pair kernel: bytes of one staging buffer (same for a
                          // whole launch)
-    unsigned *work;      // persistent pair kernel: the launch's work counter, zero at launch
+    unsigned *work;      // persistent pair kernel: this launch's work counter, zero at launch
 };
 
 // Running sums per pixel: P_1..P_n, sum x, sum x^2, where for odd n
@@ -380,8 +383,9 @@ __device__ __forceinline__ void beamform_body(const BeamParams &p, unsigned bloc
     int *s_rel = reinterpret_cast<int *>(smem + 128 + win_bytes);
     float *s_frac = reinterpret_cast<float *>(s_rel + NC * 8);
 
-    const int tile = (int)(block / (unsigned)p.n_groups);
-    const int g = (int)(block - (unsigned)tile * (unsigned)p.n_groups);
+    const unsigned item = block + p.item0;
+    const int tile = (int)(item / (unsigned)p.n_groups);
+    const int g = (int)(item - (unsigned)tile * (unsigned)p.n_groups);
     const int t0 = tile * (32 * kPix);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -603,8 +607,9 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
     // per-lane partial sums of the sample past the tile: [warp][q][lane]
     float *s_vext = s_w4 + NC * 32 + ((threadIdx.x >> 5) * NA * 32 + (threadIdx.x & 31));
 
-    const int tile = (int)(block / (unsigned)p.n_groups);
-    const int g = (int)(block - (unsigned)tile * (unsigned)p.n_groups);
+    const unsigned item = block + p.item0;
+    const int tile = (int)(item / (unsigned)p.n_groups);
+    const int g = (int)(item - (unsigned)tile * (unsigned)p.n_groups);
     const int t0 = tile * kTile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -759,7 +764,7 @@ constexpr int kPersistItems = 8;  // work items per CTA of the persistent kernel
 
 struct OneFrame {
     const BeamParams &p;
-    __device__ unsigned total() const { return (unsigned)p.n_groups * (unsigned)p.n_tiles; }
+    __device__ unsigned total() const { return p.n_items; }
     __device__ int entry(unsigned) const { return 0; }
     __device__ const BeamParams &par(int) const { return p; }
     __device__ unsigned first(int) const { return 0; }
@@ -831,7 +836,7 @@ __device__ __forceinline__ void beamform_x2_run(const Src &src) {
         }
         const int e = src.entry(uu);
         const BeamParams &q = src.par(e);
-        const unsigned loc = uu - src.first(e);
+        const unsigned loc = uu - src.first(e) + q.item0;
         const int tile = (int)(loc / (unsigned)q.n_groups);
         const int g = (int)(loc - (unsigned)tile * (unsigned)q.n_groups);
         const int nc = min(q.mic_chunk, q.N - cc);
@@ -894,7 +899,7 @@ __device__ __forceinline__ void beamform_x2_run(const Src &src) {
         const int c0 = st_c0[bf];
         const int e = src.entry(u);
         const BeamParams &p = src.par(e);
-        const unsigned loc = u - src.first(e);
+        const unsigned loc = u - src.first(e) + p.item0;
         const int tile = (int)(loc / (unsigned)p.n_groups);
         const int g = (int)(loc - (unsigned)tile * (unsigned)p.n_groups);
         const int t0 = tile * kTile;

@@ -358,6 +358,25 @@ def sampled_rows_parity(sc, order, gpu_mode, oracle_mode, cf=True):
     assert err_i <= TOL_F32 * peak_i, err_i / peak_i
 
 
+@pytest.mark.parametrize("mode,kw,M", [
+    ("linear", {}, 2048),                          # tensor-core envelope
+    ("round", {"envelope": False}, 2048),          # image = E_n x CF
+    ("round", {"env_taps": 31}, 256),              # CUDA-core envelope
+])
+def test_host_path_in_time_chunks_equals_device_path(mode, kw, M):
+    """dmas_beamform_host runs a large frame in time chunks whose image columns
+    download while the next chunk computes; the image is bitwise the device
+    path's."""
+    sc = scenes.hemi_3d(seed=2, n_dirs=M)
+    plan = gpu_plan(dm, sc, 5, dm.LINEAR if mode == "linear" else dm.ROUND, **kw)
+    x = torch.from_numpy(sc.frame).cuda()
+    ref = plan(x).cpu().numpy()
+    got = plan.beamform_host(sc.frame)
+    plan.check()
+    plan.close()
+    assert np.array_equal(got, ref)
+
+
 def test_full_size_hemisphere_sampled_rows():
     """The timed workload: 2048 directions x 16384 samples, linear delays,
     n = 5, CF, envelope."""
