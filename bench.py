@@ -493,9 +493,9 @@ def run_serving(args) -> None:
 
 # ---------------------------------------------------------------------------
 # direction sweep: frame time against the number of directions (the paper's
-# Fig. 7 shape), 2-D fan, 16384 samples, n=5 with CF
+# Fig. 7b setting: 163840 samples, DMAS5-CF, its direction counts), 2-D fan
 # ---------------------------------------------------------------------------
-SWEEP_DIRS = [2, 10, 50, 100, 250, 500, 1000, 2000, 4000]
+SWEEP_DIRS = [2, 10, 100, 200, 500, 1000, 2000, 3000, 4000]   # the paper's counts
 
 
 def run_sweep(args) -> None:
@@ -513,7 +513,7 @@ def run_sweep(args) -> None:
     wall0 = time.time()
     rows = []
     for M in SWEEP_DIRS:
-        sc = scenes.small_2d(seed=1, n_samples=16384, n_dirs=M)
+        sc = scenes.small_2d(seed=1, n_samples=163840, n_dirs=M)
         plan = dm.Plan(mic_xyz=sc.mic_xyz, dir_azel=sc.dir_azel, n_samples=sc.n_samples,
                        fs=sc.fs, c=sc.c, order=5, delay_mode=dm.ROUND)
         frame = torch.from_numpy(sc.frame).to(dev)
@@ -544,12 +544,56 @@ def run_sweep(args) -> None:
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "sweep", "description":
-                   "2-D fan (32 mics, 12 cm disc), 16384 samples at 450 kHz, n=5 with CF, "
+                   "2-D fan (32 mics, 12 cm disc), 163840 samples at 450 kHz, n=5 with CF, "
                    "nearest-sample delays, envelope; frame time per direction count "
                    "(median of CUDA-event steps, L2 flushed before each)",
                    "n_dirs": SWEEP_DIRS},
         "sweep": rows,
         "clocks": clocks.summary(wall0, wall1),
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# image SNR against microphone SNR (the paper's Sec. IV-A experiment, Table I)
+# ---------------------------------------------------------------------------
+IMAGE_SNR_MIC_DB = [-40.0, -30.0, -20.0, -10.0, 0.0, 10.0]
+
+
+def run_image_snr(args) -> None:
+    import torch
+    import paper_2511_09165_b300 as dm
+    from workloads import image_quality as iq
+
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    rows = []
+    for snr in IMAGE_SNR_MIC_DB:
+        sc = scenes.point_target(snr)
+        off = iq.off_target_mask(sc.dir_azel[:, 0], sc.n_samples, sc.fs, sc.c, 0.0, 1.0)
+        x = torch.from_numpy(sc.frame).cuda()
+        row = {"snr_mic_db": snr}
+        for n in (1, 2, 3, 4, 5):
+            for cf in (False, True):
+                plan = dm.Plan(mic_xyz=sc.mic_xyz, dir_azel=sc.dir_azel, n_samples=sc.n_samples,
+                               fs=sc.fs, c=sc.c, order=n, delay_mode=dm.LINEAR, cf=cf)
+                img = plan(x).cpu().numpy()
+                plan.check()
+                plan.close()
+                key = ("dmas%d" % n if n > 1 else "das") + ("_cf" if cf else "")
+                row[key] = round(iq.image_snr_db(img, off), 2)
+        rows.append(row)
+    print(json.dumps({
+        "metric": "image SNR (dB) against microphone SNR", "unit": "dB", "n_gpus": 1,
+        "data": "synthetic",
+        "config": {"workload": "image_snr", "description":
+                   "one reflector at broadside, 1 m, echo amplitude 1 at the 32 mics "
+                   "(12 cm disc), white noise eta = 10^(-SNR/20), 181 azimuths x 2048 "
+                   "samples, linear delays, 181-tap envelope; image normalised to max 1, "
+                   "SNR_image = 20 log10(1 / mean off-target level), target window "
+                   "+-10 deg x +-0.15 m"},
+        "table": rows,
     }), flush=True)
 
 
@@ -559,7 +603,7 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving", "sweep"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving", "sweep", "image_snr"],
                     default="hemi_3d_n5")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 1000.0])
     ap.add_argument("--serve-seconds", type=float, default=5.0)
@@ -574,6 +618,13 @@ def main() -> None:
                               "the serving workload has no CPU reference arm"}))
             return
         run_serving(args)
+        return
+    if args.workload == "image_snr":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the image-SNR experiment has no CPU reference arm"}))
+            return
+        run_image_snr(args)
         return
     if args.workload == "sweep":
         if args.impl == "reference":

@@ -1,0 +1,35 @@
+"""Image-quality measures of an acoustic image (post-processing only).
+
+The image SNR follows the paper's simulation analysis (Sec. IV-A, Table I):
+the image is normalised to a maximum of one, E_off is the mean over the
+off-target pixels, and SNR_image = 20 log10(1 / E_off).  Which pixels count
+as on target is not stated there; here it is the window within max_az_deg of
+the target's azimuth and within max_range_m of its range (one-way range
+c t).  The peak-to-sidelobe ratio is 20 log10(1 / max over the same
+off-target pixels) of the normalised image.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def off_target_mask(az_rad: np.ndarray, n_samples: int, fs: float, c: float,
+                    target_az_rad: float, target_range_m: float,
+                    max_az_deg: float = 10.0, max_range_m: float = 0.15) -> np.ndarray:
+    """Boolean [M][T]: True for pixels outside the target window."""
+    az_off = np.abs(np.degrees(az_rad - target_az_rad)) > max_az_deg
+    rng = c * np.arange(n_samples) / fs
+    r_off = np.abs(rng - target_range_m) > max_range_m
+    return az_off[:, None] | r_off[None, :]
+
+
+def image_snr_db(image: np.ndarray, off: np.ndarray) -> float:
+    img = np.abs(np.asarray(image, dtype=np.float64))
+    img = img / img.max()
+    return float(20.0 * np.log10(1.0 / img[off].mean()))
+
+
+def peak_sidelobe_db(image: np.ndarray, off: np.ndarray) -> float:
+    img = np.abs(np.asarray(image, dtype=np.float64))
+    img = img / img.max()
+    return float(20.0 * np.log10(1.0 / img[off].max()))
