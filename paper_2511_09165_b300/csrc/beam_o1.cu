@@ -5,6 +5,6 @@
 namespace dmas {
 template cudaError_t launch_beamform_order<1>(const BeamParams &, int, int, int, unsigned,
                                                size_t, cudaStream_t);
-template cudaError_t launch_beamform_batch_order<1>(const BeamBatch &, int, int, int, int,
+template cudaError_t launch_beamform_batch_order<1>(const BeamBatch &, int, int, int,
                                                      unsigned, size_t, cudaStream_t);
 }  // namespace dmas

@@ -34,21 +34,21 @@ extern template cudaError_t launch_beamform_order<8>(const BeamParams &, int, in
                                                      size_t, cudaStream_t);
 
 extern template cudaError_t launch_beamform_batch_order<1>(const BeamBatch &, int, int, int,
-                                                           int, unsigned, size_t, cudaStream_t);
+                                                           unsigned, size_t, cudaStream_t);
 extern template cudaError_t launch_beamform_batch_order<2>(const BeamBatch &, int, int, int,
-                                                           int, unsigned, size_t, cudaStream_t);
+                                                           unsigned, size_t, cudaStream_t);
 extern template cudaError_t launch_beamform_batch_order<3>(const BeamBatch &, int, int, int,
-                                                           int, unsigned, size_t, cudaStream_t);
+                                                           unsigned, size_t, cudaStream_t);
 extern template cudaError_t launch_beamform_batch_order<4>(const BeamBatch &, int, int, int,
-                                                           int, unsigned, size_t, cudaStream_t);
+                                                           unsigned, size_t, cudaStream_t);
 extern template cudaError_t launch_beamform_batch_order<5>(const BeamBatch &, int, int, int,
-                                                           int, unsigned, size_t, cudaStream_t);
+                                                           unsigned, size_t, cudaStream_t);
 extern template cudaError_t launch_beamform_batch_order<6>(const BeamBatch &, int, int, int,
-                                                           int, unsigned, size_t, cudaStream_t);
+                                                           unsigned, size_t, cudaStream_t);
 extern template cudaError_t launch_beamform_batch_order<7>(const BeamBatch &, int, int, int,
-                                                           int, unsigned, size_t, cudaStream_t);
+                                                           unsigned, size_t, cudaStream_t);
 extern template cudaError_t launch_beamform_batch_order<8>(const BeamBatch &, int, int, int,
-                                                           int, unsigned, size_t, cudaStream_t);
+                                                           unsigned, size_t, cudaStream_t);
 
 static const BeamBatchLauncher kBeamBatchLaunchers[9] = {
     nullptr,
@@ -603,8 +603,8 @@ dmas_status enqueue_batch(const std::vector<BatchEntry> &v, cudaStream_t s) {
                 for (int k = 0; k < bb.count; ++k) bb.e[k].stage_bytes = sb;
                 smem = 128 + 2 * (size_t)sb;
             }
-            e = kBeamBatchLaunchers[a.order](bb, a.delay_mode, a.chan_prec, a.ng_prec, a.pairs,
-                                             blocks, smem, s);
+            e = kBeamBatchLaunchers[a.order](bb, a.delay_mode, a.chan_prec, a.ng_prec, blocks,
+                                             smem, s);
             if (e != cudaSuccess) return cuda_fail(v[cls[b0]].plan, e, "beamform batch");
         }
     }

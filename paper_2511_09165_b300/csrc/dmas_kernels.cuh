@@ -29,8 +29,7 @@
 namespace dmas {
 
 constexpr int kThreads = 256;      // 8 warps, one direction each
-constexpr int kPix = 8;            // output samples per lane (kTimeTile / 32)
-constexpr int kTimeTileDev = 32 * kPix;  // output samples per work item
+constexpr int kPix = 8;            // scalar kernel: output samples per lane (tile 32 x kPix)
 constexpr unsigned kErrTimeout = 1u;
 constexpr unsigned kWorkSlots = 64;  // beamform work counters per frame (one per launch)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s

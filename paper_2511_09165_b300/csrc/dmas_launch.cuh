@@ -123,7 +123,7 @@ using BeamLauncher = cudaError_t (*)(const BeamParams &, int, int, int, unsigned
 
 // Batched launch of one kernel variant over up to kBatchMax entries.
 template <int ORDER, bool LINEAR, typename CH, int NGP>
-cudaError_t launch_beam_batch_variant(const BeamBatch &b, int pairs, unsigned grid, size_t smem,
+cudaError_t launch_beam_batch_variant(const BeamBatch &b, unsigned grid, size_t smem,
                                       cudaStream_t s) {
     if constexpr (std::is_same<CH, float>::value && ORDER <= kPairMaxOrder) {
         static std::once_flag once;
@@ -143,38 +143,38 @@ cudaError_t launch_beam_batch_variant(const BeamBatch &b, int pairs, unsigned gr
 }
 
 template <int ORDER, bool LINEAR, typename CH>
-cudaError_t launch_beam_batch_ng(const BeamBatch &b, int ngp, int pairs, unsigned grid,
+cudaError_t launch_beam_batch_ng(const BeamBatch &b, int ngp, unsigned grid,
                                  size_t smem, cudaStream_t s) {
     switch (ngp) {
         case NG_F64:
-            return launch_beam_batch_variant<ORDER, LINEAR, CH, NG_F64>(b, pairs, grid, smem, s);
+            return launch_beam_batch_variant<ORDER, LINEAR, CH, NG_F64>(b, grid, smem, s);
         case NG_CF32:
-            return launch_beam_batch_variant<ORDER, LINEAR, CH, NG_CF32>(b, pairs, grid, smem, s);
+            return launch_beam_batch_variant<ORDER, LINEAR, CH, NG_CF32>(b, grid, smem, s);
         default:
-            return launch_beam_batch_variant<ORDER, LINEAR, CH, NG_F32>(b, pairs, grid, smem, s);
+            return launch_beam_batch_variant<ORDER, LINEAR, CH, NG_F32>(b, grid, smem, s);
     }
 }
 
 template <int ORDER>
 cudaError_t launch_beamform_batch_order(const BeamBatch &b, int linear, int chan, int ngp,
-                                        int pairs, unsigned grid, size_t smem, cudaStream_t s) {
+                                        unsigned grid, size_t smem, cudaStream_t s) {
     if (linear) {
         switch (chan) {
-            case 1: return launch_beam_batch_ng<ORDER, true, __half>(b, ngp, pairs, grid, smem, s);
+            case 1: return launch_beam_batch_ng<ORDER, true, __half>(b, ngp, grid, smem, s);
             case 2:
-                return launch_beam_batch_ng<ORDER, true, __nv_bfloat16>(b, ngp, pairs, grid, smem, s);
-            default: return launch_beam_batch_ng<ORDER, true, float>(b, ngp, pairs, grid, smem, s);
+                return launch_beam_batch_ng<ORDER, true, __nv_bfloat16>(b, ngp, grid, smem, s);
+            default: return launch_beam_batch_ng<ORDER, true, float>(b, ngp, grid, smem, s);
         }
     }
     switch (chan) {
-        case 1: return launch_beam_batch_ng<ORDER, false, __half>(b, ngp, pairs, grid, smem, s);
+        case 1: return launch_beam_batch_ng<ORDER, false, __half>(b, ngp, grid, smem, s);
         case 2:
-            return launch_beam_batch_ng<ORDER, false, __nv_bfloat16>(b, ngp, pairs, grid, smem, s);
-        default: return launch_beam_batch_ng<ORDER, false, float>(b, ngp, pairs, grid, smem, s);
+            return launch_beam_batch_ng<ORDER, false, __nv_bfloat16>(b, ngp, grid, smem, s);
+        default: return launch_beam_batch_ng<ORDER, false, float>(b, ngp, grid, smem, s);
     }
 }
 
-using BeamBatchLauncher = cudaError_t (*)(const BeamBatch &, int, int, int, int, unsigned, size_t,
+using BeamBatchLauncher = cudaError_t (*)(const BeamBatch &, int, int, int, unsigned, size_t,
                                           cudaStream_t);
 
 }  // namespace dmas
