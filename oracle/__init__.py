@@ -22,6 +22,12 @@ Parity status of each function (what pins it is in tests/test_oracle_pins.py):
                                                 the authors' envelope is unpinned
   dmas                                          pinned (n = 1 DAS, n = 2 Eq. dmas,
                                                 brute force, closed forms, invariants)
+  matched_filter                                pinned (impulse response = the emitted
+                                                signal reversed, numpy.correlate,
+                                                linearity, frame end); the authors'
+                                                emitted signal and alignment are not
+                                                given, so agreement with their
+                                                matched filter is unpinned
 """
 from __future__ import annotations
 
@@ -84,6 +90,8 @@ def _load():
         lib.oracle_fir_taps.restype = i
         lib.oracle_envelope.argtypes = [i, p, i, p, p]
         lib.oracle_envelope.restype = None
+        lib.oracle_matched_filter.argtypes = [i, i, p, i, p, p]
+        lib.oracle_matched_filter.restype = None
         lib.oracle_dmas.argtypes = [i, i, p, i, p, d, i, i, i, d, i, p, i, i, p, p, p]
         lib.oracle_dmas.restype = i
         lib.oracle_linear_esym_ld.argtypes = [i, i, p, p, d, i, i]
@@ -177,6 +185,19 @@ def envelope(y, h) -> np.ndarray:
         rout = np.empty_like(rin)
         _load().oracle_envelope(rin.size, _ptr(rin), h.size, _ptr(h), _ptr(rout))
         rows_out[k] = rout
+    return out
+
+
+def matched_filter(frame, e) -> np.ndarray:
+    """Each row of frame [N][T] correlated with the emitted signal e [L]:
+    out[i][t] = sum_k e[k] frame[i][t + k], zero past the frame end."""
+    frame = _f64(frame)
+    e = _f64(e)
+    if frame.ndim != 2 or e.ndim != 1 or e.size < 1:
+        raise ValueError("frame must be [N][T] and e a non-empty vector")
+    out = np.empty_like(frame)
+    _load().oracle_matched_filter(frame.shape[0], frame.shape[1], _ptr(frame), e.size, _ptr(e),
+                                  _ptr(out))
     return out
 
 

@@ -33,6 +33,10 @@
  *   envelope     |y| low-pass filtered along t: a zero-phase windowed-sinc
  *                FIR (Hamming window), zero padded at the frame ends
  *                (Sec. II step 3; 5 kHz cutoff in Sec. III-B).
+ *   matched      optional, before everything above (Sec. II step 1): each
+ *   filter       microphone signal correlated with the emitted signal e,
+ *                mf_i(t) = sum_{k=0}^{L-1} e[k] m_i(t + k), m = 0 outside the
+ *                frame, so an echo arriving at t0 peaks at t0.
  *
  * Compile: gcc -O2 -fopenmp -ffp-contract=off -shared -fPIC (no fast-math).
  */
@@ -223,6 +227,21 @@ void oracle_envelope(int T, const double *y, int L, const double *h, double *env
             acc += h[k + H] * fabs(y[s]);
         }
         env[t] = acc;
+    }
+}
+
+/* mf[i][t] = sum_{k=0}^{L-1} e[k] frame[i][t + k], frame taken as zero past T. */
+void oracle_matched_filter(int N, int T, const double *frame, int L, const double *e,
+                           double *mf)
+{
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < N; ++i) {
+        const double *m = frame + (size_t)i * T;
+        for (int t = 0; t < T; ++t) {
+            double acc = 0.0;
+            for (int k = 0; k < L && t + k < T; ++k) acc += e[k] * m[t + k];
+            mf[(size_t)i * T + t] = acc;
+        }
     }
 }
 

@@ -403,3 +403,54 @@ def test_dmas_envelope_matches_separate_envelope():
     h = oracle.fir_taps(1000.0, 40.0, 15)
     out = oracle.dmas(frame, tau, fs, 3, use_cf=True, taps=h)
     np.testing.assert_allclose(out["img"], oracle.envelope(out["y"], h), rtol=0, atol=0)
+
+
+# ---------------------------------------------------------------------------
+# matched filter (Sec. II step 1): mf[t] = sum_k e[k] m[t + k]
+# ---------------------------------------------------------------------------
+def test_matched_filter_impulse_response_is_the_reversed_signal():
+    rng = np.random.default_rng(31)
+    e = rng.standard_normal(37)
+    T, t0 = 200, 120
+    frame = np.zeros((1, T))
+    frame[0, t0] = 1.0
+    mf = oracle.matched_filter(frame, e)[0]
+    want = np.zeros(T)
+    for t in range(t0 - e.size + 1, t0 + 1):
+        want[t] = e[t0 - t]
+    assert np.array_equal(mf, want)
+
+
+def test_matched_filter_equals_numpy_correlate():
+    rng = np.random.default_rng(32)
+    frame = rng.standard_normal((3, 500))
+    e = rng.standard_normal(61)
+    mf = oracle.matched_filter(frame, e)
+    for i in range(3):
+        full = np.correlate(frame[i], e, "full")
+        assert np.allclose(mf[i], full[e.size - 1:e.size - 1 + frame.shape[1]],
+                           rtol=1e-12, atol=1e-12)
+
+
+def test_matched_filter_linear_and_zero_past_the_frame():
+    rng = np.random.default_rng(33)
+    a, b = rng.standard_normal((2, 1, 300))
+    e = rng.standard_normal(45)
+    lhs = oracle.matched_filter(2.0 * a - 0.5 * b, e)
+    rhs = 2.0 * oracle.matched_filter(a, e) - 0.5 * oracle.matched_filter(b, e)
+    assert np.allclose(lhs, rhs, rtol=1e-12, atol=1e-12)
+    mf = oracle.matched_filter(a, e)[0]
+    assert mf[-1] == e[0] * a[0, -1]
+    assert np.isclose(mf[-3], e[0] * a[0, -3] + e[1] * a[0, -2] + e[2] * a[0, -1], rtol=1e-14)
+
+
+def test_matched_filter_compresses_the_chirp_echo():
+    """A chirp echo arriving at t0 peaks at t0 after the matched filter."""
+    fs = 450e3
+    e = scenes.lfm_chirp(fs)
+    T, t0 = 4096, 1500
+    frame = np.zeros((1, T))
+    frame[0, t0:t0 + e.size] = e
+    mf = oracle.matched_filter(frame, e)[0]
+    assert int(np.argmax(mf)) == t0
+    assert np.isclose(mf[t0], float(np.sum(e * e)), rtol=1e-12)

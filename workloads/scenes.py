@@ -118,7 +118,22 @@ def _point(az: float, el: float, rng_m: float) -> np.ndarray:
 # --------------------------------------------------------------------------
 # signals
 # --------------------------------------------------------------------------
-def _echo_frame(rng, mic_xyz, positions, amps, fs, T, c, f0, sigma, noise_eta):
+def lfm_chirp(fs: float, f0: float = 25e3, f1: float = 50e3, duration: float = 2.5e-3,
+              tau=None) -> np.ndarray:
+    """Linear FM chirp sin(2 pi (f0 tau + (f1 - f0) tau^2 / (2 D))) for 0 <= tau < D,
+    zero elsewhere; sampled at k / fs (k < round(D fs)) when tau is None.  The
+    defaults are the eRTIS call: 2.5 ms from 25 to 50 kHz."""
+    if tau is None:
+        tau = np.arange(int(round(duration * fs))) / fs
+    tau = np.asarray(tau, dtype=np.float64)
+    phase = 2.0 * np.pi * (f0 * tau + 0.5 * (f1 - f0) / duration * tau * tau)
+    return np.where((tau >= 0.0) & (tau < duration), np.sin(phase), 0.0)
+
+
+def _echo_frame(rng, mic_xyz, positions, amps, fs, T, c, f0, sigma, noise_eta, pulse="tone"):
+    """Echo of each point at one-way delay d/c, amplitude a/d: the Gaussian-
+    windowed tone at f0 (pulse "tone") or the eRTIS chirp (pulse "chirp",
+    evaluated at the exact delayed time)."""
     N = mic_xyz.shape[0]
     t = np.arange(T) / fs
     sig = np.zeros((N, T))
@@ -126,16 +141,21 @@ def _echo_frame(rng, mic_xyz, positions, amps, fs, T, c, f0, sigma, noise_eta):
         d = np.linalg.norm(mic_xyz - p[None, :], axis=1)
         for i in range(N):
             tt = t - d[i] / c
-            sig[i] += a / d[i] * np.exp(-tt * tt / (2.0 * sigma * sigma)) * \
-                np.cos(2.0 * np.pi * f0 * tt)
+            if pulse == "chirp":
+                sig[i] += a / d[i] * lfm_chirp(fs, tau=tt)
+            else:
+                sig[i] += a / d[i] * np.exp(-tt * tt / (2.0 * sigma * sigma)) * \
+                    np.cos(2.0 * np.pi * f0 * tt)
     sig += noise_eta * rng.standard_normal((N, T))
     return sig
 
 
 def small_2d(seed: int = 1, n_mics: int = 32, n_samples: int = 4096,
-             n_reflectors: int = 3, snr_db: float = 20.0, n_dirs: int = 91) -> Scene:
+             n_reflectors: int = 3, snr_db: float = 20.0, n_dirs: int = 91,
+             pulse: str = "tone") -> Scene:
     """2-D scene: 12 cm disc, n_dirs azimuths evenly spaced over -90..90 degrees
-    at elevation 0 (91: every 2 degrees)."""
+    at elevation 0 (91: every 2 degrees); echoes of the Gaussian tone or, with
+    pulse="chirp", of the eRTIS chirp."""
     rng = np.random.default_rng(seed)
     fs, c = 450e3, SOUND_SPEED
     mic = disc_array(rng, n_mics, 0.06)
@@ -146,7 +166,7 @@ def small_2d(seed: int = 1, n_mics: int = 32, n_samples: int = 4096,
         pos.append(_point(az, 0.0, rg))
         amps.append(1.0)
     eta = 10.0 ** (-snr_db / 20.0)
-    frame = _echo_frame(rng, mic, pos, amps, fs, n_samples, c, 40e3, 50e-6, eta)
+    frame = _echo_frame(rng, mic, pos, amps, fs, n_samples, c, 40e3, 50e-6, eta, pulse)
     dirs = azimuth_fan() if n_dirs == 91 else np.stack(
         [np.deg2rad(np.linspace(-90.0, 90.0, n_dirs)), np.zeros(n_dirs)], axis=1)
     return Scene("small_2d", mic, frame.astype(np.float32), fs, c,
@@ -174,7 +194,8 @@ def point_target(snr_db: float, seed: int = 11, n_samples: int = 2048,
 
 
 def hemi_3d(seed: int = 2, n_samples: int = 16384, n_dirs: int = 2048,
-            n_reflectors: int = 8, snr_db: float = 10.0, array_seed: int = 1) -> Scene:
+            n_reflectors: int = 8, snr_db: float = 10.0, array_seed: int = 1,
+            pulse: str = "tone") -> Scene:
     """3-D scene: the small_2d array, Fibonacci hemisphere of directions."""
     mic = disc_array(np.random.default_rng(array_seed), 32, 0.06)
     rng = np.random.default_rng(seed)
@@ -189,7 +210,7 @@ def hemi_3d(seed: int = 2, n_samples: int = 16384, n_dirs: int = 2048,
         pos.append(rg * u)
         amps.append(10.0 ** (-2.0 * rng.random()))
     eta = 10.0 ** (-snr_db / 20.0)
-    frame = _echo_frame(rng, mic, pos, amps, fs, n_samples, c, 40e3, 50e-6, eta)
+    frame = _echo_frame(rng, mic, pos, amps, fs, n_samples, c, 40e3, 50e-6, eta, pulse)
     return Scene("hemi_3d", mic, frame.astype(np.float32), fs, c, None,
                  fibonacci_hemisphere(n_dirs),
                  {"seed": seed, "reflectors": np.array(pos), "amps": np.array(amps),
