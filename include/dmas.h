@@ -108,6 +108,13 @@ typedef struct {
     int env_taps;             /* odd FIR length <= 1023; 0 selects 2*ceil(fs/fc)+1 */
     int chan_prec;            /* dmas_chan_prec */
     int ng_prec;              /* dmas_ng_prec */
+    /* Optional matched filter (Sec. II step 1, pulse compression): the emitted
+     * signal e[0..mf_len-1] at fs.  Each microphone signal is replaced by its
+     * correlation with e, mf_i(t) = sum_k e[k] m_i(t + k) (zero past the frame
+     * end, so an echo peaks at its arrival time), before the roots.  NULL and
+     * 0 turn it off; otherwise 1 <= mf_len <= 8192 and every value finite. */
+    const float *mf_signal;
+    int mf_len;
 } dmas_plan_desc;
 
 /* Read-only summary of a plan. */

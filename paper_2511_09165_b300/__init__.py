@@ -58,6 +58,7 @@ class PlanDesc(ctypes.Structure):
         ("order", ctypes.c_int), ("delay_mode", ctypes.c_int), ("flags", ctypes.c_int),
         ("cf_eps", ctypes.c_double), ("env_cutoff_hz", ctypes.c_double),
         ("env_taps", ctypes.c_int), ("chan_prec", ctypes.c_int), ("ng_prec", ctypes.c_int),
+        ("mf_signal", ctypes.c_void_p), ("mf_len", ctypes.c_int),
     ]
 
 
@@ -171,7 +172,7 @@ class Plan:
                  c: float = 343.0, delay_mode: int = ROUND, cf: bool = True,
                  envelope: bool = True, cf_eps: float = 1e-30,
                  env_cutoff_hz: float = 5000.0, env_taps: int = 0,
-                 chan_prec: int = CH_F32, ng_prec: int = NG_F32):
+                 chan_prec: int = CH_F32, ng_prec: int = NG_F32, mf_signal=None):
         xyz, azel, unit, dly = _f64(mic_xyz), _f64(dir_azel), _f64(dir_unit), _f64(delays_s)
         if dly is not None:
             M, N = dly.shape
@@ -189,10 +190,11 @@ class Plan:
         self._lib = lib
         self._h = ctypes.c_void_p()
         flags = (F_CF if cf else 0) | (F_ENVELOPE if envelope else 0)
+        mf = None if mf_signal is None else np.ascontiguousarray(mf_signal, dtype=np.float32)
         d = PlanDesc(int(N), _np_ptr(xyz), int(M), _np_ptr(azel), _np_ptr(unit), _np_ptr(dly),
                      int(n_samples), float(fs), float(c), int(order), int(delay_mode), flags,
                      float(cf_eps), float(env_cutoff_hz), int(env_taps), int(chan_prec),
-                     int(ng_prec))
+                     int(ng_prec), _np_ptr(mf), 0 if mf is None else int(mf.size))
         st = lib.dmas_plan_create(ctypes.byref(d), ctypes.byref(self._h))
         if st != 0:
             self._h = None

@@ -12,6 +12,7 @@
 #include "dmas.h"
 #include "dmas_internal.h"
 #include "dmas_envelope_fir.cuh"
+#include "dmas_mf.cuh"
 #include "dmas_envelope_tc.cuh"
 #include "dmas_launch.cuh"
 
@@ -84,6 +85,8 @@ struct dmas_plan {
     size_t smem_beam = 0, smem_env = 0;
     float *d_taps_tc = nullptr;       // envelope taps as TF32 hi/lo phase arrays [2][4][Z]
     float *d_taps = nullptr;          // envelope taps [L] (CUDA-core FIR for small frames)
+    float *d_mf = nullptr;            // matched filter: the emitted signal [mf_len], or null
+    size_t mf_bytes = 0;              // matched-filtered frame in the scratch (0: no filter)
     int num_sms = 148;
     cudaStream_t last_stream = nullptr;
     std::string last_error;
@@ -135,8 +138,10 @@ void free_plan_memory(dmas_plan *p) {
     cudaFree(p->d_io_image);
     cudaFree(p->d_taps_tc);
     cudaFree(p->d_taps);
+    cudaFree(p->d_mf);
     p->d_taps_tc = nullptr;
     p->d_taps = nullptr;
+    p->d_mf = nullptr;
     for (auto &e : p->ev) {
         if (e) cudaEventDestroy(e);
         e = nullptr;
@@ -307,13 +312,18 @@ void mark(dmas_plan *p, int k, cudaStream_t s) {
     if (p->profiling) cudaEventRecord(p->ev[k], s);
 }
 
-// Per-frame scratch: root channels, y buffer (with the envelope), and a
-// 256-byte slot for the beamform launch's work counter.
+// Per-frame scratch: root channels, y buffer (with the envelope), the
+// matched-filtered frame (with the matched filter), and a 256-byte slot for
+// the beamform launches' work counters.
 size_t scratch_bytes(const dmas_plan *p) {
-    return align256(p->chan_bytes) + align256(p->ybuf_bytes) + 256;
+    return align256(p->chan_bytes) + align256(p->ybuf_bytes) + align256(p->mf_bytes) + 256;
+}
+float *mf_buffer(const dmas_plan *p, void *scratch) {
+    return (float *)((char *)scratch + align256(p->chan_bytes) + align256(p->ybuf_bytes));
 }
 unsigned *work_counter(const dmas_plan *p, void *scratch) {
-    return (unsigned *)((char *)scratch + align256(p->chan_bytes) + align256(p->ybuf_bytes));
+    return (unsigned *)((char *)scratch + align256(p->chan_bytes) + align256(p->ybuf_bytes) +
+                        align256(p->mf_bytes));
 }
 
 // ---- per-stage launch parameters of one frame ----------------------------
@@ -383,7 +393,48 @@ unsigned beam_blocks(const dmas_plan *p) {
 }
 
 // Enqueue the whole path for one frame with the given scratch.
+MfJob mf_job(const dmas_plan *p, const float *in, void *scratch, unsigned first) {
+    MfJob j;
+    j.in = in;
+    j.out = mf_buffer(p, scratch);
+    j.taps = p->d_mf;
+    j.N = p->hp.N;
+    j.T = p->hp.T;
+    j.L = (int)p->hp.mf.size();
+    j.t_tiles = (p->hp.T + kMfTile - 1) / kMfTile;
+    j.first = first;
+    return j;
+}
+
+unsigned mf_ctas(const dmas_plan *p) {
+    return (unsigned)p->hp.N * (unsigned)((p->hp.T + kMfTile - 1) / kMfTile);
+}
+
+cudaError_t launch_mf(const MfParams &mp, unsigned grid, size_t smem, cudaStream_t s) {
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [&] {
+        attr = cudaFuncSetAttribute(matched_filter_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(float) * mf_smem_floats(kMfMaxLen)));
+    });
+    if (attr != cudaSuccess) return attr;
+    matched_filter_kernel<<<grid, kMfThreads, smem, s>>>(mp);
+    return cudaGetLastError();
+}
+
+// K0 (with the matched filter) and K1: the roots of the frame, or of its
+// matched-filtered copy in the scratch.
 dmas_status enqueue_roots(dmas_plan *p, const float *d_frame, void *scratch, cudaStream_t s) {
+    if (!p->hp.mf.empty()) {
+        MfParams mp{};
+        mp.count = 1;
+        mp.job[0] = mf_job(p, d_frame, scratch, 0);
+        const cudaError_t e =
+            launch_mf(mp, mf_ctas(p), sizeof(float) * mf_smem_floats(mp.job[0].L), s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "matched_filter_kernel launch");
+        d_frame = mf_buffer(p, scratch);
+    }
     const RootsParams rp = roots_params(p, d_frame, scratch);
     const unsigned rgrid = roots_blocks(p);
     switch (p->hp.chan_prec) {
@@ -548,6 +599,26 @@ struct BatchEntry {
 // entries at a time.
 dmas_status enqueue_batch(const std::vector<BatchEntry> &v, cudaStream_t s) {
     cudaError_t e;
+    // K0: matched filter of the entries that have one
+    {
+        std::vector<const BatchEntry *> sel;
+        for (const auto &x : v)
+            if (!x.plan->hp.mf.empty()) sel.push_back(&x);
+        for (size_t b0 = 0; b0 < sel.size(); b0 += kBatchMax) {
+            MfParams mp{};
+            mp.count = (int)std::min<size_t>(kBatchMax, sel.size() - b0);
+            unsigned ctas = 0;
+            int Lmax = 0;
+            for (int k = 0; k < mp.count; ++k) {
+                const BatchEntry &x = *sel[b0 + k];
+                mp.job[k] = mf_job(x.plan, x.frame, x.scratch, ctas);
+                ctas += mf_ctas(x.plan);
+                Lmax = std::max(Lmax, mp.job[k].L);
+            }
+            e = launch_mf(mp, ctas, sizeof(float) * mf_smem_floats(Lmax), s);
+            if (e != cudaSuccess) return cuda_fail(sel[b0]->plan, e, "matched filter batch");
+        }
+    }
     // K1: roots, grouped by channel type
     for (int chan = 0; chan < 3; ++chan) {
         std::vector<const BatchEntry *> sel;
@@ -560,7 +631,9 @@ dmas_status enqueue_batch(const std::vector<BatchEntry> &v, cudaStream_t s) {
             for (int k = 0; k < rb.count; ++k) {
                 const BatchEntry &x = *sel[b0 + k];
                 rb.start[k] = blocks;
-                rb.e[k] = roots_params(x.plan, x.frame, x.scratch);
+                rb.e[k] = roots_params(x.plan,
+                                       x.plan->hp.mf.empty() ? x.frame : mf_buffer(x.plan, x.scratch),
+                                       x.scratch);
                 blocks += roots_blocks(x.plan);
             }
             rb.start[rb.count] = blocks;
@@ -741,6 +814,13 @@ dmas_status dmas_plan_create(const dmas_plan_desc *desc, dmas_plan **out) {
     p->chan_bytes = (size_t)hp.N * hp.row * chan_elem_bytes(hp.chan_prec) *
                     (uses_shifted_rows(hp.chan_prec, hp.order, hp.delay_mode) ? 2 : 1);
     p->ybuf_bytes = hp.L > 0 ? sizeof(float) * (size_t)hp.M * hp.T : 0;
+    p->mf_bytes = hp.mf.empty() ? 0 : sizeof(float) * (size_t)hp.N * hp.T;
+    if (!hp.mf.empty() && (e = upload(&p->d_mf, hp.mf)) != cudaSuccess) {
+        free_plan_memory(p);
+        delete p;
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? DMAS_ENOMEM : DMAS_ECUDA;
+    }
     if ((e = cudaMalloc((void **)&p->d_err, 256)) != cudaSuccess ||
         (e = cudaMemset(p->d_err, 0, 256)) != cudaSuccess ||
         (e = cudaMalloc(&p->d_scratch, scratch_bytes(p))) !=

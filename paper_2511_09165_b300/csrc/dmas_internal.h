@@ -21,6 +21,7 @@ constexpr int kTimeTile = 256;
 constexpr int kAlign = 8;
 // Largest envelope FIR.
 constexpr int kMaxTaps = 1023;
+constexpr int kMfMaxLen = 8192;  // longest emitted signal for the matched filter
 // Shared memory a beamform CTA may use for its staged windows: the scalar and
 // interpolated-delay pair kernels (one buffer), and the persistent pair
 // kernel's two staging buffers together (three or more CTAs per SM).
@@ -60,6 +61,7 @@ struct HostPlan {
     int row = 0;         // root channel row length (multiple of kAlign)
 
     std::vector<float> taps;  // [L]
+    std::vector<float> mf;    // matched filter: the emitted signal (empty: off)
 };
 
 // Validate the desc and build the host tables.  Returns DMAS_OK or DMAS_EINVAL

@@ -151,6 +151,13 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
     if (d.ng_prec < DMAS_NG_F32 || d.ng_prec > DMAS_NG_CF32) return fail("unknown ng_prec");
     if (d.flags & ~(DMAS_F_CF | DMAS_F_ENVELOPE)) return fail("unknown flag bits");
     if (!finite(d.cf_eps)) return fail("cf_eps must be finite");
+    if (d.mf_len < 0 || d.mf_len > kMfMaxLen || (d.mf_len > 0) != (d.mf_signal != nullptr))
+        return fail("mf_signal and mf_len: both absent, or 1..8192 samples");
+    hp.mf.clear();
+    for (int k = 0; k < d.mf_len; ++k) {
+        if (!std::isfinite(d.mf_signal[k])) return fail("mf_signal holds a non-finite value");
+        hp.mf.push_back(d.mf_signal[k]);
+    }
     if ((double)d.n_dirs * (double)d.n_samples > 17179869184.0)
         return fail("n_dirs * n_samples exceeds 2^34");
 

@@ -54,7 +54,7 @@ def _desc(**kw):
     azel = np.zeros((3, 2))
     base = dict(n_mics=4, mic_xyz=xyz, n_dirs=3, dir_azel=azel, dir_unit=None, delays_s=None,
                 n_samples=64, fs=450e3, c=343.0, order=5, delay_mode=0, flags=3, cf_eps=0.0,
-                env_cutoff_hz=0.0, env_taps=0, chan_prec=0, ng_prec=0)
+                env_cutoff_hz=0.0, env_taps=0, chan_prec=0, ng_prec=0, mf_signal=None, mf_len=0)
     base.update(kw)
     keep = []
 
@@ -68,7 +68,12 @@ def _desc(**kw):
     d = dm.PlanDesc(base["n_mics"], ptr(base["mic_xyz"]), base["n_dirs"], ptr(base["dir_azel"]),
                     ptr(base["dir_unit"]), ptr(base["delays_s"]), base["n_samples"], base["fs"],
                     base["c"], base["order"], base["delay_mode"], base["flags"], base["cf_eps"],
-                    base["env_cutoff_hz"], base["env_taps"], base["chan_prec"], base["ng_prec"])
+                    base["env_cutoff_hz"], base["env_taps"], base["chan_prec"], base["ng_prec"],
+                    None, base["mf_len"])
+    if base["mf_signal"] is not None:
+        e = np.ascontiguousarray(base["mf_signal"], dtype=np.float32)
+        keep.append(e)
+        d.mf_signal = e.ctypes.data_as(ctypes.c_void_p)
     return d, keep
 
 
@@ -83,6 +88,11 @@ BAD = [
     dict(delays_s=np.full((3, 4), np.inf)),
     dict(delays_s=np.full((3, 4), 10.0)),          # 4.5e6 samples of delay > 2^22
     dict(delays_s=np.array([[0.0] * 4, [0.1] * 4, [0.0] * 4])),  # group spread > shared memory
+    dict(mf_signal=np.zeros(8193), mf_len=8193),   # emitted signal longer than 8192
+    dict(mf_signal=None, mf_len=5),                 # length without a signal
+    dict(mf_signal=np.ones(4), mf_len=0),           # signal without a length
+    dict(mf_signal=np.array([1.0, np.nan]), mf_len=2),
+    dict(mf_len=-1),
 ]
 
 
