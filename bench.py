@@ -75,6 +75,13 @@ WORKLOADS = {
              "over -90..90 deg, 163840 samples at 450 kHz, n=5 without CF, "
              "nearest-sample delays, 181-tap envelope; vs_baseline against the paper's "
              "RTX 3090 (40 ms per frame, Table II)"),
+    # the paper's full pipeline: chirp echoes, the eRTIS call (2.5 ms, 25 to
+    # 50 kHz, 1125 taps) as the matched filter before the roots
+    "hemi_3d_n5_mf": dict(
+        scene=lambda: scenes.hemi_3d(seed=2, pulse="chirp"), order=5, mode="linear",
+        mf=True,
+        text="3-D hemisphere as hemi_3d_n5 with chirp echoes and the matched filter "
+             "(the emitted 2.5 ms 25-50 kHz chirp, 1125 taps) before the roots"),
     "passive256_n5": dict(
         scene=lambda: scenes.passive(seed=4, n_mics=256), order=5, mode="round",
         text="passive: 256 mics in a 0.4 m square, 8192 az/el directions, 32768 samples "
@@ -206,7 +213,7 @@ def dist_barrier(td):
 # ---------------------------------------------------------------------------
 # CPU oracle timing
 # ---------------------------------------------------------------------------
-def oracle_sample(scene, order, linear, n_dirs, cf=True):
+def oracle_sample(scene, order, linear, n_dirs, cf=True, mf=False):
     import oracle
     u = scene.dir_unit if scene.dir_unit is not None else oracle.unit_vectors(scene.dir_azel)
     tau = oracle.geometric_delays(scene.mic_xyz, u, scene.c)
@@ -214,23 +221,25 @@ def oracle_sample(scene, order, linear, n_dirs, cf=True):
     frame = scene.frame.astype(np.float64)
     D = min(n_dirs, scene.n_dirs)
     t0 = time.perf_counter()
+    if mf:
+        frame = oracle.matched_filter(frame, scenes.lfm_chirp(scene.fs).astype(np.float32))
     oracle.dmas(frame, tau, scene.fs, order, oracle.LINEAR if linear else oracle.ROUND,
                 use_cf=cf, taps=taps, dir_range=(0, D))
     dt = time.perf_counter() - t0
     return D * scene.n_samples, dt
 
 
-def cpu_baseline(scene, order, linear, cf=True, min_s=10.0) -> dict:
+def cpu_baseline(scene, order, linear, cf=True, mf=False, min_s=10.0) -> dict:
     """The oracle as it stands, on all host cores: whole frames of the workload
     (or a direction subset if a frame takes longer than min_s), repeated until
     at least min_s seconds of CPU work."""
     import oracle
     cores = oracle.set_threads(os.cpu_count() or 1)
-    px, dt = oracle_sample(scene, order, linear, 64, cf)
+    px, dt = oracle_sample(scene, order, linear, 64, cf, mf)
     D = int(max(64, min(scene.n_dirs, min_s * px / dt / scene.n_samples)))
     total_px, total_s, reps = 0, 0.0, 0
     while total_s < min_s:
-        px, dt = oracle_sample(scene, order, linear, D, cf)
+        px, dt = oracle_sample(scene, order, linear, D, cf, mf)
         total_px += px
         total_s += dt
         reps += 1
@@ -246,16 +255,16 @@ def run_reference(args, wl, scene) -> None:
         return
     import oracle
     linear = wl["mode"] == "linear"
-    cf = wl.get("cf", True)
+    cf, mf = wl.get("cf", True), bool(wl.get("mf"))
     cores = oracle.set_threads(os.cpu_count() or 1)
-    px, dt = oracle_sample(scene, wl["order"], linear, 16, cf)
+    px, dt = oracle_sample(scene, wl["order"], linear, 16, cf, mf)
     rate = px / dt
     D = int(max(8, min(scene.n_dirs, 0.4 * rate / scene.n_samples)))  # ~0.4 s a step
     for _ in range(args.warmup):
-        oracle_sample(scene, wl["order"], linear, D, cf)
+        oracle_sample(scene, wl["order"], linear, D, cf, mf)
     times = []
     for _ in range(args.steps):
-        px, dt = oracle_sample(scene, wl["order"], linear, D, cf)
+        px, dt = oracle_sample(scene, wl["order"], linear, D, cf, mf)
         times.append(dt)
     value = px * len(times) / sum(times)
     line = {
@@ -288,9 +297,10 @@ def run_ours(args, wl, scene) -> None:
     linear = wl["mode"] == "linear"
     order = wl["order"]
     cf = wl.get("cf", True)
+    mf = scenes.lfm_chirp(scene.fs).astype(np.float32) if wl.get("mf") else None
     plan = dm.Plan(mic_xyz=scene.mic_xyz, dir_azel=scene.dir_azel, dir_unit=scene.dir_unit,
                    n_samples=scene.n_samples, fs=scene.fs, c=scene.c, order=order,
-                   delay_mode=dm.LINEAR if linear else dm.ROUND, cf=cf)
+                   delay_mode=dm.LINEAR if linear else dm.ROUND, cf=cf, mf_signal=mf)
     info = plan.info()
     N, M, T = scene.n_mics, scene.n_dirs, scene.n_samples
     px = M * T
@@ -370,7 +380,8 @@ def run_ours(args, wl, scene) -> None:
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                        "p99": float(np.percentile(step_ms, 99))},
-        "stage_ms": {"roots": float(np.mean(stage[:, 0])), "beamform": beam_ms,
+        "stage_ms": {("matched filter + roots" if mf is not None else "roots"):
+                     float(np.mean(stage[:, 0])), "beamform": beam_ms,
                      "envelope": float(np.mean(stage[:, 2]))},
         "roofline": {"bound": "alu", "kernel": "beamform_x2_kernel", "achieved": achieved,
                      "peak": peak, "unit": "Top/s", "frac": achieved / peak,
@@ -382,13 +393,13 @@ def run_ours(args, wl, scene) -> None:
                               "achieved": path_achieved, "frac": path_achieved / peak}},
         "e2e": {"value": px * world * e2e_steps / e2e_total, "unit": UNIT,
                 "h2d_bytes_per_step": N * T * 4, "d2h_bytes_per_step": M * T * 4},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": (4 if mf is not None else 3) * args.steps,
         "clocks": clocks.summary(wall0, wall1),
         "plan": {"window": info.window, "mic_chunk": info.mic_chunk,
                  "groups": info.n_groups},
     }
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(scene, order, linear, cf)
+        line["cpu_baseline"] = cpu_baseline(scene, order, linear, cf, mf is not None)
     print(json.dumps(line), flush=True)
 
 
