@@ -608,13 +608,122 @@ def run_image_snr(args) -> None:
     }), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# every order at once: DAS and DMAS-2..5, with and without CF, in one pass
+# against ten single-order calls
+# ---------------------------------------------------------------------------
+def orders_ops_per_pixel(N: int, nmax: int, linear: bool) -> dict:
+    """FP32 operations per direction·sample of the every-order pass, counted as
+    for one order: its running sums accumulated over N mics (twice with
+    interpolation), Newton-Girard of every order, CF, the CF-weighted copies."""
+    sums = 2 + (1 if nmax >= 2 else 0) + nmax * (nmax - 1) // 2
+    main = N * sums * (2 if linear else 1)
+    ng = sum(k * (k + 1) // 2 + k for k in range(2, nmax + 1))
+    return {"main": main, "newton_girard": ng, "cf": 6 + nmax, "beam_total": main + ng + 6 + nmax}
+
+
+def run_orders(args) -> None:
+    import torch
+    import paper_2511_09165_b300 as dm
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+    steps = max(5, min(args.steps, 30))
+    sc = scenes.hemi_3d(seed=2)
+    N, M, T = sc.n_mics, sc.n_dirs, sc.n_samples
+    px = M * T
+    frame = torch.from_numpy(sc.frame).to(dev)
+    images = torch.empty((2, 5, M, T), device=dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    wall0 = time.time()
+    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    modes = []
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            flush.zero_()
+            fn()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        return float(np.median([a.elapsed_time(b) for a, b in ev]))
+
+    for mode in ("linear", "round"):
+        dmode = dm.LINEAR if mode == "linear" else dm.ROUND
+        kw = dict(mic_xyz=sc.mic_xyz, dir_unit=sc.dir_unit, n_samples=T, fs=sc.fs, c=sc.c,
+                  delay_mode=dmode)
+        plan = dm.Plan(order=5, **kw)
+        pass_ms = timed(lambda: plan.beamform_orders(frame, out=images, stream=stream))
+        plan.set_profiling(True)
+        stages = []
+        for _ in range(5):
+            plan.beamform_orders(frame, out=images, stream=stream)
+            stages.append(plan.stage_ms())
+        plan.check()
+        plan.close()
+        st = np.median(np.array(stages), axis=0)
+        singles = [dm.Plan(order=k, cf=cf, **kw) for cf in (False, True) for k in range(1, 6)]
+
+        def separate():
+            for i, pl in enumerate(singles):
+                pl(frame, out=images[i // 5, i % 5], stream=stream)
+
+        sep_ms = timed(separate)
+        for pl in singles:
+            pl.check()
+            pl.close()
+        ops = orders_ops_per_pixel(N, 5, mode == "linear")
+        achieved = ops["beam_total"] * px / (st[1] * 1e-3) / 1e12
+        modes.append({
+            "delays": mode, "pass_ms": pass_ms, "separate_ms": sep_ms,
+            "speedup": sep_ms / pass_ms,
+            "stage_ms": {"root planes": float(st[0]), "beamform (every order)": float(st[1]),
+                         "envelope (10 images)": float(st[2])},
+            "images_dir_samples_per_s": 10 * px / (pass_ms * 1e-3),
+            "roofline_beamform": {"bound": "alu", "kernel": "beamform_orders_kernel",
+                                  "ops_per_pixel": ops, "achieved": achieved, "peak": peak,
+                                  "unit": "Top/s", "frac": achieved / peak},
+        })
+    wall1 = time.time()
+    clocks.stop()
+    if rank != 0:
+        return
+    top = modes[0]
+    print(json.dumps({
+        "metric": "image·direction·samples/s: DAS and DMAS-2..5, each with and without CF "
+                  "(10 images) per frame",
+        "value": top["images_dir_samples_per_s"], "unit": "image·direction·samples/s",
+        "n_gpus": world, "steps": steps, "warmup": args.warmup, "ms_per_step": top["pass_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "orders", "description":
+                   "3-D hemisphere (32 mics, 2048 directions, 16384 samples), the ten images "
+                   "of Table I's algorithms with the 181-tap envelope: one dmas_beamform_orders "
+                   "call against ten dmas_beamform calls (median of CUDA-event steps, L2 "
+                   "flushed before each)", "l2": "flushed (256 MB write) before every step"},
+        "modes": modes,
+        "gpu_launches": 3 * steps,
+        "clocks": clocks.summary(wall0, wall1),
+    }), flush=True)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["serving", "sweep", "image_snr"],
+    ap.add_argument("--workload",
+                    choices=sorted(WORKLOADS) + ["serving", "sweep", "image_snr", "orders"],
                     default="hemi_3d_n5")
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 1000.0])
     ap.add_argument("--serve-seconds", type=float, default=5.0)
@@ -636,6 +745,13 @@ def main() -> None:
                               "the image-SNR experiment has no CPU reference arm"}))
             return
         run_image_snr(args)
+        return
+    if args.workload == "orders":
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable":
+                              "the every-order comparison has no CPU reference arm"}))
+            return
+        run_orders(args)
         return
     if args.workload == "sweep":
         if args.impl == "reference":

@@ -160,6 +160,43 @@ dmas_status dmas_destroy(dmas_plan *plan);
 dmas_status dmas_beamform(dmas_plan *plan, const float *d_frame, float *d_image,
                           float *d_y, float *d_cf, void *stream);
 
+/* dmas_beamform_orders: which image(s) per selected order */
+enum {
+    DMAS_V_PLAIN = 1,  /* E_k */
+    DMAS_V_CF = 2      /* E_k x CF */
+};
+
+/*
+ * Every order at once: DAS and DMAS-2..n, each with and without the coherence
+ * factor (the algorithms Table I and Fig. 5 compare), from one pass over the
+ * delayed samples.  The root step writes sgn(m)|m|^(1/q) for every
+ * q = 1..order (Sec. II-B); the beamform step keeps per pixel sum x, sum x^2,
+ * sum |x| and the power sums P_1..P_{q-1} of every q (Eq. power_sum), with
+ * P_k = sum x for odd k and P_k = sum |x| for even k, and forms E_k of every
+ * selected k by Newton-Girard (Eqs. dmas2_impl..dmas5_impl).  The plan's delay
+ * mode, Newton-Girard precision, cf_eps, envelope and matched filter apply;
+ * its DMAS_F_CF flag does not (`variants` decides).
+ *   orders_mask : bit k-1 selects order k; non-zero, no bit above the plan's
+ *                 order.
+ *   variants    : DMAS_V_PLAIN, DMAS_V_CF, or both.
+ *   d_images    : device [V][K][M][T] float32, V = the selected variants
+ *                 (plain first), K = the selected orders (ascending); each
+ *                 image is the envelope (DMAS_F_ENVELOPE) or E_k (x CF).
+ *   d_cf        : optional device [M][T] float32: the coherence factor.
+ * The plan must have FP32 channels and order <= 5.  Each image equals that of
+ * dmas_beamform with a plan of that order to FP32 rounding (not bitwise: the
+ * sums differ, e.g. P_k of odd k is sum x rather than the sum of the roots'
+ * k-th powers).  The first call allocates the pass's scratch (the order root
+ * planes of the frame and, with the envelope, the V x K pre-envelope images)
+ * and the plan keeps it; a later call that needs more grows it, which waits
+ * for the device.  Same stream rule as dmas_beamform.
+ * Errors: DMAS_EINVAL (NULL plan/frame/images, a plan without the pass, a bad
+ * mask or variants; the reason in dmas_plan_last_error), DMAS_ENOMEM,
+ * DMAS_ECUDA.
+ */
+dmas_status dmas_beamform_orders(dmas_plan *plan, const float *d_frame, unsigned orders_mask,
+                                 int variants, float *d_images, float *d_cf, void *stream);
+
 /*
  * Same as dmas_beamform but with HOST buffers: copies h_frame ([N][T] float32)
  * to the device, beamforms, copies the image back to h_image ([M][T] float32)

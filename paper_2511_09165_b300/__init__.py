@@ -25,13 +25,15 @@ ROUND, LINEAR = 0, 1
 CH_F32, CH_F16, CH_BF16 = 0, 1, 2
 NG_F32, NG_F64, NG_CF32 = 0, 1, 2
 F_CF, F_ENVELOPE = 1, 2
+V_PLAIN, V_CF = 1, 2  # dmas_beamform_orders: images without / with the coherence factor
 
 STATUS = {0: "DMAS_OK", 1: "DMAS_EINVAL", 2: "DMAS_ENOMEM", 3: "DMAS_ECUDA",
           4: "DMAS_EBUSY", 5: "DMAS_ETIMEOUT"}
 
 # Every symbol include/dmas.h declares.
 EXPORTS = [
-    "dmas_plan_create", "dmas_destroy", "dmas_beamform", "dmas_beamform_host",
+    "dmas_plan_create", "dmas_destroy", "dmas_beamform", "dmas_beamform_orders",
+    "dmas_beamform_host",
     "dmas_beamform_batch", "dmas_batch_workspace_bytes", "dmas_plan_workspace_bytes",
     "dmas_plan_get_info", "dmas_plan_get_delays", "dmas_plan_get_taps", "dmas_plan_check",
     "dmas_plan_last_error", "dmas_plan_set_profiling", "dmas_plan_stage_ms",
@@ -91,6 +93,7 @@ def load_library(path: str | None = None):
             "dmas_destroy": ([vp], i),
             "dmas_beamform": ([vp, vp, vp, vp, vp, vp], i),
             "dmas_beamform_host": ([vp, vp, vp, vp], i),
+            "dmas_beamform_orders": ([vp, vp, ctypes.c_uint, i, vp, vp, vp], i),
             "dmas_beamform_batch": ([i, vp, vp, vp, vp, sz, vp], i),
             "dmas_batch_workspace_bytes": ([i, vp], sz),
             "dmas_plan_workspace_bytes": ([vp], sz),
@@ -299,6 +302,35 @@ class Plan:
             ctypes.c_void_p(_stream_handle(stream)))
         if st != 0:
             self._raise(st, "dmas_beamform")
+        return out
+
+    def beamform_orders(self, frame, orders=None, variants=V_PLAIN | V_CF, out=None, cf=None,
+                        stream=None):
+        """Every order at once: images [V][K][M][T] of the orders `orders`
+        (default 1..order, ascending) for the variants V_PLAIN (E_k) and/or
+        V_CF (E_k x CF), plain first, from one pass over the delayed samples."""
+        import torch
+        _check_tensor(frame, (self.n_mics, self.n_samples), "frame")
+        orders = sorted(set(range(1, self.order + 1) if orders is None else orders))
+        mask = 0
+        for k in orders:
+            if not 1 <= k <= 8:
+                raise ValueError(f"order {k} out of range")
+            mask |= 1 << (k - 1)
+        n_v = bin(int(variants) & 3).count("1")
+        shape = (n_v, len(orders), self.n_dirs, self.n_samples)
+        if out is None:
+            out = torch.empty(shape, device=frame.device, dtype=torch.float32)
+        _check_tensor(out, shape, "out")
+        if cf is not None:
+            _check_tensor(cf, (self.n_dirs, self.n_samples), "cf")
+        st = self._lib.dmas_beamform_orders(
+            self.handle, ctypes.c_void_p(frame.data_ptr()), mask, int(variants),
+            ctypes.c_void_p(out.data_ptr()),
+            ctypes.c_void_p(cf.data_ptr()) if cf is not None else None,
+            ctypes.c_void_p(_stream_handle(stream)))
+        if st != 0:
+            self._raise(st, "dmas_beamform_orders")
         return out
 
     def beamform_host(self, frame: np.ndarray, out: np.ndarray | None = None, stream=None):

@@ -15,6 +15,7 @@
 #include "dmas_mf.cuh"
 #include "dmas_envelope_tc.cuh"
 #include "dmas_launch.cuh"
+#include "dmas_orders.cuh"
 
 namespace dmas {
 extern template cudaError_t launch_beamform_order<1>(const BeamParams &, int, int, int, unsigned,
@@ -64,6 +65,21 @@ static const BeamLauncher kBeamLaunchers[9] = {
     &launch_beamform_order<4>, &launch_beamform_order<5>, &launch_beamform_order<6>,
     &launch_beamform_order<7>, &launch_beamform_order<8>};
 
+extern template cudaError_t launch_orders<1>(const OrdersParams &, int, int, unsigned, size_t,
+                                              cudaStream_t);
+extern template cudaError_t launch_orders<2>(const OrdersParams &, int, int, unsigned, size_t,
+                                              cudaStream_t);
+extern template cudaError_t launch_orders<3>(const OrdersParams &, int, int, unsigned, size_t,
+                                              cudaStream_t);
+extern template cudaError_t launch_orders<4>(const OrdersParams &, int, int, unsigned, size_t,
+                                              cudaStream_t);
+extern template cudaError_t launch_orders<5>(const OrdersParams &, int, int, unsigned, size_t,
+                                              cudaStream_t);
+
+static const OrdersLauncher kOrdersLaunchers[kOrdersMaxOrder + 1] = {
+    nullptr, &launch_orders<1>, &launch_orders<2>, &launch_orders<3>, &launch_orders<4>,
+    &launch_orders<5>};
+
 static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 }  // namespace dmas
 
@@ -98,6 +114,10 @@ struct dmas_plan {
     // dmas_beamform_host: the image download stream and one event per chunk
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t chunk_ev[kHostChunks] = {};
+    // dmas_beamform_orders: root planes, pre-envelope images and the
+    // matched-filtered frame; allocated by its first call, grown on demand
+    void *d_orders = nullptr;
+    size_t orders_bytes = 0;
 };
 
 namespace {
@@ -139,6 +159,9 @@ void free_plan_memory(dmas_plan *p) {
     cudaFree(p->d_taps_tc);
     cudaFree(p->d_taps);
     cudaFree(p->d_mf);
+    cudaFree(p->d_orders);
+    p->d_orders = nullptr;
+    p->orders_bytes = 0;
     p->d_taps_tc = nullptr;
     p->d_taps = nullptr;
     p->d_mf = nullptr;
@@ -251,13 +274,17 @@ EncodeTiledFn encode_tiled() {
     return fn;
 }
 
-EnvTcJob env_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned first) {
+// `rows` (0: the plan's M) rows of T samples: the every-order pass filters
+// several images of one plan in one launch.
+EnvTcJob env_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned first,
+                 int rows = 0) {
+    if (rows == 0) rows = p->hp.M;
     EnvTcJob j;
     std::memset(&j, 0, sizeof(j));
     j.use_tma = 0;
     if ((p->hp.T & 3) == 0 && ((uintptr_t)ybuf & 15) == 0) {
         if (EncodeTiledFn enc = encode_tiled()) {
-            cuuint64_t dims[2] = {(cuuint64_t)p->hp.T, (cuuint64_t)p->hp.M};
+            cuuint64_t dims[2] = {(cuuint64_t)p->hp.T, (cuuint64_t)rows};
             cuuint64_t strides[1] = {(cuuint64_t)p->hp.T * 4};
             cuuint32_t box[2] = {kTcAtomK, kTcRows};
             cuuint32_t es[2] = {1, 1};
@@ -270,7 +297,7 @@ EnvTcJob env_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned
     }
     j.y = ybuf;
     j.img = d_image;
-    j.M = p->hp.M;
+    j.M = rows;
     j.T = p->hp.T;
     j.tt0 = 0;
     j.t_tiles = (p->hp.T + kTcJ - 1) / kTcJ;
@@ -278,8 +305,9 @@ EnvTcJob env_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned
     return j;
 }
 
-unsigned env_tiles(const dmas_plan *p) {
-    return (unsigned)(((size_t)p->hp.M + kTcRows - 1) / kTcRows *
+unsigned env_tiles(const dmas_plan *p, int rows = 0) {
+    if (rows == 0) rows = p->hp.M;
+    return (unsigned)(((size_t)rows + kTcRows - 1) / kTcRows *
                       (((size_t)p->hp.T + kTcJ - 1) / kTcJ));
 }
 
@@ -292,11 +320,12 @@ bool env_on_cuda_cores(const dmas_plan *p) {
     return (double)p->hp.M * (double)p->hp.T * (double)p->hp.L <= 1.5e8;
 }
 
-EnvFirJob fir_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned first) {
+EnvFirJob fir_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned first,
+                  int rows = 0) {
     EnvFirJob j;
     j.y = ybuf;
     j.img = d_image;
-    j.M = p->hp.M;
+    j.M = rows ? rows : p->hp.M;
     j.T = p->hp.T;
     j.tt0 = 0;
     j.t_tiles = (p->hp.T + kFirTile - 1) / kFirTile;
@@ -304,8 +333,8 @@ EnvFirJob fir_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigne
     return j;
 }
 
-unsigned fir_ctas(const dmas_plan *p) {
-    return (unsigned)((size_t)p->hp.M * ((p->hp.T + kFirTile - 1) / kFirTile));
+unsigned fir_ctas(const dmas_plan *p, int rows = 0) {
+    return (unsigned)((size_t)(rows ? rows : p->hp.M) * ((p->hp.T + kFirTile - 1) / kFirTile));
 }
 
 void mark(dmas_plan *p, int k, cudaStream_t s) {
@@ -733,6 +762,142 @@ dmas_status enqueue_batch(const std::vector<BatchEntry> &v, cudaStream_t s) {
     return DMAS_OK;
 }
 
+// The every-order pass: matched filter (if the plan has one), root planes,
+// one every-order beamform launch into `n_img` images (or their pre-envelope
+// copies), and one envelope launch over all of them.
+dmas_status enqueue_orders(dmas_plan *p, const float *d_frame, unsigned mask, int variants,
+                           float *d_images, float *d_cf, cudaStream_t s) {
+    const HostPlan &hp = p->hp;
+    OrdersParams op;
+    std::memset(&op, 0, sizeof(op));
+    int n_img = 0;
+    for (int v = 0; v < 2; ++v)
+        for (int k = 0; k <= kOrdersMaxOrder; ++k)
+            op.slot[v][k] = (k >= 1 && ((variants >> v) & 1) && ((mask >> (k - 1)) & 1))
+                                ? n_img++
+                                : -1;
+    const size_t plane = (size_t)hp.N * hp.row;
+    const size_t chan_b = align256(sizeof(float) * plane * hp.order);
+    const size_t img = (size_t)hp.M * hp.T;
+    const size_t y_b = hp.L > 0 ? align256(sizeof(float) * img * n_img) : 0;
+    const size_t need = chan_b + y_b + align256(p->mf_bytes);
+    cudaError_t e;
+    if (need > p->orders_bytes) {
+        cudaFree(p->d_orders);  // waits for work still using the old buffer
+        p->d_orders = nullptr;
+        p->orders_bytes = 0;
+        if ((e = cudaMalloc(&p->d_orders, need)) != cudaSuccess) {
+            cudaGetLastError();
+            p->last_error = "every-order scratch: " + std::string(cudaGetErrorString(e));
+            return e == cudaErrorMemoryAllocation ? DMAS_ENOMEM : DMAS_ECUDA;
+        }
+        p->orders_bytes = need;
+    }
+    char *base = (char *)p->d_orders;
+    float *chan = (float *)base;
+    float *ybuf = hp.L > 0 ? (float *)(base + chan_b) : d_images;
+    mark(p, 0, s);
+    if (!hp.mf.empty()) {
+        MfParams mp{};
+        mp.count = 1;
+        mp.job[0] = mf_job(p, d_frame, p->d_scratch, 0);
+        mp.job[0].out = (float *)(base + chan_b + y_b);
+        e = launch_mf(mp, mf_ctas(p), sizeof(float) * mf_smem_floats(mp.job[0].L), s);
+        if (e != cudaSuccess) return cuda_fail(p, e, "matched_filter_kernel launch");
+        d_frame = mp.job[0].out;
+    }
+    RootPlanesParams rp;
+    rp.frame = d_frame;
+    rp.chan = chan;
+    rp.plane = plane;
+    rp.N = hp.N;
+    rp.T = hp.T;
+    rp.row = hp.row;
+    rp.padl = hp.padl;
+    const unsigned rgrid = roots_blocks(p);
+    switch (hp.order) {
+        case 1: root_planes_kernel<1><<<rgrid, 256, 0, s>>>(rp); break;
+        case 2: root_planes_kernel<2><<<rgrid, 256, 0, s>>>(rp); break;
+        case 3: root_planes_kernel<3><<<rgrid, 256, 0, s>>>(rp); break;
+        case 4: root_planes_kernel<4><<<rgrid, 256, 0, s>>>(rp); break;
+        default: root_planes_kernel<5><<<rgrid, 256, 0, s>>>(rp); break;
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(p, e, "root_planes_kernel launch");
+    mark(p, 1, s);
+
+    op.chan = chan;
+    op.plane = plane;
+    op.use_tma = 0;
+    if (hp.mo_window <= kOrdersTmaMaxWindow) {
+        if (EncodeTiledFn enc = encode_tiled()) {
+            // planes [order][N][row]: one box per microphone, its window of
+            // every plane
+            cuuint64_t dims[3] = {(cuuint64_t)hp.row, (cuuint64_t)hp.N, (cuuint64_t)hp.order};
+            cuuint64_t strides[2] = {(cuuint64_t)hp.row * 4, (cuuint64_t)plane * 4};
+            cuuint32_t box[3] = {(cuuint32_t)hp.mo_window, 1, (cuuint32_t)hp.order};
+            cuuint32_t es[3] = {1, 1, 1};
+            if (enc(&op.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)chan, dims, strides, box,
+                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+                op.use_tma = 1;
+        }
+    }
+    op.gdir = p->d_gdir;
+    op.gws = p->d_gws;
+    op.rel = p->d_rel;
+    op.w4 = p->d_w4;
+    op.y = ybuf;
+    op.img = img;
+    op.cf = d_cf;
+    op.err = p->d_err;
+    op.N = hp.N;
+    op.T = hp.T;
+    op.row = hp.row;
+    op.padl = hp.padl;
+    op.window = hp.mo_window;
+    op.mic_chunk = hp.mo_chunk;
+    op.n_groups = hp.n_groups;
+    op.n_mics_f = (float)hp.N;
+    op.cf_eps = (float)hp.cf_eps;
+    const bool lin = hp.delay_mode == DMAS_DELAY_LINEAR;
+    e = kOrdersLaunchers[hp.order](op, lin ? 1 : 0, hp.ng_prec,
+                                   (unsigned)((size_t)hp.n_groups * hp.mo_tiles),
+                                   orders_smem_bytes(hp.order, lin, hp.mo_chunk, hp.mo_window), s);
+    if (e != cudaSuccess) return cuda_fail(p, e, "beamform_orders_kernel launch");
+    mark(p, 2, s);
+    p->env_ran = hp.L > 0;
+    if (hp.L > 0) {
+        // the plan's envelope engine (chosen by its M), so an image does not
+        // depend on how many others the call asked for
+        const int rows = hp.M * n_img;
+        if (env_on_cuda_cores(p)) {
+            EnvFirParams fp{};
+            fp.count = 1;
+            fp.H = (hp.L - 1) / 2;
+            fp.taps = p->d_taps;
+            fp.job[0] = fir_job(p, ybuf, d_images, 0, rows);
+            envelope_fir_kernel<<<fir_ctas(p, rows), kFirTile, 0, s>>>(fp);
+            if ((e = cudaGetLastError()) != cudaSuccess)
+                return cuda_fail(p, e, "envelope_fir_kernel launch");
+        } else {
+            EnvTcParams ep{};
+            ep.count = 1;
+            ep.job[0] = env_job(p, ybuf, d_images, 0, rows);
+            ep.total_tiles = env_tiles(p, rows);
+            ep.H = (hp.L - 1) / 2;
+            ep.taps = p->d_taps_tc;
+            ep.err = p->d_err;
+            e = launch_env_tc(ep, std::min<unsigned>(ep.total_tiles, (unsigned)p->num_sms),
+                              p->smem_env, s);
+            if (e != cudaSuccess) return cuda_fail(p, e, "envelope_tc_kernel launch");
+        }
+    }
+    mark(p, 3, s);
+    p->profiled_once = p->profiled_once || p->profiling;
+    return DMAS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -853,6 +1018,28 @@ dmas_status dmas_beamform(dmas_plan *p, const float *d_frame, float *d_image, fl
     cudaStream_t s = (cudaStream_t)stream;
     p->last_stream = s;
     return enqueue_frame(p, d_frame, d_image, d_y, d_cf, p->d_scratch, s);
+}
+
+dmas_status dmas_beamform_orders(dmas_plan *p, const float *d_frame, unsigned orders_mask,
+                                 int variants, float *d_images, float *d_cf, void *stream) {
+    if (!p || !d_frame || !d_images) return DMAS_EINVAL;
+    const HostPlan &hp = p->hp;
+    if (hp.mo_chunk == 0) {
+        p->last_error = "dmas_beamform_orders: the plan needs FP32 channels, order <= 5 and a "
+                        "delay spread whose staged windows fit in shared memory";
+        return DMAS_EINVAL;
+    }
+    if (orders_mask == 0 || (orders_mask >> hp.order) != 0) {
+        p->last_error = "dmas_beamform_orders: orders_mask must select orders in 1..order";
+        return DMAS_EINVAL;
+    }
+    if (variants < DMAS_V_PLAIN || variants > (DMAS_V_PLAIN | DMAS_V_CF)) {
+        p->last_error = "dmas_beamform_orders: variants must be DMAS_V_PLAIN, DMAS_V_CF or both";
+        return DMAS_EINVAL;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    p->last_stream = s;
+    return enqueue_orders(p, d_frame, orders_mask, variants, d_images, d_cf, s);
 }
 
 dmas_status dmas_beamform_host(dmas_plan *p, const float *h_frame, float *h_image,

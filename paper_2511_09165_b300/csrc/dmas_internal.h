@@ -59,6 +59,12 @@ struct HostPlan {
     int n_tiles = 0;     // time tiles of `tile` samples
     int padl = 0;        // zero samples before t = 0 in the root channel rows
     int row = 0;         // root channel row length (multiple of kAlign)
+    int spread = 0;      // largest (last sample read - window start) over groups, mics
+
+    // every-order pass (dmas_beamform_orders; FP32 channels, order <= 5):
+    // its time tile, staged window, microphones per stage and time tiles;
+    // mo_chunk == 0 when the pass is not available for this plan
+    int mo_tile = 0, mo_window = 0, mo_chunk = 0, mo_tiles = 0;
 
     std::vector<float> taps;  // [L]
     std::vector<float> mf;    // matched filter: the emitted signal (empty: off)
@@ -103,5 +109,29 @@ inline size_t lin_pair_smem_bytes(int mic_chunk, int window) {
     return 128 + 2 * pair_window_bytes(mic_chunk, window) + (size_t)mic_chunk * kGroup * 24 +
            8 * 6 * 32 * 4;
 }
+
+// Every-order pass (dmas_beamform_orders): one microphone's staged block
+// (its plane rows), padded to 128 bytes; one staging buffer (mic_chunk blocks,
+// the chunk's shift table and, interpolated, its {1-f, 1-f, f, f} table); the
+// CTA's dynamic shared memory: barrier slot, two staging buffers and, for
+// interpolated delays, the per-lane sums of the sample past the tile.
+constexpr int kOrdersMaxOrder = 5;  // highest order of the every-order pass
+inline int orders_tile(bool lin) { return lin ? 64 : 128; }
+inline int orders_num_sums(int nmax) { return 2 + (nmax >= 2 ? 1 : 0) + nmax * (nmax - 1) / 2; }
+inline size_t orders_mic_bytes(int nmax, int window) {
+    return ((size_t)nmax * window * 4 + 127) & ~(size_t)127;
+}
+inline size_t orders_stage_bytes(int nmax, bool lin, int mic_chunk, int window) {
+    return ((size_t)mic_chunk * orders_mic_bytes(nmax, window) + (size_t)mic_chunk * kGroup * 4 +
+            (lin ? (size_t)mic_chunk * kGroup * 16 : 0) + 127) & ~(size_t)127;
+}
+inline size_t orders_smem_bytes(int nmax, bool lin, int mic_chunk, int window) {
+    return 128 + 2 * orders_stage_bytes(nmax, lin, mic_chunk, window) +
+           (lin ? (size_t)8 * orders_num_sums(nmax) * 32 * 4 : 0);
+}
+// Shared memory of one every-order CTA (two per SM: the register limit).
+constexpr size_t kOrdersSmemBudget = 110 * 1024;
+// Largest window one tensor copy (box dimension <= 256) stages.
+constexpr int kOrdersTmaMaxWindow = 256;
 
 }  // namespace dmas

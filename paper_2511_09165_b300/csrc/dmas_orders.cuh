@@ -1,0 +1,459 @@
+// Every order at once: DAS and DMAS-2..n, each with and without the
+// coherence factor (the algorithms compared in Table I and Fig. 5), from one
+// gather of the delayed samples.
+//
+//   root_planes_kernel   per microphone sample, the planes r_q = sgn(m)|m|^(1/q)
+//                        for q = 1..NMAX (r_1 = m itself), [q][mic][row], zero
+//                        padded like the single-order root channel.
+//   beamform_orders_kernel
+//                        one CTA per (group of 8 directions, time tile); lane l
+//                        of warp w owns direction w and the samples t0 + l and
+//                        t0 + l + 32 (+ 64 for the second pair of a 128-sample
+//                        tile) as packed f32x2 pixel pairs.  The tensor-copy
+//                        engine stages, per microphone, one 3-D box: its window
+//                        of every plane, so a chunk of microphones costs one
+//                        copy per microphone; two chunks in flight.  Per pixel
+//                        the lane keeps, in FP32 registers:
+//                          sum x, sum x^2          CF (Eq. cf) and E_1 = DAS
+//                          sum |x|                 P_2 of order 2 and P_4 of
+//                                                  order 4 (|r_2|^2 = |r_4|^4 = |x|)
+//                          P_1..P_{q-1} of r_q     for q = 2..NMAX (Eq. power_sum;
+//                                                  P_q of odd q is sum x)
+//                        then Newton-Girard per order (Eqs. dmas2_impl..
+//                        dmas5_impl) and writes the requested images.
+//
+// For NMAX = 5 that is 13 running sums and 5 staged roots per sample, against
+// 2 + 4 + 5 + 6 + 6 sums and 5 gathers over 5 separate passes.  Nearest-sample
+// delays take a 128-sample tile (two pairs per lane), interpolated ones a
+// 64-sample tile (one pair: their sums are split in two, U[t] with weight
+// 1 - f and V[t] with weight f over the same staged sample, the interpolated
+// sum being U[t] + V[t + 1], so each staged sample's powers are formed once).
+//
+// Waits on the stage barriers are bounded as in the single-order kernels.
+#pragma once
+
+#include <cuda.h>
+
+#include "dmas_launch.cuh"
+
+namespace dmas {
+
+template <int NMAX> struct OrdersLayout {
+    static constexpr int kAbs = NMAX >= 2 ? 1 : 0;  // sum |x| kept
+    static constexpr int kNum = 2 + kAbs + NMAX * (NMAX - 1) / 2;
+    // index of P_1 of order q; P_2..P_{q-1} follow
+    static constexpr int base(int q) { return 2 + kAbs + (q - 2) * (q - 1) / 2; }
+};
+
+struct RootPlanesParams {
+    const float *frame;  // [N][T]
+    float *chan;         // [NMAX][N][row]
+    size_t plane;        // N * row
+    int N, T, row, padl;
+};
+
+template <int NMAX>
+__global__ void __launch_bounds__(256) root_planes_kernel(const __grid_constant__ RootPlanesParams p) {
+    const size_t total = (size_t)p.N * (size_t)p.row;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / (size_t)p.row);
+        const int t = (int)(idx - (size_t)i * p.row) - p.padl;
+        const float m = (t >= 0 && t < p.T) ? p.frame[(size_t)i * p.T + t] : 0.0f;
+        p.chan[idx] = m;
+#pragma unroll
+        for (int q = 2; q <= NMAX; ++q)
+            p.chan[(size_t)(q - 1) * p.plane + idx] = signed_root(m, q, 1.0f / (float)q);
+    }
+}
+
+struct OrdersParams {
+    // 3-D view of the planes for the tensor-copy engine: dims (row, N, NMAX),
+    // box (window, 1, NMAX); valid when use_tma != 0 (window <= 256)
+    CUtensorMap tmap;
+    const float *chan;  // [NMAX][N][row] root planes
+    size_t plane;       // elements from one plane to the next (N * row)
+    const int *gdir;    // [n_groups * 8] direction index or -1
+    const int *gws;     // [n_groups][N] window start relative to t0
+    const int *rel;     // [n_groups][N][8] shift relative to the window start
+    const float *w4;    // [n_groups][N][8][4] {1 - f, 1 - f, f, f} (interpolated delays)
+    float *y;           // images [n_images][M][T]
+    size_t img;         // elements from one image to the next (M * T)
+    float *cf;          // [M][T] or nullptr
+    unsigned *err;      // error word
+    // image index of order k without (slot[0][k]) and with (slot[1][k]) the
+    // coherence factor; -1: not wanted
+    int slot[2][kOrdersMaxOrder + 1];
+    int N, T, row, padl, window, mic_chunk, n_groups, use_tma;
+    float n_mics_f, cf_eps;
+};
+
+// Bytes of one microphone's staged block (its NMAX plane rows of `window`
+// samples), padded to 128 bytes, and of one staging buffer (mic_chunk blocks,
+// the chunk's shift table and, interpolated, its weight table).  The host
+// computes the same (orders_mic_bytes, orders_stage_bytes).
+__device__ __forceinline__ int orders_mic_bytes_dev(int nmax, int window) {
+    return (nmax * window * 4 + 127) & ~127;
+}
+__device__ __forceinline__ int orders_stage_bytes_dev(int nmax, bool lin, int mic_chunk,
+                                                      int window) {
+    return (mic_chunk * orders_mic_bytes_dev(nmax, window) + mic_chunk * 32 +
+            (lin ? mic_chunk * 128 : 0) + 127) & ~127;
+}
+
+// 3-D tensor copy global -> shared, completion counted in bytes on `bar`.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait that lets the thread sleep in the barrier (up to a few
+// microseconds per try) instead of spinning on it, so waiting warps leave
+// their issue slots to the warps that compute.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(4000u)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_sleep_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait_sleep(bar, parity)) return true;
+    const unsigned long long start = global_ns();
+    while (!mbar_try_wait_sleep(bar, parity)) {
+        if (global_ns() - start > kWaitLimitNs) return false;
+    }
+    return true;
+}
+
+constexpr unsigned long long kAbsMask2 = 0x7fffffff7fffffffull;
+
+// Nearest-sample delays: add one delayed pixel pair (its planes s[0..NMAX-1])
+// to the running sums.
+template <int NMAX>
+__device__ __forceinline__ void accumulate_orders(f32x2_t (&a)[OrdersLayout<NMAX>::kNum],
+                                                  const f32x2_t (&s)[NMAX]) {
+    const f32x2_t x = s[0];
+    a[0] = f2_add(a[0], x);
+    a[1] = f2_fma(x, x, a[1]);
+    if constexpr (NMAX >= 2) a[2] = f2_add(a[2], x & kAbsMask2);
+#pragma unroll
+    for (int q = 2; q <= NMAX; ++q) {
+        const int b = OrdersLayout<NMAX>::base(q);
+        f32x2_t pw = s[q - 1];
+        a[b] = f2_add(a[b], pw);
+#pragma unroll
+        for (int j = 2; j < q; ++j) {
+            pw = f2_mul(pw, s[q - 1]);
+            a[b + j - 1] = f2_add(a[b + j - 1], pw);
+        }
+    }
+}
+
+// Interpolated delays: every power of the sample goes (1 - f)-weighted into U
+// and f-weighted into V.
+template <int NMAX>
+__device__ __forceinline__ void accumulate_orders_split(f32x2_t (&u)[OrdersLayout<NMAX>::kNum],
+                                                        f32x2_t (&v)[OrdersLayout<NMAX>::kNum],
+                                                        const f32x2_t (&s)[NMAX], f32x2_t w0,
+                                                        f32x2_t w1) {
+    const f32x2_t x = s[0];
+    const f32x2_t xx = f2_mul(x, x);
+    u[0] = f2_fma(w0, x, u[0]);
+    v[0] = f2_fma(w1, x, v[0]);
+    u[1] = f2_fma(w0, xx, u[1]);
+    v[1] = f2_fma(w1, xx, v[1]);
+    if constexpr (NMAX >= 2) {
+        const f32x2_t ax = x & kAbsMask2;
+        u[2] = f2_fma(w0, ax, u[2]);
+        v[2] = f2_fma(w1, ax, v[2]);
+    }
+#pragma unroll
+    for (int q = 2; q <= NMAX; ++q) {
+        const int b = OrdersLayout<NMAX>::base(q);
+        f32x2_t pw = s[q - 1];
+        u[b] = f2_fma(w0, pw, u[b]);
+        v[b] = f2_fma(w1, pw, v[b]);
+#pragma unroll
+        for (int j = 2; j < q; ++j) {
+            pw = f2_mul(pw, s[q - 1]);
+            u[b + j - 1] = f2_fma(w0, pw, u[b + j - 1]);
+            v[b + j - 1] = f2_fma(w1, pw, v[b + j - 1]);
+        }
+    }
+}
+
+// The f-weighted part for one sample in scalar arithmetic (the sample past
+// the tile).
+template <int NMAX>
+__device__ __forceinline__ void accumulate_orders_v(float (&v)[OrdersLayout<NMAX>::kNum],
+                                                    const float (&s)[NMAX], float w1) {
+    const float x = s[0];
+    v[0] = fmaf(w1, x, v[0]);
+    v[1] = fmaf(w1, x * x, v[1]);
+    if constexpr (NMAX >= 2) v[2] = fmaf(w1, fabsf(x), v[2]);
+#pragma unroll
+    for (int q = 2; q <= NMAX; ++q) {
+        const int b = OrdersLayout<NMAX>::base(q);
+        float pw = s[q - 1];
+        v[b] = fmaf(w1, pw, v[b]);
+#pragma unroll
+        for (int j = 2; j < q; ++j) {
+            pw *= s[q - 1];
+            v[b + j - 1] = fmaf(w1, pw, v[b + j - 1]);
+        }
+    }
+}
+
+// E_K from the running sums of one pixel, written to the images that want it;
+// then the next order.
+template <int K, int NMAX, int NGP>
+__device__ __forceinline__ void emit_orders(const float (&a)[OrdersLayout<NMAX>::kNum], float cf,
+                                            const OrdersParams &p, size_t pix) {
+    if constexpr (K <= NMAX) {
+        const int s0 = p.slot[0][K], s1 = p.slot[1][K];
+        if (s0 >= 0 || s1 >= 0) {
+            float E;
+            if constexpr (K == 1) {
+                E = a[0];
+            } else {
+                float P[K + 1];
+                P[0] = 0.0f;
+#pragma unroll
+                for (int j = 1; j < K; ++j) P[j] = a[OrdersLayout<NMAX>::base(K) + j - 1];
+                P[K] = (K & 1) ? a[0] : a[2];
+                E = esym_from_power_sums<K, NGP>(P);
+            }
+            if (s0 >= 0) p.y[(size_t)s0 * p.img + pix] = E;
+            if (s1 >= 0) p.y[(size_t)s1 * p.img + pix] = E * cf;
+        }
+        emit_orders<K + 1, NMAX, NGP>(a, cf, p, pix);
+    }
+}
+
+template <int NMAX, bool LINEAR, int NGP>
+__global__ void __launch_bounds__(kThreads, 2)
+    beamform_orders_kernel(const __grid_constant__ OrdersParams p) {
+    constexpr int kPairs = LINEAR ? 1 : 2;
+    constexpr int kTile = 64 * kPairs;
+    constexpr int NA = OrdersLayout<NMAX>::kNum;
+    extern __shared__ __align__(128) unsigned char smem[];
+    // smem: two stage barriers; two staging buffers (microphone chunks c and
+    // c + 1 in flight while chunk c is summed), each [mic][plane][window] (one
+    // 128-byte aligned block per microphone), the shift table and
+    // (interpolated) the weight table; then the per-lane V of the sample past
+    // the tile (interpolated), [warp][q][lane]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    const int WS = p.window;
+    const int NC = p.mic_chunk;
+    const int MB = orders_mic_bytes_dev(NMAX, WS) >> 2;  // floats per microphone block
+    const int SB = orders_stage_bytes_dev(NMAX, LINEAR, NC, WS);
+    const int n_chunks = (p.N + NC - 1) / NC;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *s_vext = reinterpret_cast<float *>(smem + 128 + 2 * SB) + (warp * NA * 32 + lane);
+
+    const int tile = (int)(blockIdx.x / (unsigned)p.n_groups);
+    const int g = (int)(blockIdx.x - (unsigned)tile * (unsigned)p.n_groups);
+    const int t0 = tile * kTile;
+
+    // Stage microphone chunk ci into buffer ci & 1 (called by warp 0).
+    auto stage = [&](int ci) {
+        unsigned char *bb = smem + 128 + (ci & 1) * SB;
+        float *win = reinterpret_cast<float *>(bb);
+        int *rel = reinterpret_cast<int *>(win + NC * MB);
+        float *w4 = reinterpret_cast<float *>(rel + NC * 8);
+        const int c0 = ci * NC;
+        const int nc = min(NC, p.N - c0);
+        const uint32_t row_bytes = (uint32_t)(WS * 4);
+        const uint32_t tab_bytes = (uint32_t)(nc * 8 * 4);
+        if (lane == 0)
+            mbar_arrive_expect_tx(&bar[ci & 1], (uint32_t)NMAX * nc * row_bytes + tab_bytes +
+                                                    (LINEAR ? 4u * tab_bytes : 0u));
+        __syncwarp();
+        const int *gws = p.gws + (size_t)g * p.N;
+        for (int il = lane; il < nc; il += 32) {
+            const int i = c0 + il;
+            const int x = p.padl + t0 + gws[i];  // a multiple of 8 samples (32 bytes)
+            if (p.use_tma) {
+                tma_load_3d(win + il * MB, &p.tmap, x, i, 0, &bar[ci & 1]);
+            } else {
+                const float *src = p.chan + (size_t)i * p.row + x;
+#pragma unroll
+                for (int q = 0; q < NMAX; ++q)
+                    bulk_g2s(win + il * MB + q * WS, src + (size_t)q * p.plane, row_bytes,
+                             &bar[ci & 1]);
+            }
+        }
+        if (lane == 0) {
+            const size_t to = ((size_t)g * p.N + c0) * 8;
+            bulk_g2s(rel, p.rel + to, tab_bytes, &bar[ci & 1]);
+            if (LINEAR) bulk_g2s(w4, p.w4 + to * 4, 4 * tab_bytes, &bar[ci & 1]);
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (warp == 0) {
+        stage(0);
+        if (n_chunks > 1) stage(1);
+    }
+
+    f32x2_t acc[kPairs][NA];
+    f32x2_t vac[LINEAR ? NA : 1];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+#pragma unroll
+        for (int k = 0; k < kPairs; ++k) acc[k][q] = 0ull;
+        if constexpr (LINEAR) {
+            vac[q] = 0ull;
+            s_vext[q * 32] = 0.0f;
+        }
+    }
+
+    for (int ci = 0; ci < n_chunks; ++ci) {
+        const int b = ci & 1;
+        const uint32_t parity = (uint32_t)(ci >> 1) & 1u;
+        const bool ok = mbar_wait_sleep_bounded(&bar[b], parity);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(p.err, kErrTimeout);
+                // let the copies in flight land: this chunk's and the next one's
+                mbar_wait_bounded(&bar[b], parity);
+                if (ci + 1 < n_chunks)
+                    mbar_wait_bounded(&bar[b ^ 1], (uint32_t)((ci + 1) >> 1) & 1u);
+            }
+            return;
+        }
+        const unsigned char *bb = smem + 128 + b * SB;
+        const float *win = reinterpret_cast<const float *>(bb);
+        const int *s_rel = reinterpret_cast<const int *>(win + NC * MB);
+        const float *s_w4 = reinterpret_cast<const float *>(s_rel + NC * 8);
+        const int nc = min(NC, p.N - ci * NC);
+
+#pragma unroll 2
+        for (int il = 0; il < nc; ++il) {
+            const float *r = win + il * MB + s_rel[il * 8 + warp] + lane;
+            if constexpr (LINEAR) {
+                const ulonglong2 w =
+                    reinterpret_cast<const ulonglong2 *>(s_w4)[il * 8 + warp];  // {1-f,1-f},{f,f}
+                f32x2_t s[NMAX];
+#pragma unroll
+                for (int q = 0; q < NMAX; ++q) s[q] = f2_pack(r[q * WS], r[q * WS + 32]);
+                accumulate_orders_split<NMAX>(acc[0], vac, s, w.x, w.y);
+            } else {
+#pragma unroll
+                for (int k = 0; k < kPairs; ++k) {
+                    f32x2_t s[NMAX];
+#pragma unroll
+                    for (int q = 0; q < NMAX; ++q)
+                        s[q] = f2_pack(r[q * WS + 64 * k], r[q * WS + 64 * k + 32]);
+                    accumulate_orders<NMAX>(acc[k], s);
+                }
+            }
+        }
+        if constexpr (LINEAR) {
+            // the sample past the tile, one microphone per lane
+            if (lane < nc) {
+                float ve[NA];
+#pragma unroll
+                for (int q = 0; q < NA; ++q) ve[q] = s_vext[q * 32];
+                for (int il = lane; il < nc; il += 32) {
+                    const float *r = win + il * MB + s_rel[il * 8 + warp] + kTile;
+                    float sv[NMAX];
+#pragma unroll
+                    for (int q = 0; q < NMAX; ++q) sv[q] = r[q * WS];
+                    accumulate_orders_v<NMAX>(ve, sv, s_w4[(il * 8 + warp) * 4 + 2]);
+                }
+#pragma unroll
+                for (int q = 0; q < NA; ++q) s_vext[q * 32] = ve[q];
+            }
+        }
+        if (ci + 2 < n_chunks) {
+            __syncthreads();  // every warp is done with buffer b
+            if (warp == 0) {
+                fence_proxy_async_smem();  // the warps' reads before the copy's writes
+                stage(ci + 2);
+            }
+        }
+    }
+
+    const int dir = p.gdir[(size_t)g * 8 + warp];
+    if (dir < 0) return;
+    if constexpr (LINEAR) {
+        // sum[t] = U[t] + V[t + 1]: for lane l's t0 + l that is lane l + 1's
+        // first half (lane 31: lane 0's second half); for t0 + 32 + l, lane
+        // l + 1's second half (lane 31: the sample past the tile, summed over
+        // the lanes' microphones).
+#pragma unroll
+        for (int q = 0; q < NA; ++q) {
+            float ve = s_vext[q * 32];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) ve += __shfl_xor_sync(0xffffffffu, ve, o);
+            float ulo, uhi, vlo, vhi;
+            f2_unpack(acc[0][q], ulo, uhi);
+            f2_unpack(vac[q], vlo, vhi);
+            const float nlo = __shfl_sync(0xffffffffu, vlo, (lane + 1) & 31);
+            const float nhi = __shfl_sync(0xffffffffu, vhi, (lane + 1) & 31);
+            acc[0][q] = f2_pack(ulo + (lane < 31 ? nlo : nhi), uhi + (lane < 31 ? nhi : ve));
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kPairs; ++k) {
+        float a[2][NA];
+#pragma unroll
+        for (int q = 0; q < NA; ++q) f2_unpack(acc[k][q], a[0][q], a[1][q]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = t0 + lane + 32 * h + 64 * k;
+            if (t >= p.T) continue;
+            const size_t pix = (size_t)dir * p.T + t;
+            const float cf = cf_ratio(a[h][0], a[h][1], p.n_mics_f, p.cf_eps);
+            emit_orders<1, NMAX, NGP>(a[h], cf, p, pix);
+            if (p.cf) p.cf[pix] = cf;
+        }
+    }
+}
+
+// Launch of one (NMAX, delay mode, Newton-Girard precision) variant; each
+// NMAX is instantiated in its own translation unit (orders_o<NMAX>.cu).
+template <int NMAX, bool LINEAR, int NGP>
+cudaError_t launch_orders_variant(const OrdersParams &p, unsigned grid, size_t smem,
+                                  cudaStream_t s) {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    return launch_kernel(beamform_orders_kernel<NMAX, LINEAR, NGP>, once, err, p, grid, smem, s);
+}
+
+template <int NMAX, bool LINEAR>
+cudaError_t launch_orders_ng(const OrdersParams &p, int ngp, unsigned grid, size_t smem,
+                             cudaStream_t s) {
+    switch (ngp) {
+        case NG_F64: return launch_orders_variant<NMAX, LINEAR, NG_F64>(p, grid, smem, s);
+        case NG_CF32: return launch_orders_variant<NMAX, LINEAR, NG_CF32>(p, grid, smem, s);
+        default: return launch_orders_variant<NMAX, LINEAR, NG_F32>(p, grid, smem, s);
+    }
+}
+
+template <int NMAX>
+cudaError_t launch_orders(const OrdersParams &p, int linear, int ngp, unsigned grid, size_t smem,
+                          cudaStream_t s) {
+    if (linear) return launch_orders_ng<NMAX, true>(p, ngp, grid, smem, s);
+    return launch_orders_ng<NMAX, false>(p, ngp, grid, smem, s);
+}
+
+using OrdersLauncher = cudaError_t (*)(const OrdersParams &, int, int, unsigned, size_t,
+                                       cudaStream_t);
+
+}  // namespace dmas

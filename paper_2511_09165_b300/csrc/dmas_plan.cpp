@@ -328,6 +328,25 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
                     hp.gw4[o * 4 + 3] = f;
                 }
     }
+    hp.spread = (int)spread;
+    // Every-order pass: 128-sample tiles for nearest-sample delays, 64 for
+    // interpolated ones; as many microphones per stage as fit two stages in
+    // the budget, in balanced chunks.
+    hp.mo_tile = hp.mo_window = hp.mo_chunk = hp.mo_tiles = 0;
+    if (pair) {
+        const int mt = orders_tile(lin);
+        const int mw = (int)round_up(mt + spread, kAlign);
+        int chunk = 0;
+        while (chunk < N && orders_smem_bytes(d.order, lin, chunk + 1, mw) <= kOrdersSmemBudget)
+            ++chunk;
+        if (chunk > 0) {
+            const int n_chunks = (N + chunk - 1) / chunk;
+            hp.mo_tile = mt;
+            hp.mo_window = mw;
+            hp.mo_chunk = (N + n_chunks - 1) / n_chunks;
+            hp.mo_tiles = (T + mt - 1) / mt;
+        }
+    }
     hp.n_tiles = (T + hp.tile - 1) / hp.tile;
     hp.padl = (int)round_up(std::max(0, -ws_min), kAlign);
     long long read_end = (long long)hp.padl + (long long)(hp.n_tiles - 1) * hp.tile +

@@ -1,0 +1,8 @@
+// Every-order beamform kernels up to order 1 (both delay modes, all
+// Newton-Girard precisions), instantiated in their own translation unit.
+#include "dmas_orders.cuh"
+
+namespace dmas {
+template cudaError_t launch_orders<1>(const OrdersParams &, int, int, unsigned, size_t,
+                                        cudaStream_t);
+}  // namespace dmas
