@@ -777,7 +777,8 @@ dmas_status enqueue_orders(dmas_plan *p, const float *d_frame, unsigned mask, in
                                 ? n_img++
                                 : -1;
     const size_t plane = (size_t)hp.N * hp.row;
-    const size_t chan_b = align256(sizeof(float) * plane * hp.order);
+    const int n_planes = orders_planes(hp.order);
+    const size_t chan_b = align256(sizeof(float) * plane * n_planes);
     const size_t img = (size_t)hp.M * hp.T;
     const size_t y_b = hp.L > 0 ? align256(sizeof(float) * img * n_img) : 0;
     const size_t need = chan_b + y_b + align256(p->mf_bytes);
@@ -830,11 +831,11 @@ dmas_status enqueue_orders(dmas_plan *p, const float *d_frame, unsigned mask, in
     op.use_tma = 0;
     if (hp.mo_window <= kOrdersTmaMaxWindow) {
         if (EncodeTiledFn enc = encode_tiled()) {
-            // planes [order][N][row]: one box per microphone, its window of
-            // every plane
-            cuuint64_t dims[3] = {(cuuint64_t)hp.row, (cuuint64_t)hp.N, (cuuint64_t)hp.order};
+            // planes [n_planes][N][row]: one box per microphone, its window
+            // of every plane
+            cuuint64_t dims[3] = {(cuuint64_t)hp.row, (cuuint64_t)hp.N, (cuuint64_t)n_planes};
             cuuint64_t strides[2] = {(cuuint64_t)hp.row * 4, (cuuint64_t)plane * 4};
-            cuuint32_t box[3] = {(cuuint32_t)hp.mo_window, 1, (cuuint32_t)hp.order};
+            cuuint32_t box[3] = {(cuuint32_t)hp.mo_window, 1, (cuuint32_t)n_planes};
             cuuint32_t es[3] = {1, 1, 1};
             if (enc(&op.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)chan, dims, strides, box,
                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,

@@ -118,8 +118,11 @@ inline size_t lin_pair_smem_bytes(int mic_chunk, int window) {
 constexpr int kOrdersMaxOrder = 5;  // highest order of the every-order pass
 inline int orders_tile(bool lin) { return lin ? 64 : 128; }
 inline int orders_num_sums(int nmax) { return 2 + (nmax >= 2 ? 1 : 0) + nmax * (nmax - 1) / 2; }
+// staged root planes: orders floor(nmax/2)+1..nmax (the lower roots follow
+// from them)
+inline int orders_planes(int nmax) { return nmax >= 2 ? nmax - nmax / 2 : 1; }
 inline size_t orders_mic_bytes(int nmax, int window) {
-    return ((size_t)nmax * window * 4 + 127) & ~(size_t)127;
+    return ((size_t)orders_planes(nmax) * window * 4 + 127) & ~(size_t)127;
 }
 inline size_t orders_stage_bytes(int nmax, bool lin, int mic_chunk, int window) {
     return ((size_t)mic_chunk * orders_mic_bytes(nmax, window) + (size_t)mic_chunk * kGroup * 4 +

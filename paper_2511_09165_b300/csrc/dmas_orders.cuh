@@ -3,8 +3,12 @@
 // gather of the delayed samples.
 //
 //   root_planes_kernel   per microphone sample, the planes r_q = sgn(m)|m|^(1/q)
-//                        for q = 1..NMAX (r_1 = m itself), [q][mic][row], zero
-//                        padded like the single-order root channel.
+//                        of the upper half of the orders, q = floor(NMAX/2)+1
+//                        ..NMAX ([q][mic][row], zero padded like the
+//                        single-order root channel); the lower roots follow
+//                        from them in registers: r_{q} = sgn(r_{2q}) r_{2q}^2
+//                        and m = r_3^3 (or sgn(r_2) r_2^2), so NMAX = 5 stages
+//                        3 planes, not 5.
 //   beamform_orders_kernel
 //                        one CTA per (group of 8 directions, time tile); lane l
 //                        of warp w owns direction w and the samples t0 + l and
@@ -38,6 +42,12 @@
 
 namespace dmas {
 
+// Orders whose roots are staged: q = kFirst..NMAX.
+template <int NMAX> struct OrdersPlanes {
+    static constexpr int kFirst = NMAX >= 2 ? NMAX / 2 + 1 : 1;
+    static constexpr int kNum = NMAX - kFirst + 1;
+};
+
 template <int NMAX> struct OrdersLayout {
     static constexpr int kAbs = NMAX >= 2 ? 1 : 0;  // sum |x| kept
     static constexpr int kNum = 2 + kAbs + NMAX * (NMAX - 1) / 2;
@@ -47,7 +57,7 @@ template <int NMAX> struct OrdersLayout {
 
 struct RootPlanesParams {
     const float *frame;  // [N][T]
-    float *chan;         // [NMAX][N][row]
+    float *chan;         // [planes][N][row]: plane j holds r_(kFirst + j)
     size_t plane;        // N * row
     int N, T, row, padl;
 };
@@ -60,18 +70,19 @@ __global__ void __launch_bounds__(256) root_planes_kernel(const __grid_constant_
         const int i = (int)(idx / (size_t)p.row);
         const int t = (int)(idx - (size_t)i * p.row) - p.padl;
         const float m = (t >= 0 && t < p.T) ? p.frame[(size_t)i * p.T + t] : 0.0f;
-        p.chan[idx] = m;
+        constexpr int F = OrdersPlanes<NMAX>::kFirst;
 #pragma unroll
-        for (int q = 2; q <= NMAX; ++q)
-            p.chan[(size_t)(q - 1) * p.plane + idx] = signed_root(m, q, 1.0f / (float)q);
+        for (int q = F; q <= NMAX; ++q)
+            p.chan[(size_t)(q - F) * p.plane + idx] =
+                q == 1 ? m : signed_root(m, q, 1.0f / (float)q);
     }
 }
 
 struct OrdersParams {
-    // 3-D view of the planes for the tensor-copy engine: dims (row, N, NMAX),
-    // box (window, 1, NMAX); valid when use_tma != 0 (window <= 256)
+    // 3-D view of the planes for the tensor-copy engine: dims (row, N,
+    // planes), box (window, 1, planes); valid when use_tma != 0 (window <= 256)
     CUtensorMap tmap;
-    const float *chan;  // [NMAX][N][row] root planes
+    const float *chan;  // [planes][N][row] staged root planes
     size_t plane;       // elements from one plane to the next (N * row)
     const int *gdir;    // [n_groups * 8] direction index or -1
     const int *gws;     // [n_groups][N] window start relative to t0
@@ -88,16 +99,16 @@ struct OrdersParams {
     float n_mics_f, cf_eps;
 };
 
-// Bytes of one microphone's staged block (its NMAX plane rows of `window`
+// Bytes of one microphone's staged block (its plane rows of `window`
 // samples), padded to 128 bytes, and of one staging buffer (mic_chunk blocks,
 // the chunk's shift table and, interpolated, its weight table).  The host
 // computes the same (orders_mic_bytes, orders_stage_bytes).
-__device__ __forceinline__ int orders_mic_bytes_dev(int nmax, int window) {
-    return (nmax * window * 4 + 127) & ~127;
+__device__ __forceinline__ int orders_mic_bytes_dev(int planes, int window) {
+    return (planes * window * 4 + 127) & ~127;
 }
-__device__ __forceinline__ int orders_stage_bytes_dev(int nmax, bool lin, int mic_chunk,
+__device__ __forceinline__ int orders_stage_bytes_dev(int planes, bool lin, int mic_chunk,
                                                       int window) {
-    return (mic_chunk * orders_mic_bytes_dev(nmax, window) + mic_chunk * 32 +
+    return (mic_chunk * orders_mic_bytes_dev(planes, window) + mic_chunk * 32 +
             (lin ? mic_chunk * 128 : 0) + 127) & ~127;
 }
 
@@ -135,6 +146,40 @@ __device__ __forceinline__ bool mbar_wait_sleep_bounded(uint64_t *bar, uint32_t 
 }
 
 constexpr unsigned long long kAbsMask2 = 0x7fffffff7fffffffull;
+
+// All roots s[q - 1] = r_q, q = 1..NMAX, of a pixel pair from its staged
+// ones st[j] = r_(kFirst + j): r_q = sgn(r_2q) r_2q^2, and m = r_3^3 when
+// order 3 is staged.
+template <int NMAX>
+__device__ __forceinline__ void expand_roots(const f32x2_t (&st)[OrdersPlanes<NMAX>::kNum],
+                                             f32x2_t (&s)[NMAX]) {
+    constexpr int F = OrdersPlanes<NMAX>::kFirst;
+#pragma unroll
+    for (int q = NMAX; q >= 1; --q) {
+        if (q >= F) {
+            s[q - 1] = st[q - F];
+        } else if (q == 1 && NMAX >= 3) {
+            s[0] = f2_mul(f2_mul(s[2], s[2]), s[2]);
+        } else {
+            s[q - 1] = f2_copysign(f2_mul(s[2 * q - 1], s[2 * q - 1]), s[2 * q - 1]);
+        }
+    }
+}
+template <int NMAX>
+__device__ __forceinline__ void expand_roots(const float (&st)[OrdersPlanes<NMAX>::kNum],
+                                             float (&s)[NMAX]) {
+    constexpr int F = OrdersPlanes<NMAX>::kFirst;
+#pragma unroll
+    for (int q = NMAX; q >= 1; --q) {
+        if (q >= F) {
+            s[q - 1] = st[q - F];
+        } else if (q == 1 && NMAX >= 3) {
+            s[0] = s[2] * s[2] * s[2];
+        } else {
+            s[q - 1] = copysignf(s[2 * q - 1] * s[2 * q - 1], s[2 * q - 1]);
+        }
+    }
+}
 
 // Nearest-sample delays: add one delayed pixel pair (its planes s[0..NMAX-1])
 // to the running sums.
@@ -245,6 +290,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     constexpr int kPairs = LINEAR ? 1 : 2;
     constexpr int kTile = 64 * kPairs;
     constexpr int NA = OrdersLayout<NMAX>::kNum;
+    constexpr int NP = OrdersPlanes<NMAX>::kNum;
     extern __shared__ __align__(128) unsigned char smem[];
     // smem: two stage barriers; two staging buffers (microphone chunks c and
     // c + 1 in flight while chunk c is summed), each [mic][plane][window] (one
@@ -254,8 +300,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     const int WS = p.window;
     const int NC = p.mic_chunk;
-    const int MB = orders_mic_bytes_dev(NMAX, WS) >> 2;  // floats per microphone block
-    const int SB = orders_stage_bytes_dev(NMAX, LINEAR, NC, WS);
+    const int MB = orders_mic_bytes_dev(NP, WS) >> 2;  // floats per microphone block
+    const int SB = orders_stage_bytes_dev(NP, LINEAR, NC, WS);
     const int n_chunks = (p.N + NC - 1) / NC;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *s_vext = reinterpret_cast<float *>(smem + 128 + 2 * SB) + (warp * NA * 32 + lane);
@@ -275,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const uint32_t row_bytes = (uint32_t)(WS * 4);
         const uint32_t tab_bytes = (uint32_t)(nc * 8 * 4);
         if (lane == 0)
-            mbar_arrive_expect_tx(&bar[ci & 1], (uint32_t)NMAX * nc * row_bytes + tab_bytes +
+            mbar_arrive_expect_tx(&bar[ci & 1], (uint32_t)NP * nc * row_bytes + tab_bytes +
                                                     (LINEAR ? 4u * tab_bytes : 0u));
         __syncwarp();
         const int *gws = p.gws + (size_t)g * p.N;
@@ -287,7 +333,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             } else {
                 const float *src = p.chan + (size_t)i * p.row + x;
 #pragma unroll
-                for (int q = 0; q < NMAX; ++q)
+                for (int q = 0; q < NP; ++q)
                     bulk_g2s(win + il * MB + q * WS, src + (size_t)q * p.plane, row_bytes,
                              &bar[ci & 1]);
             }
@@ -348,17 +394,19 @@ __global__ void __launch_bounds__(kThreads, 2)
             if constexpr (LINEAR) {
                 const ulonglong2 w =
                     reinterpret_cast<const ulonglong2 *>(s_w4)[il * 8 + warp];  // {1-f,1-f},{f,f}
-                f32x2_t s[NMAX];
+                f32x2_t st[NP], s[NMAX];
 #pragma unroll
-                for (int q = 0; q < NMAX; ++q) s[q] = f2_pack(r[q * WS], r[q * WS + 32]);
+                for (int q = 0; q < NP; ++q) st[q] = f2_pack(r[q * WS], r[q * WS + 32]);
+                expand_roots<NMAX>(st, s);
                 accumulate_orders_split<NMAX>(acc[0], vac, s, w.x, w.y);
             } else {
 #pragma unroll
                 for (int k = 0; k < kPairs; ++k) {
-                    f32x2_t s[NMAX];
+                    f32x2_t st[NP], s[NMAX];
 #pragma unroll
-                    for (int q = 0; q < NMAX; ++q)
-                        s[q] = f2_pack(r[q * WS + 64 * k], r[q * WS + 64 * k + 32]);
+                    for (int q = 0; q < NP; ++q)
+                        st[q] = f2_pack(r[q * WS + 64 * k], r[q * WS + 64 * k + 32]);
+                    expand_roots<NMAX>(st, s);
                     accumulate_orders<NMAX>(acc[k], s);
                 }
             }
@@ -371,9 +419,10 @@ __global__ void __launch_bounds__(kThreads, 2)
                 for (int q = 0; q < NA; ++q) ve[q] = s_vext[q * 32];
                 for (int il = lane; il < nc; il += 32) {
                     const float *r = win + il * MB + s_rel[il * 8 + warp] + kTile;
-                    float sv[NMAX];
+                    float st[NP], sv[NMAX];
 #pragma unroll
-                    for (int q = 0; q < NMAX; ++q) sv[q] = r[q * WS];
+                    for (int q = 0; q < NP; ++q) st[q] = r[q * WS];
+                    expand_roots<NMAX>(st, sv);
                     accumulate_orders_v<NMAX>(ve, sv, s_w4[(il * 8 + warp) * 4 + 2]);
                 }
 #pragma unroll
