@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const float *s_w4 = reinterpret_cast<const float *>(s_rel + NC * 8);
         const int nc = min(NC, p.N - ci * NC);
 
-#pragma unroll 2
+#pragma unroll 4
         for (int il = 0; il < nc; ++il) {
             const float *r = win + il * MB + s_rel[il * 8 + warp] + lane;
             if constexpr (LINEAR) {
