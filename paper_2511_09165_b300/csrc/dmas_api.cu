@@ -387,6 +387,23 @@ float *y_target(const dmas_plan *p, float *d_image, float *d_y, void *scratch) {
 BeamParams beam_params(const dmas_plan *p, void *scratch, float *ybuf, float *d_cf) {
     const HostPlan &hp = p->hp;
     BeamParams bp;
+    std::memset(&bp, 0, sizeof(bp));
+    bp.use_tma = 0;
+    if (uses_shifted_rows(hp.chan_prec, hp.order, hp.delay_mode) && hp.window <= kTmaMaxBox) {
+        if (EncodeTiledFn enc = encode_tiled()) {
+            // root rows [N][row], then their shifted copies: one box per
+            // microphone, its window in both
+            cuuint64_t dims[3] = {(cuuint64_t)hp.row, (cuuint64_t)hp.N, 2};
+            cuuint64_t strides[2] = {(cuuint64_t)hp.row * 4, (cuuint64_t)hp.N * hp.row * 4};
+            cuuint32_t box[3] = {(cuuint32_t)hp.window, 1, 2};
+            cuuint32_t es[3] = {1, 1, 1};
+            if (enc(&bp.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, scratch, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+                bp.use_tma = 1;
+        }
+    }
     bp.chan = scratch;
     bp.work = work_counter(p, scratch);
     bp.gdir = p->d_gdir;
@@ -829,7 +846,7 @@ dmas_status enqueue_orders(dmas_plan *p, const float *d_frame, unsigned mask, in
     op.chan = chan;
     op.plane = plane;
     op.use_tma = 0;
-    if (hp.mo_window <= kOrdersTmaMaxWindow) {
+    if (hp.mo_window <= kTmaMaxBox) {
         if (EncodeTiledFn enc = encode_tiled()) {
             // planes [n_planes][N][row]: one box per microphone, its window
             // of every plane

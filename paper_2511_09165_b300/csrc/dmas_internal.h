@@ -97,18 +97,22 @@ inline size_t pair_stage_bytes(int mic_chunk, int window) {
            ~(size_t)127;
 }
 // Pair kernel with interpolated delays: its root rows are also stored shifted
-// by one sample; its CTA stages mic_chunk window rows as is, the same rows
-// shifted (each block padded to 128 bytes), and per microphone and direction
-// the shift (int), the pair offset (int) and the weights (4 floats).
+// by one sample; its CTA stages, per microphone, one 128-byte aligned block
+// holding the window as is and then shifted (lin_mic_bytes), and per
+// microphone and direction the shift (int), the pair offset (int) and the
+// weights (4 floats).
 inline bool uses_shifted_rows(int chan_prec, int order, int delay_mode) {
     return uses_pair_kernel(chan_prec, order) && delay_mode == DMAS_DELAY_LINEAR;
 }
+inline size_t lin_mic_bytes(int window) { return ((size_t)2 * window * 4 + 127) & ~(size_t)127; }
 // The CTA also keeps per-lane partial sums of the sample past its tile
 // (8 warps x up to 6 sums x 32 lanes).
 inline size_t lin_pair_smem_bytes(int mic_chunk, int window) {
-    return 128 + 2 * pair_window_bytes(mic_chunk, window) + (size_t)mic_chunk * kGroup * 24 +
+    return 128 + (size_t)mic_chunk * lin_mic_bytes(window) + (size_t)mic_chunk * kGroup * 24 +
            8 * 6 * 32 * 4;
 }
+// Largest window one tensor copy (box dimension <= 256) stages.
+constexpr int kTmaMaxBox = 256;
 
 // Every-order pass (dmas_beamform_orders): one microphone's staged block
 // (its plane rows), padded to 128 bytes; one staging buffer (mic_chunk blocks,
@@ -134,7 +138,5 @@ inline size_t orders_smem_bytes(int nmax, bool lin, int mic_chunk, int window) {
 }
 // Shared memory of one every-order CTA (two per SM: the register limit).
 constexpr size_t kOrdersSmemBudget = 110 * 1024;
-// Largest window one tensor copy (box dimension <= 256) stages.
-constexpr int kOrdersTmaMaxWindow = 256;
 
 }  // namespace dmas

@@ -21,6 +21,7 @@
 // expiry the kernel sets a bit in the plan's error word and returns.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -104,6 +105,39 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
             "r"(smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+
+// 3-D tensor copy global -> shared, completion counted in bytes on `bar`.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait that lets the thread sleep in the barrier (up to a few
+// microseconds per try) instead of spinning on it, so waiting warps leave
+// their issue slots to the warps that compute.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(4000u)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_sleep_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait_sleep(bar, parity)) return true;
+    const unsigned long long start = global_ns();
+    while (!mbar_try_wait_sleep(bar, parity)) {
+        if (global_ns() - start > kWaitLimitNs) return false;
+    }
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -322,6 +356,10 @@ __device__ __forceinline__ float cf_ratio(float A, float B, float n_mics, float 
 }
 
 struct BeamParams {
+    // interpolated-delay pair kernel: 3-D view of the root rows and their
+    // shifted copies, dims (row, N, 2), box (window, 1, 2): one tensor copy
+    // stages both windows of a microphone; valid when use_tma != 0
+    CUtensorMap tmap;
     const void *chan;    // [N][row] roots, zero padded
     const int *gdir;     // [n_groups * 8] direction index or -1
     const int *gws;      // [n_groups][N] window start relative to t0
@@ -341,6 +379,7 @@ struct BeamParams {
     int stage_bytes;     // persistent pair kernel: bytes of one staging buffer (same for a
                          // whole launch)
     unsigned *work;      // persistent pair kernel: this launch's work counter, zero at launch
+    int use_tma;         // interpolated-delay pair kernel: stage by tmap (window <= 256)
 };
 
 // Running sums per pixel: P_1..P_n, sum x, sum x^2, where for odd n
@@ -597,10 +636,11 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     const int WS = p.window;
     const int NC = p.mic_chunk;
-    const int win_bytes = (NC * WS * 4 + 127) & ~127;
-    float *copy0 = reinterpret_cast<float *>(smem + 128);
-    float *copy1 = reinterpret_cast<float *>(smem + 128 + win_bytes);
-    int *s_rel = reinterpret_cast<int *>(smem + 128 + 2 * win_bytes);
+    // per microphone one 128-byte aligned block: its window, then the window
+    // shifted by one sample
+    const int MBf = ((2 * WS * 4 + 127) & ~127) >> 2;
+    float *win = reinterpret_cast<float *>(smem + 128);
+    int *s_rel = reinterpret_cast<int *>(smem + 128 + NC * MBf * 4);
     int *s_sel = s_rel + NC * 8;
     float *s_w4 = reinterpret_cast<float *>(s_sel + NC * 8);
     // per-lane partial sums of the sample past the tile: [warp][q][lane]
@@ -642,9 +682,14 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
             const int *gws = p.gws + (size_t)g * p.N;
             for (int il = lane; il < nc; il += 32) {
                 const int i = c0 + il;
-                const size_t o = (size_t)i * p.row + p.padl + t0 + gws[i];
-                bulk_g2s(copy0 + il * WS, chan0 + o, row_bytes, bar);
-                bulk_g2s(copy1 + il * WS, chan1 + o, row_bytes, bar);
+                const int x = p.padl + t0 + gws[i];  // a multiple of 8 samples (32 bytes)
+                if (p.use_tma) {
+                    tma_load_3d(win + il * MBf, &p.tmap, x, i, 0, bar);
+                } else {
+                    const size_t o = (size_t)i * p.row + x;
+                    bulk_g2s(win + il * MBf, chan0 + o, row_bytes, bar);
+                    bulk_g2s(win + il * MBf + WS, chan1 + o, row_bytes, bar);
+                }
             }
             if (lane == 0) {
                 const size_t to = ((size_t)g * p.N + c0) * 8;
@@ -653,7 +698,7 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
                 bulk_g2s(s_w4, p.w4 + to * 4, 4 * tab_bytes, bar);
             }
         }
-        const bool ok = mbar_wait_bounded(bar, parity);
+        const bool ok = mbar_wait_sleep_bounded(bar, parity);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
                 atomicOr(p.err, kErrTimeout);
@@ -665,7 +710,7 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
 
         // (x, x+1), x = off + 2l + 64k: at x in copy 0 (even off) or at x - 1
         // in copy 1 (odd off); s_sel holds that byte offset for lane 0, k = 0
-        const unsigned char *base = reinterpret_cast<const unsigned char *>(copy0) + 8 * lane;
+        const unsigned char *base = reinterpret_cast<const unsigned char *>(win) + 8 * lane;
         const ulonglong2 *wq = reinterpret_cast<const ulonglong2 *>(s_w4) + warp;
 #pragma unroll 4
         for (int il = 0; il < nc; ++il) {
@@ -682,7 +727,7 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
 #pragma unroll
             for (int q = 0; q < NA; ++q) ve[q] = s_vext[q * 32];
             for (int il = lane; il < nc; il += 32)
-                accumulate_v<ORDER>(ve, copy0[il * WS + s_rel[il * 8 + warp] + kTile],
+                accumulate_v<ORDER>(ve, win[il * MBf + s_rel[il * 8 + warp] + kTile],
                                     s_w4[(il * 8 + warp) * 4 + 2]);
 #pragma unroll
             for (int q = 0; q < NA; ++q) s_vext[q * 32] = ve[q];

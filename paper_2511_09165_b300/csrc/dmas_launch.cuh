@@ -12,6 +12,9 @@
 
 namespace dmas {
 
+// A batch travels in the kernel's parameter space (at most 32764 bytes).
+static_assert(sizeof(BeamBatch) <= 32764, "BeamBatch exceeds the kernel parameter limit");
+
 // Dynamic shared memory a beamform kernel is allowed to request (the sm_100
 // family's per-CTA opt-in maximum, 227 KB).
 constexpr int kBeamSmemOptIn = 227 * 1024;

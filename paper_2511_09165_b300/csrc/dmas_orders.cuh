@@ -36,8 +36,6 @@
 // Waits on the stage barriers are bounded as in the single-order kernels.
 #pragma once
 
-#include <cuda.h>
-
 #include "dmas_launch.cuh"
 
 namespace dmas {
@@ -110,39 +108,6 @@ __device__ __forceinline__ int orders_stage_bytes_dev(int planes, bool lin, int 
                                                       int window) {
     return (mic_chunk * orders_mic_bytes_dev(planes, window) + mic_chunk * 32 +
             (lin ? mic_chunk * 128 : 0) + 127) & ~127;
-}
-
-// 3-D tensor copy global -> shared, completion counted in bytes on `bar`.
-__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1,
-                                            int c2, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
-        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_addr(bar))
-        : "memory");
-}
-
-// Bounded wait that lets the thread sleep in the barrier (up to a few
-// microseconds per try) instead of spinning on it, so waiting warps leave
-// their issue slots to the warps that compute.
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity), "r"(4000u)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_sleep_bounded(uint64_t *bar, uint32_t parity) {
-    if (mbar_try_wait_sleep(bar, parity)) return true;
-    const unsigned long long start = global_ns();
-    while (!mbar_try_wait_sleep(bar, parity)) {
-        if (global_ns() - start > kWaitLimitNs) return false;
-    }
-    return true;
 }
 
 constexpr unsigned long long kAbsMask2 = 0x7fffffff7fffffffull;

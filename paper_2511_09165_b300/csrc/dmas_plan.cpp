@@ -299,7 +299,7 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
                                      : kWindowSmemBudget - (pair ? 8 * 6 * 32 * 4 : 0);
     const size_t tab = (size_t)kGroup * 4 * (lin ? 2 : 1);
     const size_t per_mic = persistent ? 2 * ((size_t)window * eb + tab)
-                                      : (pair ? 2 * (size_t)window * eb + (size_t)kGroup * 24
+                                      : (pair ? lin_mic_bytes((int)window) + (size_t)kGroup * 24
                                               : (size_t)window * eb + tab);
     if (per_mic > budget)
         return fail("a direction group's delay spread does not fit in shared memory");
@@ -310,7 +310,7 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
         hp.mic_chunk = (N + n_chunks - 1) / n_chunks;
     }
     if (pair && lin) {
-        const size_t wb = pair_window_bytes(hp.mic_chunk, hp.window);
+        const size_t mb = lin_mic_bytes(hp.window);
         hp.gsel.assign(hp.rel.size(), 0);
         hp.gw4.assign(hp.rel.size() * 4, 0.0f);
         for (int g = 0; g < G; ++g)
@@ -318,8 +318,9 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
                 for (int s = 0; s < kGroup; ++s) {
                     const size_t o = ((size_t)g * N + i) * kGroup + s;
                     const int off = hp.rel[o];
-                    const size_t row = (size_t)(i % hp.mic_chunk) * hp.window * 4;
-                    hp.gsel[o] = (int32_t)(row + ((off & 1) ? wb + (size_t)(off - 1) * 4
+                    const size_t blk = (size_t)(i % hp.mic_chunk) * mb;
+                    hp.gsel[o] = (int32_t)(blk + ((off & 1) ? (size_t)hp.window * 4 +
+                                                                  (size_t)(off - 1) * 4
                                                             : (size_t)off * 4));
                     const float f = hp.gfrac[o];
                     hp.gw4[o * 4 + 0] = 1.0f - f;
