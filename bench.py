@@ -41,8 +41,8 @@ METRIC = "direction·samples/s for 5th-order DMAS+CF at N=32 mics; p50/p99 frame
 UNIT = "direction·samples/s"
 
 # MEASURED_PEAKS.json carries the HBM and tensor peaks; the FP32 ALU peak of
-# this path is derived from the unit counts: 148 SMs x 128 FP32 lanes x 2032 MHz.
-SM_COUNT = 148
+# this path is derived from the unit counts: the device's SM count x 128 FP32
+# lanes x the maximum SM clock (2032 MHz on B300).
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
 
@@ -82,6 +82,15 @@ WORKLOADS = {
         mf=True,
         text="3-D hemisphere as hemi_3d_n5 with chirp echoes and the matched filter "
              "(the emitted 2.5 ms 25-50 kHz chirp, 1125 taps) before the roots"),
+    "passive64_n3": dict(
+        scene=lambda: scenes.passive(seed=4, n_mics=64), order=3, mode="round",
+        text="passive as passive64_n5 at n=3"),
+    "passive64_n5_linear": dict(
+        scene=lambda: scenes.passive(seed=4, n_mics=64), order=5, mode="linear",
+        text="passive as passive64_n5 with linear (fractional) delays"),
+    "passive256_n3": dict(
+        scene=lambda: scenes.passive(seed=4, n_mics=256), order=3, mode="round",
+        text="passive as passive256_n5 at n=3"),
     "passive256_n5": dict(
         scene=lambda: scenes.passive(seed=4, n_mics=256), order=5, mode="round",
         text="passive: 256 mics in a 0.4 m square, 8192 az/el directions, 32768 samples "
@@ -244,9 +253,29 @@ def cpu_baseline(scene, order, linear, cf=True, mf=False, min_s=10.0) -> dict:
         total_s += dt
         reps += 1
     what = "all" if D == scene.n_dirs else f"directions 0..{D - 1} of"
+    # one core, on a smaller direction subset (about min_s / 4 seconds)
+    oracle.set_threads(1)
+    px1, dt1 = oracle_sample(scene, order, linear, 8, cf, mf)
+    D1 = int(max(8, min(scene.n_dirs, 0.25 * min_s * px1 / dt1 / scene.n_samples)))
+    px1, dt1 = oracle_sample(scene, order, linear, D1, cf, mf)
+    oracle.set_threads(cores)
     return {"value": total_px / total_s, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{reps} x ({what} {scene.n_dirs} directions x {scene.n_samples} "
-                      f"samples), {total_s:.1f} s, FP64"}
+                      f"samples), {total_s:.1f} s, FP64",
+            "single_core": {"value": px1 / dt1, "sample": f"directions 0..{D1 - 1}, "
+                                                          f"{dt1:.1f} s"},
+            "cpu_model": cpu_model()}
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def run_reference(args, wl, scene) -> None:
@@ -362,7 +391,8 @@ def run_ours(args, wl, scene) -> None:
     ops = algorithmic_ops_per_pixel(N, order, linear)
     beam_ms = float(np.mean(stage[:, 1]))
     env_ms = float(np.mean(stage[:, 2]))
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12   # T op/s
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12   # T op/s
     achieved = ops["beam_total"] * px / (beam_ms * 1e-3) / 1e12
     # the whole per-pixel path (beamform + envelope, L taps), as one roofline
     path_ops = ops["beam_total"] + info.env_taps
@@ -386,7 +416,8 @@ def run_ours(args, wl, scene) -> None:
         "roofline": {"bound": "alu", "kernel": "beamform_x2_kernel", "achieved": achieved,
                      "peak": peak, "unit": "Top/s", "frac": achieved / peak,
                      "ops_per_pixel": ops, "pixels_per_launch": px,
-                     "peak_source": "148 SMs x 128 FP32 lanes x 2032 MHz (unit counts)",
+                     "peak_source": f"{sms} SMs (device properties) x 128 FP32 lanes x "
+                                    f"{SM_MAX_MHZ:.0f} MHz (max SM clock)",
                      "traffic": beam_traffic(args.workload),
                      "algorithmic_bytes": px * 4 + N * T * 4 * (2 if linear else 1),
                      "path": {"stages": "beamform + envelope", "ops_per_pixel": path_ops,
@@ -640,7 +671,8 @@ def run_orders(args) -> None:
     clocks = ClockSampler(local)
     clocks.start()
     wall0 = time.time()
-    peak = SM_COUNT * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak = (torch.cuda.get_device_properties(dev).multi_processor_count * FP32_LANES_PER_SM *
+            SM_MAX_MHZ * 1e6 / 1e12)
     modes = []
 
     def timed(fn):
@@ -678,6 +710,10 @@ def run_orders(args) -> None:
                 pl(frame, out=images[i // 5, i % 5], stream=stream)
 
         sep_ms = timed(separate)
+        per_order = {}
+        for i, pl in enumerate(singles):
+            name = ("das" if i % 5 == 0 else "dmas%d" % (i % 5 + 1)) + ("_cf" if i >= 5 else "")
+            per_order[name] = timed(lambda: pl(frame, out=images[i // 5, i % 5], stream=stream))
         for pl in singles:
             pl.check()
             pl.close()
@@ -685,6 +721,7 @@ def run_orders(args) -> None:
         achieved = ops["beam_total"] * px / (st[1] * 1e-3) / 1e12
         modes.append({
             "delays": mode, "pass_ms": pass_ms, "separate_ms": sep_ms,
+            "single_call_ms": per_order,
             "speedup": sep_ms / pass_ms,
             "stage_ms": {"root planes": float(st[0]), "beamform (every order)": float(st[1]),
                          "envelope (10 images)": float(st[2])},
