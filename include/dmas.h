@@ -201,9 +201,9 @@ dmas_status dmas_beamform_orders(dmas_plan *plan, const float *d_frame, unsigned
  * Same as dmas_beamform but with HOST buffers: copies h_frame ([N][T] float32)
  * to the device, beamforms, copies the image back to h_image ([M][T] float32)
  * and synchronises `stream` before returning.  A large frame (at least 2^22
- * pixels) runs in 4 time chunks whose image columns download on a second,
- * plan-owned stream while the next chunk computes; the image is bitwise the
- * one dmas_beamform produces.  Pinned (page-locked) host memory gives the
+ * pixels) runs in time chunks (one per 2^21 pixels, 4 to 16) whose image
+ * columns download on a second, plan-owned stream while the next chunk
+ * computes; the image is bitwise the one dmas_beamform produces.  Pinned (page-locked) host memory gives the
  * fastest copies.  The device staging buffers, the copy stream and its events
  * are created on the first call and kept by the plan.  With stage profiling
  * on, the interleaved stages report as one: the whole frame under
