@@ -463,7 +463,8 @@ def run_serving(args) -> None:
     def run_server(rate, seed):
         offs, which, fidx = schedule(rate, seed)
         reqs = []
-        with serving.Server(sensors, budget_bytes=args.serve_budget_gb << 30, streams=2) as srv:
+        with serving.Server(sensors, budget_bytes=args.serve_budget_gb << 30, streams=2,
+                            bulk_streams=args.serve_bulk_streams) as srv:
             t0 = time.perf_counter() + 0.05
             for o, w, f in zip(offs, which, fidx):
                 while time.perf_counter() < t0 + o:
@@ -481,10 +482,14 @@ def run_serving(args) -> None:
         serving.one_frame_per_launch(sensors, reqs)
         return reqs, t0
 
+    fast = [sn.cost <= serving.FAST_COST for sn in sensors]
+
     def summary(reqs, t0, batches=None):
         done = [r for r in reqs if not r.rejected]
         span = max(r.t_done for r in done) - t0
         d = serving.latency_summary(reqs)
+        d["small_frames"] = serving.latency_summary([r for r in reqs if fast[r.sensor]])
+        d["big_frames"] = serving.latency_summary([r for r in reqs if not fast[r.sensor]])
         d["frames_per_s"] = len(done) / span
         d["dir_samples_per_s"] = sum(px[r.sensor] for r in done) / span
         d["rejected"] = sum(r.rejected for r in reqs)
@@ -524,6 +529,7 @@ def run_serving(args) -> None:
                    f"{args.serve_seconds:g} s each; latency = arrival to image resident "
                    "on the device; value = delivered direction*samples/s at the highest rate",
                    "budget_gb": args.serve_budget_gb, "streams": 2,
+                   "bulk_streams": args.serve_bulk_streams,
                    "sensors": [f"N{s.n_mics} M{s.n_dirs} T{s.n_samples} n{s.order}"
                                for s in mix]},
         "latency_ms": {"p50": top.get("p50_ms"), "p99": top.get("p99_ms")},
@@ -765,6 +771,7 @@ def main() -> None:
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 1000.0])
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-budget-gb", type=int, default=48)
+    ap.add_argument("--serve-bulk-streams", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -202,7 +202,7 @@ constexpr int kTcStageBytes = 2 * kTcBufBytes;  // A_hi (loaded raw, split in pl
 
 __global__ void __launch_bounds__(kTcThreadsWS, 1)
     envelope_tc_kernel(const __grid_constant__ EnvTcParams p) {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char env_smem[];
     __shared__ uint64_t full[kTcStages], split_done[kTcStages], empty[kTcStages];
     __shared__ uint64_t acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_slot;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
     const int H = p.H, HA = tc_halo(H), K = tc_K(H), Z = tc_Z(H);
     const int n_kb = (K + kTcKB - 1) / kTcKB;
     // the dynamic window starts 1024-aligned (its size has 1 KB to spare)
-    unsigned char *base = smem + ((1024u - (smem_addr(smem) & 1023u)) & 1023u);
+    unsigned char *base = env_smem + ((1024u - (smem_addr(env_smem) & 1023u)) & 1023u);
     float *s_taps = reinterpret_cast<float *>(base);                               // [2][4][Z]
     unsigned char *stages = base + (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023);  // [S][hi,lo]
     const unsigned n_tiles = (blockIdx.x < p.total_tiles)

@@ -64,6 +64,11 @@ class Sensor:
         return self.plan.n_mics * self.plan.n_dirs * self.plan.n_samples
 
 
+# Frames of at most this cost (microphones x directions x samples) take the
+# fast lane.
+FAST_COST = 1.3e9
+
+
 class _Lane:
     def __init__(self, name, streams, max_batch):
         self.name = name
@@ -102,7 +107,8 @@ class Server:
 
     def __init__(self, sensors, device=None, budget_bytes: int = 32 << 30,
                  max_batch: int = 64, streams: int = 2, copy_back: bool = False,
-                 fast_cost: float = 1.3e9, bulk_batch: int = 1, bulk_streams: int | None = 3):
+                 fast_cost: float = FAST_COST, bulk_batch: int = 1,
+                 bulk_streams: int | None = 3):
         import torch
         self.torch = torch
         self.sensors = list(sensors)
