@@ -139,6 +139,15 @@ def test_ragged_and_chunked():
         check_against_oracle(sc, img, cf, [1, 3, 5], dm.V_PLAIN | dm.V_CF, mode)
 
 
+@pytest.mark.parametrize("mode", ["round", "linear"])
+def test_frame_length_not_a_multiple_of_four(mode):
+    """T % 4 != 0: the envelope of the ten images takes its plain-load path and
+    the last time tile is ragged."""
+    sc = hemi(T=1501, M=100)
+    img, cf = run_orders(sc, 5, mode)
+    check_against_oracle(sc, img, cf, [1, 2, 3, 4, 5], dm.V_PLAIN | dm.V_CF, mode)
+
+
 def test_full_size_hemisphere_sampled_rows():
     """The 3-D frame in its benchmark size (2048 directions, 16384 samples,
     interpolated delays): rows sampled across the direction range."""
