@@ -1,12 +1,14 @@
 """The paper's qualitative image-quality claims (Sec. IV-A, Table I), checked
 on a seeded point-target scene: at 0 dB microphone SNR the image SNR (mean
 off-target level of the normalised image) rises with the DMAS order and the
-coherence factor raises it at every order.  The absolute values depend on
-details the paper does not give (array, pulse, target window) and are not
-pinned.
+coherence factor raises it at every order; without noise, the dynamic range
+of the directional point-spread function does the same.  The absolute values
+depend on details the paper does not give (array, pulse, target window) and
+are not pinned.
 
-CPU: the FP64 oracle shows the trend.  GPU: the CUDA path shows it and its
-image SNR agrees with the oracle's to 0.01 dB.
+CPU: the FP64 oracle shows the trends.  GPU: the CUDA path shows them; its
+image SNR agrees with the oracle's to 0.01 dB and its PSF dynamic range (all
+ten images from one every-order pass) to 0.5 dB.
 """
 import functools
 
@@ -64,3 +66,47 @@ def test_gpu_image_snr_matches_oracle_and_trend():
     ref = _oracle_snr()
     for k, v in got.items():
         assert abs(v - ref[k]) < 0.01, (k, v, ref[k])
+
+
+@functools.lru_cache(maxsize=None)
+def _psf_scene():
+    return scenes.point_target(float("inf"))
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_psf():
+    sc = _psf_scene()
+    az = sc.dir_azel[:, 0]
+    return {(n, cf): iq.psf_dynamic_range_db(oracle_run(sc, n, oracle.LINEAR, cf=cf)["img"],
+                                             az, 0.0)
+            for n in ORDERS for cf in (False, True)}
+
+
+def _assert_psf_trend(dr):
+    for cf in (False, True):
+        vals = [dr[(n, cf)] for n in ORDERS]
+        assert all(b > a + 3.0 for a, b in zip(vals, vals[1:])), (cf, vals)
+    for n in ORDERS:
+        assert dr[(n, True)] > dr[(n, False)] + 3.0, n
+
+
+def test_oracle_psf_dynamic_range_rises_with_order_and_cf():
+    _assert_psf_trend(_oracle_psf())
+
+
+@pytest.mark.gpu
+def test_gpu_psf_dynamic_range_matches_oracle_and_trend():
+    torch = pytest.importorskip("torch")
+    dm = pytest.importorskip("paper_2511_09165_b300")
+    sc = _psf_scene()
+    az = sc.dir_azel[:, 0]
+    plan = gpu_plan(dm, sc, 5, dm.LINEAR)
+    imgs = plan.beamform_orders(torch.from_numpy(sc.frame).cuda()).cpu().numpy()
+    plan.check()
+    plan.close()
+    got = {(n, cf): iq.psf_dynamic_range_db(imgs[int(cf), n - 1], az, 0.0)
+           for n in ORDERS for cf in (False, True)}
+    _assert_psf_trend(got)
+    ref = _oracle_psf()
+    for k, v in got.items():
+        assert abs(v - ref[k]) < 0.5, (k, v, ref[k])
