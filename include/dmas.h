@@ -154,6 +154,10 @@ dmas_status dmas_destroy(dmas_plan *plan);
  *   d_cf    : optional device [M][T] float32: the coherence factor.
  * The plan's scratch is reused by every call: calls on one plan must be
  * ordered on one stream (or synchronised); use one plan per concurrent stream.
+ * The call only enqueues kernels on `stream` (no allocation, no
+ * synchronisation, stage profiling off), so it can be captured into a CUDA
+ * graph; a replay reads whatever d_frame then holds and reuses the plan's
+ * scratch, under the same ordering rule.
  * Errors: DMAS_EINVAL (NULL plan/frame/image), DMAS_ECUDA (launch failure).
  * Device-side wait timeouts surface as DMAS_ETIMEOUT from dmas_plan_check.
  */
