@@ -19,25 +19,30 @@
 // the _hi parts rounded to TF32; each k-step issues A_hi.B_hi + A_hi.B_lo +
 // A_lo.B_hi (the dropped A_lo.B_lo term is ~2^-22 relative).
 //
-// A is held in the K-major layout with the 128-byte swizzle: for each 32-sample
-// column of a k-block ("atom"), row m occupies bytes [128 m, 128 m + 128) and
-// its 16-byte chunk c (samples 4c..4c+3) sits at chunk position c ^ (m & 7);
-// the pattern repeats every 8 rows (1024 bytes, so atoms are 1024-aligned).
-// TMA writes it directly from 128-byte rows of y, the split pass reads and
-// writes it without bank conflicts, and a k-step's descriptor starts 32 bytes
-// further into the atom.
+// The split |y| (A_hi, A_lo) is the MMA's A operand in tensor memory, so
+// shared memory feeds the tensor core only the taps (B): with A in shared
+// memory, the four phases x three products re-read the same A twelve times per
+// k-step and shared-memory bandwidth bound the kernel (L1 79 % busy).
 //
-// CTA: 10 warps, persistent over tiles (and over the frames of a batch), with
+// |y| is staged in the K-major layout with the 128-byte swizzle: for each
+// 32-sample column of a k-block ("atom"), row m occupies bytes
+// [128 m, 128 m + 128) and its 16-byte chunk c (samples 4c..4c+3) sits at
+// chunk position c ^ (m & 7); TMA writes it directly from 128-byte rows of y
+// and the split pass reads a row per thread without bank conflicts.
+//
+// CTA: 13 warps, persistent over tiles (and over the frames of a batch), with
 // warp roles: a producer stages each k-block of 64 samples of y by TMA (2-D
 // tensor map, two boxes of 32 samples x 128 rows; cp.async to the same layout
-// when T % 4 != 0) into one of 3 stages;
-// 4 split warps (one row per thread) replace it by |y| rounded to TF32 and
-// write the remainder as A_lo; one thread issues the k-block's 8 k-steps x 4
-// phases x 3 MMAs into one of two TMEM accumulators (2 x 256 columns) and
-// commits them to the stage's and, after a tile's last k-block, the
-// accumulator's mbarrier; 4 epilogue warps read their row of the finished
-// accumulator (TMEM lane = row) while the next tile accumulates, and store 8
-// consecutive outputs (one 32-byte sector) at a time.  Every wait is bounded.
+// when T % 4 != 0) into one of kTcStages shared-memory stages; 4 split warps
+// (one row per thread, the warp's TMEM lane quarter) read |y| rounded to TF32
+// and the remainder and store them (tcgen05.st) into one of two A stages in
+// TMEM (hi, lo: 2 x 64 columns); four MMA warps issue the k-block's 8 k-steps
+// x (one phase each) x 3 MMAs into the accumulator (4 x 64 columns) and commit
+// them to the A stage's and, after a tile's last k-block, the accumulator's
+// mbarrier; 4 epilogue warps read their row of the finished accumulator (TMEM
+// lane = row) and store 8 consecutive outputs (one 32-byte sector) at a time,
+// then release it to the next tile.  TMEM: accumulator columns 0..255, A
+// stages 256..511.  Every wait is bounded.
 #pragma once
 
 #include <cuda.h>
@@ -188,23 +193,47 @@ __device__ __forceinline__ TcTile tc_tile(const EnvTcParams &p, unsigned tile) {
     return {&jb, rb * kTcRows, (jb.tt0 + tt) * kTcJ};
 }
 
-// Warp roles: 0-3 split (one row each), 4-7 epilogue (TMEM lane quarters),
-// 8 producer, 9.. MMA issue (lane 0 of each; warp 9 also allocates TMEM).  A
-// tcgen05.mma costs its issuing thread tens of cycles (measured: ~70 per
-// M=128 N=64 K=8 instruction), more than the tensor core needs to run it, so
+// Warp roles: 0-3 split (one row each, TMEM lane quarters), 4-7 epilogue
+// (TMEM lane quarters), 8 producer, 9.. MMA issue (lane 0 of each; warp 9 also
+// allocates TMEM).  A tcgen05.mma costs its issuing thread tens of cycles, so
 // the phases are spread over kTcMmaWarps issuing warps.
-constexpr int kTcStages = 3;
-constexpr int kTcMmaWarps = 2;
+constexpr int kTcStages = 4;
+constexpr int kTcMmaWarps = 4;
 constexpr int kTcPhasesPerWarp = 4 / kTcMmaWarps;
 constexpr int kTcWarps = 9 + kTcMmaWarps;
 constexpr int kTcThreadsWS = kTcWarps * 32;
-constexpr int kTcStageBytes = 2 * kTcBufBytes;  // A_hi (loaded raw, split in place) + A_lo
+constexpr int kTcStageBytes = kTcBufBytes;  // |y| of one k-block, FP32
+constexpr uint32_t kTcACol0 = 4 * kTcNq;    // first TMEM column of the A stages
+constexpr uint32_t kTcACols = 2 * kTcKB;    // one A stage: hi then lo
+
+__device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
+                                          uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 32 consecutive TMEM columns of this thread's lane (warp-collective)
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+        "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]),
+        "f"(v[8]), "f"(v[9]), "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]),
+        "f"(v[15]), "f"(v[16]), "f"(v[17]), "f"(v[18]), "f"(v[19]), "f"(v[20]), "f"(v[21]),
+        "f"(v[22]), "f"(v[23]), "f"(v[24]), "f"(v[25]), "f"(v[26]), "f"(v[27]), "f"(v[28]),
+        "f"(v[29]), "f"(v[30]), "f"(v[31])
+        : "memory");
+}
 
 __global__ void __launch_bounds__(kTcThreadsWS, 1)
     envelope_tc_kernel(const __grid_constant__ EnvTcParams p) {
     extern __shared__ __align__(128) unsigned char env_smem[];
-    __shared__ uint64_t full[kTcStages], split_done[kTcStages], empty[kTcStages];
-    __shared__ uint64_t acc_full[2], acc_empty[2];
+    __shared__ uint64_t full[kTcStages], empty[kTcStages];
+    __shared__ uint64_t a_full[2], a_empty[2], acc_full, acc_empty;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -213,7 +242,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
     // the dynamic window starts 1024-aligned (its size has 1 KB to spare)
     unsigned char *base = env_smem + ((1024u - (smem_addr(env_smem) & 1023u)) & 1023u);
     float *s_taps = reinterpret_cast<float *>(base);                               // [2][4][Z]
-    unsigned char *stages = base + (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023);  // [S][hi,lo]
+    unsigned char *stages = base + (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023);  // [S]
     const unsigned n_tiles = (blockIdx.x < p.total_tiles)
                                  ? (p.total_tiles - 1 - blockIdx.x) / gridDim.x + 1
                                  : 0;
@@ -228,14 +257,15 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
     }
     if (tid == 0) {
         for (int s = 0; s < kTcStages; ++s) {
-            mbar_init(&full[s], 1);         // producer lane 0 (+ bytes or cp.async arrivals)
-            mbar_init(&split_done[s], 128); // split threads
-            mbar_init(&empty[s], kTcMmaWarps);  // MMA commits
+            mbar_init(&full[s], 1);     // producer lane 0 (+ bytes or cp.async arrivals)
+            mbar_init(&empty[s], 128);  // split threads, once they have read the stage
         }
         for (int a = 0; a < 2; ++a) {
-            mbar_init(&acc_full[a], kTcMmaWarps);  // MMA commits after a tile's last k-block
-            mbar_init(&acc_empty[a], 128);  // epilogue threads
+            mbar_init(&a_full[a], 128);          // split threads, after their TMEM stores
+            mbar_init(&a_empty[a], kTcMmaWarps); // MMA commits of the k-block that read it
         }
+        mbar_init(&acc_full, kTcMmaWarps);  // MMA commits after a tile's last k-block
+        mbar_init(&acc_empty, 128);         // epilogue threads
         abort_flag = 0;
         fence_mbar_init();
     }
@@ -300,30 +330,44 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
             }
         }
     } else if (warp < 4) {
-        // -------------------------- split |y| -> hi, lo ---------------------
-        const int m = tid;  // row of the tile
+        // ---------------------- split |y| -> hi, lo into TMEM ---------------
+        const int m = tid;  // row of the tile = TMEM lane (warp w owns lanes 32w..)
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
         unsigned g = 0;
         for (unsigned i = 0; i < n_tiles; ++i) {
             for (int kb = 0; kb < n_kb; ++kb, ++g) {
                 const int s = (int)(g % kTcStages);
+                const int t = (int)(g & 1u);
                 if (!wait(&full[s], (g / kTcStages) & 1u)) goto done;
-                float *ahi = reinterpret_cast<float *>(stages + (size_t)s * kTcStageBytes);
-                float *alo = ahi + kTcBufBytes / 4;
-                const int nc4 = min(kTcKB, K - kb * kTcKB) / 4;
-#pragma unroll 4
-                for (int c = 0; c < nc4; ++c) {
-                    const int off = sw128_off(m, c) >> 2;
-                    const float4 v = *reinterpret_cast<const float4 *>(ahi + off);
-                    float4 h, l;
-                    h.x = tf32_round(fabsf(v.x)); l.x = fabsf(v.x) - h.x;
-                    h.y = tf32_round(fabsf(v.y)); l.y = fabsf(v.y) - h.y;
-                    h.z = tf32_round(fabsf(v.z)); l.z = fabsf(v.z) - h.z;
-                    h.w = tf32_round(fabsf(v.w)); l.w = fabsf(v.w) - h.w;
-                    *reinterpret_cast<float4 *>(ahi + off) = h;
-                    *reinterpret_cast<float4 *>(alo + off) = l;
+                // the MMAs of k-block g - 2 have finished reading A stage t
+                if (g >= 2 && !wait(&a_empty[t], ((g >> 1) - 1) & 1u)) goto done;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const float *ay = reinterpret_cast<const float *>(stages + (size_t)s * kTcStageBytes);
+                const uint32_t acol = kTcACol0 + (uint32_t)t * kTcACols;
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    float h[32], l[32];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const float4 v = *reinterpret_cast<const float4 *>(
+                            ay + (sw128_off(m, 8 * half + c) >> 2));
+                        const float x[4] = {fabsf(v.x), fabsf(v.y), fabsf(v.z), fabsf(v.w)};
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            h[4 * c + e] = tf32_round(x[e]);
+                            l[4 * c + e] = x[e] - h[4 * c + e];
+                        }
+                    }
+                    tmem_st32(lane_base + acol + (uint32_t)(32 * half), h);
+                    tmem_st32(lane_base + acol + (uint32_t)(kTcKB + 32 * half), l);
                 }
+                // the stage has been read: order these reads before the
+                // producer's next bulk copy into it
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(&split_done[s]);
+                mbar_arrive(&empty[s]);
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(&a_full[t]);
             }
         }
     } else if (warp >= 9) {
@@ -333,25 +377,20 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
         const uint32_t taps_base = smem_addr(s_taps);
         unsigned g = 0;
         for (unsigned i = 0; i < n_tiles; ++i) {
-            const int a = (int)(i & 1u);
-            // the epilogue must have drained this accumulator (tile i - 2)
-            if (i >= 2 && !wait(&acc_empty[a], ((i >> 1) - 1) & 1u)) goto done;
+            // the epilogue must have drained the accumulator (tile i - 1)
+            if (i >= 1 && !wait(&acc_empty, (i - 1) & 1u)) goto done;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t dacc = tmem + (uint32_t)(a * 256);
             for (int kb = 0; kb < n_kb; ++kb, ++g) {
-                const int s = (int)(g % kTcStages);
-                if (!wait(&split_done[s], (g / kTcStages) & 1u)) goto done;
+                const int t = (int)(g & 1u);
+                if (!wait(&a_full[t], (g >> 1) & 1u)) goto done;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 if (lane == 0) {
-                    const uint32_t a_hi = smem_addr(stages + (size_t)s * kTcStageBytes);
                     const int u0 = kb * kTcKB;
                     const int nks = min(kTcKB, K - u0) / 8;
-                    // descriptors of the k-block's first k-step.  A (128-byte swizzle,
-                    // 8-row groups 1024 B apart): a k-step of 8 samples advances 32 B
-                    // within an atom column, the fifth starts the next atom column.
-                    // B advances 8 samples (32 B).  Both in 16-byte address units.
-                    const uint64_t dah0 = smem_desc(a_hi, 16, 1024, 2);
-                    const uint64_t dal0 = smem_desc(a_hi + kTcBufBytes, 16, 1024, 2);
+                    // A: 8 TMEM columns per k-step (hi, then lo 64 columns on);
+                    // B: the phase's tap array, 8 samples (32 B) per k-step, in
+                    // 16-byte descriptor units
+                    const uint32_t a_hi = tmem + kTcACol0 + (uint32_t)t * kTcACols;
                     uint64_t dbh0[kTcPhasesPerWarp], dbl0[kTcPhasesPerWarp];
 #pragma unroll
                     for (int rr = 0; rr < kTcPhasesPerWarp; ++rr) {
@@ -363,23 +402,21 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
 #pragma unroll
                     for (int ks = 0; ks < kTcKB / 8; ++ks) {
                         if (ks < nks) {
-                            const uint64_t da =
-                                (uint64_t)((ks >> 2) * (kTcAtomBytes >> 4) + (ks & 3) * 2);
-                            const uint64_t dah = dah0 + da;
-                            const uint64_t dal = dal0 + da;
+                            const uint32_t ah = a_hi + (uint32_t)(8 * ks);
+                            const uint32_t al = ah + (uint32_t)kTcKB;
 #pragma unroll
                             for (int rr = 0; rr < kTcPhasesPerWarp; ++rr) {
-                                const uint32_t d = dacc + (uint32_t)((r0 + rr) * kTcNq);
+                                const uint32_t d = tmem + (uint32_t)((r0 + rr) * kTcNq);
                                 const uint64_t dbh = dbh0[rr] + (uint64_t)(2 * ks);
                                 const uint64_t dbl = dbl0[rr] + (uint64_t)(2 * ks);
-                                tc_mma(d, dah, dbh, idesc, (ks > 0) ? 1u : acc0);
-                                tc_mma(d, dah, dbl, idesc, 1u);
-                                tc_mma(d, dal, dbh, idesc, 1u);
+                                tc_mma_ts(d, ah, dbh, idesc, (ks > 0) ? 1u : acc0);
+                                tc_mma_ts(d, ah, dbl, idesc, 1u);
+                                tc_mma_ts(d, al, dbh, idesc, 1u);
                             }
                         }
                     }
-                    tc_commit(&empty[s]);                     // stage s may be refilled
-                    if (kb == n_kb - 1) tc_commit(&acc_full[a]);  // the tile is complete
+                    tc_commit(&a_empty[t]);                    // A stage t may be refilled
+                    if (kb == n_kb - 1) tc_commit(&acc_full);  // the tile is complete
                 }
                 __syncwarp();
             }
@@ -389,12 +426,11 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
         const int m = (warp & 3) * 32 + lane;  // TMEM lane = row of the tile
         const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         for (unsigned i = 0; i < n_tiles; ++i) {
-            const int a = (int)(i & 1u);
             const TcTile tl = tc_tile(p, blockIdx.x + i * gridDim.x);
             const EnvTcJob &jb = *tl.job;
             const bool vec = (jb.T & 3) == 0;
             const bool vec8 = (jb.T & 7) == 0 && (reinterpret_cast<uintptr_t>(jb.img) & 31) == 0;
-            if (!wait(&acc_full[a], (i >> 1) & 1u)) goto done;
+            if (!wait(&acc_full, i & 1u)) goto done;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int row = tl.row0 + m;
             const bool row_ok = row < jb.M;
@@ -404,7 +440,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                 float v[4][16];
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
-                    tmem_ld16(lane_base + (uint32_t)(a * 256 + r * kTcNq + qc), v[r]);
+                    tmem_ld16(lane_base + (uint32_t)(r * kTcNq + qc), v[r]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (row_ok && vec8 && tl.t0 + 4 * (kTcNq - qc) <= jb.T) {
                     // the 64 outputs are whole: 8 aligned sectors, columns k + 1 and k
@@ -432,7 +468,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(&acc_empty[a]);
+            mbar_arrive(&acc_empty);
         }
     }
 done:
