@@ -52,9 +52,9 @@
 namespace dmas {
 
 constexpr int kTcRows = 128;         // direction rows per tile (MMA M)
-constexpr int kTcJ = 256;            // output samples per tile
+constexpr int kTcJ = 192;            // output samples per tile
 constexpr int kTcNq = kTcJ / 4;      // columns per phase (MMA N)
-constexpr int kTcKB = 64;            // samples per k-block
+constexpr int kTcKB = 32;            // samples per k-block
 constexpr int kTcAtomK = 32;         // samples per 128-byte swizzle atom column
 constexpr int kTcAtomBytes = kTcRows * 128;  // one atom column of 128 rows
 constexpr int kTcBufBytes = kTcRows * kTcKB * 4;  // one of A_hi / A_lo for a k-block
@@ -197,13 +197,14 @@ __device__ __forceinline__ TcTile tc_tile(const EnvTcParams &p, unsigned tile) {
 // (TMEM lane quarters), 8 producer, 9.. MMA issue (lane 0 of each; warp 9 also
 // allocates TMEM).  A tcgen05.mma costs its issuing thread tens of cycles, so
 // the phases are spread over kTcMmaWarps issuing warps.
-constexpr int kTcStages = 4;
+constexpr int kTcStages = 6;
 constexpr int kTcMmaWarps = 4;
 constexpr int kTcPhasesPerWarp = 4 / kTcMmaWarps;
 constexpr int kTcWarps = 9 + kTcMmaWarps;
 constexpr int kTcThreadsWS = kTcWarps * 32;
 constexpr int kTcStageBytes = kTcBufBytes;  // |y| of one k-block, FP32
-constexpr uint32_t kTcACol0 = 4 * kTcNq;    // first TMEM column of the A stages
+constexpr uint32_t kTcAccCols = 4 * kTcNq;  // one accumulator (4 phases)
+constexpr uint32_t kTcACol0 = 2 * kTcAccCols;  // first TMEM column of the A stages
 constexpr uint32_t kTcACols = 2 * kTcKB;    // one A stage: hi then lo
 
 __device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
     envelope_tc_kernel(const __grid_constant__ EnvTcParams p) {
     extern __shared__ __align__(128) unsigned char env_smem[];
     __shared__ uint64_t full[kTcStages], empty[kTcStages];
-    __shared__ uint64_t a_full[2], a_empty[2], acc_full, acc_empty;
+    __shared__ uint64_t a_full[2], a_empty[2], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -264,8 +265,10 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
             mbar_init(&a_full[a], 128);          // split threads, after their TMEM stores
             mbar_init(&a_empty[a], kTcMmaWarps); // MMA commits of the k-block that read it
         }
-        mbar_init(&acc_full, kTcMmaWarps);  // MMA commits after a tile's last k-block
-        mbar_init(&acc_empty, 128);         // epilogue threads
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], kTcMmaWarps);  // MMA commits after a tile's last k-block
+            mbar_init(&acc_empty[a], 128);         // epilogue threads
+        }
         abort_flag = 0;
         fence_mbar_init();
     }
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                 const float *ay = reinterpret_cast<const float *>(stages + (size_t)s * kTcStageBytes);
                 const uint32_t acol = kTcACol0 + (uint32_t)t * kTcACols;
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
+                for (int half = 0; half < kTcKB / 32; ++half) {
                     float h[32], l[32];
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
@@ -377,9 +380,11 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
         const uint32_t taps_base = smem_addr(s_taps);
         unsigned g = 0;
         for (unsigned i = 0; i < n_tiles; ++i) {
-            // the epilogue must have drained the accumulator (tile i - 1)
-            if (i >= 1 && !wait(&acc_empty, (i - 1) & 1u)) goto done;
+            const int a = (int)(i & 1u);
+            // the epilogue must have drained this accumulator (tile i - 2)
+            if (i >= 2 && !wait(&acc_empty[a], ((i >> 1) - 1) & 1u)) goto done;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t dacc = tmem + (uint32_t)a * kTcAccCols;
             for (int kb = 0; kb < n_kb; ++kb, ++g) {
                 const int t = (int)(g & 1u);
                 if (!wait(&a_full[t], (g >> 1) & 1u)) goto done;
@@ -406,7 +411,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                             const uint32_t al = ah + (uint32_t)kTcKB;
 #pragma unroll
                             for (int rr = 0; rr < kTcPhasesPerWarp; ++rr) {
-                                const uint32_t d = tmem + (uint32_t)((r0 + rr) * kTcNq);
+                                const uint32_t d = dacc + (uint32_t)((r0 + rr) * kTcNq);
                                 const uint64_t dbh = dbh0[rr] + (uint64_t)(2 * ks);
                                 const uint64_t dbl = dbl0[rr] + (uint64_t)(2 * ks);
                                 tc_mma_ts(d, ah, dbh, idesc, (ks > 0) ? 1u : acc0);
@@ -416,7 +421,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                         }
                     }
                     tc_commit(&a_empty[t]);                    // A stage t may be refilled
-                    if (kb == n_kb - 1) tc_commit(&acc_full);  // the tile is complete
+                    if (kb == n_kb - 1) tc_commit(&acc_full[a]);  // the tile is complete
                 }
                 __syncwarp();
             }
@@ -426,11 +431,12 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
         const int m = (warp & 3) * 32 + lane;  // TMEM lane = row of the tile
         const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
         for (unsigned i = 0; i < n_tiles; ++i) {
+            const int a = (int)(i & 1u);
             const TcTile tl = tc_tile(p, blockIdx.x + i * gridDim.x);
             const EnvTcJob &jb = *tl.job;
             const bool vec = (jb.T & 3) == 0;
             const bool vec8 = (jb.T & 7) == 0 && (reinterpret_cast<uintptr_t>(jb.img) & 31) == 0;
-            if (!wait(&acc_full, i & 1u)) goto done;
+            if (!wait(&acc_full[a], (i >> 1) & 1u)) goto done;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const int row = tl.row0 + m;
             const bool row_ok = row < jb.M;
@@ -440,7 +446,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                 float v[4][16];
 #pragma unroll
                 for (int r = 0; r < 4; ++r)
-                    tmem_ld16(lane_base + (uint32_t)(r * kTcNq + qc), v[r]);
+                    tmem_ld16(lane_base + (uint32_t)a * kTcAccCols + (uint32_t)(r * kTcNq + qc), v[r]);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (row_ok && vec8 && tl.t0 + 4 * (kTcNq - qc) <= jb.T) {
                     // the 64 outputs are whole: 8 aligned sectors, columns k + 1 and k
@@ -468,7 +474,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            mbar_arrive(&acc_empty);
+            mbar_arrive(&acc_empty[a]);
         }
     }
 done:
