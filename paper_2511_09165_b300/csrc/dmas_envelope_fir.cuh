@@ -12,7 +12,7 @@
 
 namespace dmas {
 
-constexpr int kFirTile = 192;  // outputs per CTA (one per thread)
+constexpr int kFirTile = 128;  // outputs per CTA (one per thread)
 constexpr int kFirMaxH = 511;  // taps up to 1023
 
 struct EnvFirJob {

@@ -52,9 +52,9 @@
 namespace dmas {
 
 constexpr int kTcRows = 128;         // direction rows per tile (MMA M)
-constexpr int kTcJ = 192;            // output samples per tile
+constexpr int kTcJ = 128;            // output samples per tile
 constexpr int kTcNq = kTcJ / 4;      // columns per phase (MMA N)
-constexpr int kTcKB = 32;            // samples per k-block
+constexpr int kTcKB = 64;            // samples per k-block
 constexpr int kTcAtomK = 32;         // samples per 128-byte swizzle atom column
 constexpr int kTcAtomBytes = kTcRows * 128;  // one atom column of 128 rows
 constexpr int kTcBufBytes = kTcRows * kTcKB * 4;  // one of A_hi / A_lo for a k-block
