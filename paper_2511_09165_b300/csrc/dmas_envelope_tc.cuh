@@ -1,7 +1,7 @@
 // Envelope low-pass on the tensor cores (tcgen05, kind::tf32).
 //
 // The FIR  e[d][t] = sum_x g[x] |y[d][t - H + x]|  (g the symmetric taps,
-// x = 0..2H) is, for a tile of 128 direction rows and J = 256 output samples
+// x = 0..2H) is, for a tile of 128 direction rows and J = 128 output samples
 // starting at t0, the product  E[128][J] = A[128][K] . B[K][J]  with
 //   A[m][u] = |y[d0 + m][t0 - HA + u]|        (u = 0..K-1, K = J + 2 HA)
 //   B[u][j] = g~[u - j]                        (a band: the taps slid by j)
@@ -10,10 +10,13 @@
 // contiguous in t).  B is K-major too, but its rows are the tap vector slid by
 // one sample each, and a shared-memory matrix descriptor can only step rows by
 // 16 bytes (4 samples): so the J outputs are taken as 4 phases r (j = 4q + r),
-// and phase r's 64 columns, in reverse order of q, are rows of a tap array
+// and phase r's J/4 columns, in reverse order of q, are rows of a tap array
 // that step by exactly 16 bytes -- one descriptor over one array per phase, no
 // Toeplitz matrix materialised.  Phase r accumulates into TMEM columns
-// [64 r, 64 r + 64).
+// [r J/4, (r + 1) J/4) of its accumulator.  A shorter tile wastes less of K on
+// the band's zeros (each output needs 2H + 1 of its tile's K = J + 2 HA):
+// measured on B300, J = 128 is fastest (J = 256: 131 us, 192: 120 us, 128:
+// 110 us, 64: 161 us for a 2048 x 16384 frame).
 //
 // FP32 accuracy from TF32 products: A = A_hi + A_lo and g = g_hi + g_lo with
 // the _hi parts rounded to TF32; each k-step issues A_hi.B_hi + A_hi.B_lo +
@@ -37,12 +40,12 @@
 // (one row per thread, the warp's TMEM lane quarter) read |y| rounded to TF32
 // and the remainder and store them (tcgen05.st) into one of two A stages in
 // TMEM (hi, lo: 2 x 64 columns); four MMA warps issue the k-block's 8 k-steps
-// x (one phase each) x 3 MMAs into the accumulator (4 x 64 columns) and commit
-// them to the A stage's and, after a tile's last k-block, the accumulator's
-// mbarrier; 4 epilogue warps read their row of the finished accumulator (TMEM
-// lane = row) and store 8 consecutive outputs (one 32-byte sector) at a time,
-// then release it to the next tile.  TMEM: accumulator columns 0..255, A
-// stages 256..511.  Every wait is bounded.
+// x (one phase each) x 3 MMAs into one of two accumulators (4 x J/4 columns)
+// and commit them to the A stage's and, after a tile's last k-block, the
+// accumulator's mbarrier; 4 epilogue warps read their row of a finished
+// accumulator (TMEM lane = row) and store 8 consecutive outputs (one 32-byte
+// sector) at a time while the next tile accumulates into the other.  TMEM:
+// accumulators from column 0, A stages after them.  Every wait is bounded.
 #pragma once
 
 #include <cuda.h>
