@@ -120,6 +120,13 @@ struct dmas_plan {
     // matched-filtered frame; allocated by its first call, grown on demand
     void *d_orders = nullptr;
     size_t orders_bytes = 0;
+    // the last tensor maps encoded for this plan (the envelope's view of a y
+    // buffer, the interpolated-delay beamform's view of its root rows), reused
+    // while the buffer is the same: encoding is host work on every call
+    mutable std::mutex map_mu;
+    mutable CUtensorMap env_map{}, beam_map{};
+    mutable const void *env_map_ptr = nullptr, *beam_map_ptr = nullptr;
+    mutable int env_map_rows = -1;
 };
 
 namespace {
@@ -205,11 +212,25 @@ size_t beam_smem_bytes(const HostPlan &hp) {
     return 128 + win + tabs;
 }
 
+// Dynamic shared memory the tensor-core envelope may take (its opt-in below;
+// the kernel also has ~1 KB of static shared memory).
+constexpr size_t kEnvSmemMax = 222 * 1024;
+
+// Shared-memory stages of the tensor-core envelope: as many as fit beside the
+// taps (long filters have long tap arrays), at most kTcStages.
+int env_tc_stages(const HostPlan &hp) {
+    if (hp.L == 0) return 0;
+    const size_t taps = ((size_t)8 * tc_Z((hp.L - 1) / 2) * 4 + 1023) & ~(size_t)1023;
+    const size_t room = kEnvSmemMax - 1024 - taps;
+    return (int)std::min<size_t>((size_t)kTcStages, room / kTcStageBytes);
+}
+
 size_t env_smem_bytes(const HostPlan &hp) {
     if (hp.L == 0) return 0;
     const int Z = tc_Z((hp.L - 1) / 2);
     // + 1 KB: the kernel aligns its stages to 1024 bytes (the 128-byte swizzle period)
-    return 1024 + (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023) + (size_t)kTcStages * kTcStageBytes;
+    return 1024 + (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023) +
+           (size_t)env_tc_stages(hp) * kTcStageBytes;
 }
 
 // TF32 rounding (nearest, ties away from zero) of a finite float, as cvt.rna.
@@ -249,7 +270,8 @@ cudaError_t launch_env_tc(const EnvTcParams &ep, unsigned grid, size_t smem, cud
     std::call_once(once, [&] {
         // the kernel also has ~1 KB of static shared memory (barriers, TMEM slot)
         attr = cudaFuncSetAttribute(envelope_tc_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 222 * 1024);
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kEnvSmemMax);
     });
     if (attr != cudaSuccess) return attr;
     envelope_tc_kernel<<<grid, kTcThreadsWS, smem, s>>>(ep);
@@ -285,7 +307,11 @@ EnvTcJob env_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned
     std::memset(&j, 0, sizeof(j));
     j.use_tma = 0;
     if ((p->hp.T & 3) == 0 && ((uintptr_t)ybuf & 15) == 0) {
-        if (EncodeTiledFn enc = encode_tiled()) {
+        std::lock_guard<std::mutex> lock(p->map_mu);
+        if (p->env_map_ptr == ybuf && p->env_map_rows == rows) {
+            j.tmap = p->env_map;
+            j.use_tma = 1;
+        } else if (EncodeTiledFn enc = encode_tiled()) {
             cuuint64_t dims[2] = {(cuuint64_t)p->hp.T, (cuuint64_t)rows};
             cuuint64_t strides[1] = {(cuuint64_t)p->hp.T * 4};
             cuuint32_t box[2] = {kTcAtomK, kTcRows};
@@ -293,8 +319,12 @@ EnvTcJob env_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned
             if (enc(&j.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ybuf, dims, strides, box,
                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
                 j.use_tma = 1;
+                p->env_map = j.tmap;
+                p->env_map_ptr = ybuf;
+                p->env_map_rows = rows;
+            }
         }
     }
     j.y = ybuf;
@@ -313,13 +343,13 @@ unsigned env_tiles(const dmas_plan *p, int rows = 0) {
                       (((size_t)p->hp.T + kTcJ - 1) / kTcJ));
 }
 
-// Small frames take the CUDA-core FIR: at most 1.5e8 tap products (M T L), about
-// what one wave of tensor-core tiles costs (measured on B300: the 2-D frame,
-// 91 x 4096 x 181 = 6.7e7, runs 23 us there against ~50 us on the tensor
-// cores; 250 x 16384 x 181 = 7.4e8 runs faster on the tensor cores).  A
-// property of the plan, so a frame gets the same kernel alone and in a batch.
+// Only tiny frames take the CUDA-core FIR: at most 2e7 tap products (M T L).
+// Measured on B300 with the tensor-memory envelope: the 2-D frame, 91 x 4096 x
+// 181 = 6.7e7, runs 15.4 us on the tensor cores against 18.4 us on the CUDA
+// cores, 150 x 4096 x 181 17.4 against 26.6 us.  A property of the plan, so a
+// frame gets the same kernel alone and in a batch.
 bool env_on_cuda_cores(const dmas_plan *p) {
-    return (double)p->hp.M * (double)p->hp.T * (double)p->hp.L <= 1.5e8;
+    return (double)p->hp.M * (double)p->hp.T * (double)p->hp.L <= 2e7;
 }
 
 EnvFirJob fir_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned first,
@@ -392,7 +422,11 @@ BeamParams beam_params(const dmas_plan *p, void *scratch, float *ybuf, float *d_
     std::memset(&bp, 0, sizeof(bp));
     bp.use_tma = 0;
     if (uses_shifted_rows(hp.chan_prec, hp.order, hp.delay_mode) && hp.window <= kTmaMaxBox) {
-        if (EncodeTiledFn enc = encode_tiled()) {
+        std::lock_guard<std::mutex> lock(p->map_mu);
+        if (p->beam_map_ptr == scratch) {
+            bp.tmap = p->beam_map;
+            bp.use_tma = 1;
+        } else if (EncodeTiledFn enc = encode_tiled()) {
             // root rows [N][row], then their shifted copies: one box per
             // microphone, its window in both
             cuuint64_t dims[3] = {(cuuint64_t)hp.row, (cuuint64_t)hp.N, 2};
@@ -402,8 +436,11 @@ BeamParams beam_params(const dmas_plan *p, void *scratch, float *ybuf, float *d_
             if (enc(&bp.tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, scratch, dims, strides, box, es,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
                 bp.use_tma = 1;
+                p->beam_map = bp.tmap;
+                p->beam_map_ptr = scratch;
+            }
         }
     }
     bp.chan = scratch;
@@ -544,6 +581,7 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
     ep.job[0] = env_job(p, ybuf, d_image, 0);
     ep.total_tiles = env_tiles(p);
     ep.H = (hp.L - 1) / 2;
+    ep.n_stages = env_tc_stages(hp);
     ep.taps = p->d_taps_tc;
     ep.err = p->d_err;
     e = launch_env_tc(ep, std::min<unsigned>(ep.total_tiles, (unsigned)p->num_sms), p->smem_env, s);
@@ -619,6 +657,7 @@ dmas_status enqueue_host_chunks(dmas_plan *p, const float *d_frame, float *d_ima
             ep.job[0].t_tiles = u_hi - u_lo;
             ep.total_tiles = (unsigned)((hp.M + kTcRows - 1) / kTcRows) * (unsigned)(u_hi - u_lo);
             ep.H = H;
+            ep.n_stages = env_tc_stages(hp);
             ep.taps = p->d_taps_tc;
             ep.err = p->d_err;
             e = launch_env_tc(ep, std::min<unsigned>(ep.total_tiles, (unsigned)p->num_sms),
@@ -778,6 +817,7 @@ dmas_status enqueue_batch(const std::vector<BatchEntry> &v, cudaStream_t s) {
             const dmas_plan *pa = v[cls[b0]].plan;
             ep.total_tiles = tiles;
             ep.H = (a.L - 1) / 2;
+            ep.n_stages = env_tc_stages(a);
             ep.taps = pa->d_taps_tc;
             ep.err = pa->d_err;
             e = launch_env_tc(ep, std::min<unsigned>(tiles, (unsigned)pa->num_sms), pa->smem_env, s);
@@ -912,6 +952,7 @@ dmas_status enqueue_orders(dmas_plan *p, const float *d_frame, unsigned mask, in
             ep.job[0] = env_job(p, ybuf, d_images, 0, rows);
             ep.total_tiles = env_tiles(p, rows);
             ep.H = (hp.L - 1) / 2;
+            ep.n_stages = env_tc_stages(hp);
             ep.taps = p->d_taps_tc;
             ep.err = p->d_err;
             e = launch_env_tc(ep, std::min<unsigned>(ep.total_tiles, (unsigned)p->num_sms),

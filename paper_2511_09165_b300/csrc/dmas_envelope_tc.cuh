@@ -36,7 +36,8 @@
 // CTA: 13 warps, persistent over tiles (and over the frames of a batch), with
 // warp roles: a producer stages each k-block of 64 samples of y by TMA (2-D
 // tensor map, two boxes of 32 samples x 128 rows; cp.async to the same layout
-// when T % 4 != 0) into one of kTcStages shared-memory stages; 4 split warps
+// when T % 4 != 0) into one of n_stages shared-memory stages (up to
+// kTcStages: as many as fit beside the taps); 4 split warps
 // (one row per thread, the warp's TMEM lane quarter) read |y| rounded to TF32
 // and the remainder and store them (tcgen05.st) into one of two A stages in
 // TMEM (hi, lo: 2 x 64 columns); four MMA warps issue the k-block's 8 k-steps
@@ -85,6 +86,7 @@ struct EnvTcParams {
     int count;
     unsigned total_tiles;
     int H;
+    int n_stages;       // shared-memory stages of |y|, 2..kTcStages
     const float *taps;  // [2][4][Z]: hi then lo, phase r = 0..3 (device)
     unsigned *err;
     EnvTcJob job[kBatchMax];
@@ -200,7 +202,7 @@ __device__ __forceinline__ TcTile tc_tile(const EnvTcParams &p, unsigned tile) {
 // (TMEM lane quarters), 8 producer, 9.. MMA issue (lane 0 of each; warp 9 also
 // allocates TMEM).  A tcgen05.mma costs its issuing thread tens of cycles, so
 // the phases are spread over kTcMmaWarps issuing warps.
-constexpr int kTcStages = 6;
+constexpr int kTcStages = 6;  // most shared-memory stages (fewer for long filters)
 constexpr int kTcMmaWarps = 4;
 constexpr int kTcPhasesPerWarp = 4 / kTcMmaWarps;
 constexpr int kTcWarps = 9 + kTcMmaWarps;
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < p.n_stages; ++s) {
             mbar_init(&full[s], 1);     // producer lane 0 (+ bytes or cp.async arrivals)
             mbar_init(&empty[s], 128);  // split threads, once they have read the stage
         }
@@ -296,8 +298,8 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
             const TcTile tl = tc_tile(p, blockIdx.x + i * gridDim.x);
             const EnvTcJob &jb = *tl.job;
             for (int kb = 0; kb < n_kb; ++kb, ++g) {
-                const int s = (int)(g % kTcStages);
-                const unsigned use = g / kTcStages;
+                const int s = (int)(g % (unsigned)p.n_stages);
+                const unsigned use = g / (unsigned)p.n_stages;
                 if (use > 0 && !wait(&empty[s], (use - 1) & 1u)) goto done;
                 float *ahi = reinterpret_cast<float *>(stages + (size_t)s * kTcStageBytes);
                 const int u0 = kb * kTcKB;
@@ -342,9 +344,9 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
         unsigned g = 0;
         for (unsigned i = 0; i < n_tiles; ++i) {
             for (int kb = 0; kb < n_kb; ++kb, ++g) {
-                const int s = (int)(g % kTcStages);
+                const int s = (int)(g % (unsigned)p.n_stages);
                 const int t = (int)(g & 1u);
-                if (!wait(&full[s], (g / kTcStages) & 1u)) goto done;
+                if (!wait(&full[s], (g / (unsigned)p.n_stages) & 1u)) goto done;
                 // the MMAs of k-block g - 2 have finished reading A stage t
                 if (g >= 2 && !wait(&a_empty[t], ((g >> 1) - 1) & 1u)) goto done;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
