@@ -211,6 +211,7 @@ constexpr int kTcStageBytes = kTcBufBytes;  // |y| of one k-block, FP32
 constexpr uint32_t kTcAccCols = 4 * kTcNq;  // one accumulator (4 phases)
 constexpr uint32_t kTcACol0 = 2 * kTcAccCols;  // first TMEM column of the A stages
 constexpr uint32_t kTcACols = 2 * kTcKB;    // one A stage: hi then lo
+constexpr int kTcAStages = (512 - (int)kTcACol0) / (int)kTcACols;  // A stages in TMEM
 
 __device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
                                           uint32_t idesc, uint32_t accumulate) {
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
     envelope_tc_kernel(const __grid_constant__ EnvTcParams p) {
     extern __shared__ __align__(128) unsigned char env_smem[];
     __shared__ uint64_t full[kTcStages], empty[kTcStages];
-    __shared__ uint64_t a_full[2], a_empty[2], acc_full[2], acc_empty[2];
+    __shared__ uint64_t a_full[kTcAStages], a_empty[kTcAStages], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -266,7 +267,7 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
             mbar_init(&full[s], 1);     // producer lane 0 (+ bytes or cp.async arrivals)
             mbar_init(&empty[s], 128);  // split threads, once they have read the stage
         }
-        for (int a = 0; a < 2; ++a) {
+        for (int a = 0; a < kTcAStages; ++a) {
             mbar_init(&a_full[a], 128);          // split threads, after their TMEM stores
             mbar_init(&a_empty[a], kTcMmaWarps); // MMA commits of the k-block that read it
         }
@@ -345,10 +346,11 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
         for (unsigned i = 0; i < n_tiles; ++i) {
             for (int kb = 0; kb < n_kb; ++kb, ++g) {
                 const int s = (int)(g % (unsigned)p.n_stages);
-                const int t = (int)(g & 1u);
+                const int t = (int)(g % (unsigned)kTcAStages);
+                const unsigned use = g / (unsigned)kTcAStages;
                 if (!wait(&full[s], (g / (unsigned)p.n_stages) & 1u)) goto done;
-                // the MMAs of k-block g - 2 have finished reading A stage t
-                if (g >= 2 && !wait(&a_empty[t], ((g >> 1) - 1) & 1u)) goto done;
+                // the MMAs of the k-block kTcAStages back have finished reading A stage t
+                if (use > 0 && !wait(&a_empty[t], (use - 1) & 1u)) goto done;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const float *ay = reinterpret_cast<const float *>(stages + (size_t)s * kTcStageBytes);
                 const uint32_t acol = kTcACol0 + (uint32_t)t * kTcACols;
@@ -391,8 +393,8 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t dacc = tmem + (uint32_t)a * kTcAccCols;
             for (int kb = 0; kb < n_kb; ++kb, ++g) {
-                const int t = (int)(g & 1u);
-                if (!wait(&a_full[t], (g >> 1) & 1u)) goto done;
+                const int t = (int)(g % (unsigned)kTcAStages);
+                if (!wait(&a_full[t], (g / (unsigned)kTcAStages) & 1u)) goto done;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 if (lane == 0) {
                     const int u0 = kb * kTcKB;
