@@ -46,6 +46,18 @@ UNIT = "direction·samples/s"
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2032.0
 
+
+def measured_peaks() -> dict:
+    """MEASURED_PEAKS.json next to this file (copy bandwidth and bf16 GEMM rate
+    measured on this machine type), else the stated fallback figures."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "source": "measured (MEASURED_PEAKS.json)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "source": "fallback"}
+
 WORKLOADS = {
     "hemi_3d_n5": dict(
         scene=lambda: scenes.hemi_3d(seed=2), order=5, mode="linear",
@@ -428,6 +440,10 @@ def run_ours(args, wl, scene) -> None:
     achieved = ops["beam_total"] * px / (beam_ms * 1e-3) / 1e12
     # the whole per-pixel path (beamform + envelope, L taps), as one roofline
     path_ops = ops["beam_total"] + info.env_taps
+    peaks = measured_peaks()
+    roots_ms = float(np.mean(stage[:, 0]))
+    roots_bytes = N * T * 4 + N * info.row * 4 * (2 if linear else 1)
+    roots_gbs = roots_bytes / (roots_ms * 1e-3) / 1e9
     path_achieved = path_ops * px / ((beam_ms + env_ms) * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -453,7 +469,13 @@ def run_ours(args, wl, scene) -> None:
                      "traffic": beam_traffic(args.workload),
                      "algorithmic_bytes": px * 4 + N * T * 4 * (2 if linear else 1),
                      "path": {"stages": "beamform + envelope", "ops_per_pixel": path_ops,
-                              "achieved": path_achieved, "frac": path_achieved / peak}},
+                              "achieved": path_achieved, "frac": path_achieved / peak},
+                     # K1 alone: the roots kernel reads the frame and writes the root
+                     # rows (twice with interpolation): an HBM-bound pass
+                     "roots": None if mf is not None else {
+                         "bound": "hbm", "unit": "GB/s", "bytes": roots_bytes,
+                         "achieved": roots_gbs, "peak": peaks["hbm_gbs"],
+                         "frac": roots_gbs / peaks["hbm_gbs"], "peak_source": peaks["source"]}},
         "e2e": {"value": px * world * e2e_steps / e2e_total, "unit": UNIT,
                 "h2d_bytes_per_step": N * T * 4, "d2h_bytes_per_step": M * T * 4},
         "gpu_launches": (4 if mf is not None else 3) * args.steps,

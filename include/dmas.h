@@ -127,6 +127,7 @@ typedef struct {
     int window;                /* staged samples per microphone per time tile */
     int mic_chunk;             /* microphones staged per pass */
     int time_tile;             /* output samples per CTA */
+    int row;                   /* samples per root-channel row (zero pads included) */
     size_t workspace_bytes;    /* device scratch a beamform call uses */
     size_t table_bytes;        /* device bytes of the resident delay tables */
 } dmas_plan_info;

@@ -67,7 +67,8 @@ class PlanDesc(ctypes.Structure):
 class PlanInfo(ctypes.Structure):
     _fields_ = [(name, ctypes.c_int) for name in (
         "n_mics", "n_dirs", "n_samples", "order", "delay_mode", "flags", "chan_prec",
-        "ng_prec", "env_taps", "n_groups", "group_size", "window", "mic_chunk", "time_tile")] + [
+        "ng_prec", "env_taps", "n_groups", "group_size", "window", "mic_chunk", "time_tile",
+        "row")] + [
         ("workspace_bytes", ctypes.c_size_t), ("table_bytes", ctypes.c_size_t)]
 
 
@@ -162,6 +163,7 @@ class Info:
     window: int
     mic_chunk: int
     time_tile: int
+    row: int
     workspace_bytes: int
     table_bytes: int
 

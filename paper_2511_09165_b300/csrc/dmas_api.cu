@@ -1209,6 +1209,7 @@ dmas_status dmas_plan_get_info(const dmas_plan *p, dmas_plan_info *info) {
     info->window = hp.window;
     info->mic_chunk = hp.mic_chunk;
     info->time_tile = hp.tile;
+    info->row = hp.row;
     info->workspace_bytes = dmas_plan_workspace_bytes(p);
     info->table_bytes = p->table_bytes;
     return DMAS_OK;
