@@ -157,20 +157,25 @@ def test_microphone_chunks_and_wide_delays():
         assert_parity(g, r)
 
 
-def test_several_staging_passes():
+@pytest.mark.parametrize("mode", ["round", "linear"])
+def test_several_staging_passes(mode):
     """Directions spread over the whole field in one group force a wide window,
-    so fewer microphones fit per staging pass than the array has."""
+    so fewer microphones fit per staging pass than the array has; 301
+    microphones leave a last pass whose count is not a multiple of 4."""
     rng = np.random.default_rng(9)
-    N, T, M, fs = 300, 600, 16, 1000.0
+    N, T, M, fs = 301, 600, 16, 1000.0
     frame = rng.standard_normal((N, T)).astype(np.float32)
     tau = rng.integers(-60, 61, size=(M, N)) / fs
-    plan = dm.Plan(delays_s=tau, n_samples=T, fs=fs, order=3, env_cutoff_hz=100.0,
-                   env_taps=15)
+    if mode == "linear":
+        tau = tau + rng.uniform(0.0, 1.0, size=(M, N)) / fs
+    dmode, omode = {"round": (dm.ROUND, oracle.ROUND), "linear": (dm.LINEAR, oracle.LINEAR)}[mode]
+    plan = dm.Plan(delays_s=tau, n_samples=T, fs=fs, order=3, delay_mode=dmode,
+                   env_cutoff_hz=100.0, env_taps=15)
     info = plan.info()
     plan.close()
-    assert info.mic_chunk < N
-    g = _explicit(frame, tau, fs, 3, env_cutoff_hz=100.0, env_taps=15)
-    r = oracle.dmas(frame.astype(np.float64), tau, fs, 3, oracle.ROUND, use_cf=True,
+    assert info.mic_chunk < N and N % info.mic_chunk != 0
+    g = _explicit(frame, tau, fs, 3, dmode, env_cutoff_hz=100.0, env_taps=15)
+    r = oracle.dmas(frame.astype(np.float64), tau, fs, 3, omode, use_cf=True,
                     taps=oracle.fir_taps(fs, 100.0, 15))
     assert_parity(g, r)
 
