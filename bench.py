@@ -114,9 +114,9 @@ WORKLOADS = {
 # DRAM bytes (read + write) of one beamform launch on the default workload, from
 # one ncu capture (profiles/beamform_x2_hemi3d_n5.md), valid while the kernel
 # source is the one that was measured.
-TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "kernel_src_sha256_16": "c33a5c247faa41f6",
-                  # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (MB, 2 decimals)
-                  "bytes": 5_880_000 + 75_210_000}
+TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "kernel_src_sha256_16": "c8808104e97912af",
+                  # ncu dram__bytes_read.sum + dram__bytes_write.sum (bytes)
+                  "bytes": 5_880_576 + 75_538_944}
 
 
 def beam_traffic(workload: str):
