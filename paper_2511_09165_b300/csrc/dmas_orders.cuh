@@ -29,9 +29,9 @@
 // For NMAX = 5 that is 13 running sums and 5 staged roots per sample, against
 // 2 + 4 + 5 + 6 + 6 sums and 5 gathers over 5 separate passes.  Nearest-sample
 // delays take a 128-sample tile (two pairs per lane), interpolated ones a
-// 64-sample tile (one pair: their sums are split in two, U[t] with weight
-// 1 - f and V[t] with weight f over the same staged sample, the interpolated
-// sum being U[t] + V[t + 1], so each staged sample's powers are formed once).
+// 64-sample tile (one pair: their sums are split in two, S[t] plain and V[t]
+// with weight f over the same staged sample, the interpolated sum being
+// S[t] - V[t] + V[t + 1], so each staged sample's powers are formed once).
 //
 // Waits on the stage barriers are bounded as in the single-order kernels.
 #pragma once
@@ -168,35 +168,35 @@ __device__ __forceinline__ void accumulate_orders(f32x2_t (&a)[OrdersLayout<NMAX
     }
 }
 
-// Interpolated delays: every power of the sample goes (1 - f)-weighted into U
-// and f-weighted into V.
+// Interpolated delays: every power of the sample goes plain into S and
+// f-weighted into V (the (1 - f)-weighted sum is S - V; only the weight {f, f}
+// is held per microphone).
 template <int NMAX>
-__device__ __forceinline__ void accumulate_orders_split(f32x2_t (&u)[OrdersLayout<NMAX>::kNum],
-                                                        f32x2_t (&v)[OrdersLayout<NMAX>::kNum],
-                                                        const f32x2_t (&s)[NMAX], f32x2_t w0,
-                                                        f32x2_t w1) {
+__device__ __forceinline__ void accumulate_orders_sv(f32x2_t (&sa)[OrdersLayout<NMAX>::kNum],
+                                                     f32x2_t (&v)[OrdersLayout<NMAX>::kNum],
+                                                     const f32x2_t (&s)[NMAX], f32x2_t wf) {
     const f32x2_t x = s[0];
     const f32x2_t xx = f2_mul(x, x);
-    u[0] = f2_fma(w0, x, u[0]);
-    v[0] = f2_fma(w1, x, v[0]);
-    u[1] = f2_fma(w0, xx, u[1]);
-    v[1] = f2_fma(w1, xx, v[1]);
+    sa[0] = f2_add(sa[0], x);
+    v[0] = f2_fma(wf, x, v[0]);
+    sa[1] = f2_add(sa[1], xx);
+    v[1] = f2_fma(wf, xx, v[1]);
     if constexpr (NMAX >= 2) {
         const f32x2_t ax = x & kAbsMask2;
-        u[2] = f2_fma(w0, ax, u[2]);
-        v[2] = f2_fma(w1, ax, v[2]);
+        sa[2] = f2_add(sa[2], ax);
+        v[2] = f2_fma(wf, ax, v[2]);
     }
 #pragma unroll
     for (int q = 2; q <= NMAX; ++q) {
         const int b = OrdersLayout<NMAX>::base(q);
         f32x2_t pw = s[q - 1];
-        u[b] = f2_fma(w0, pw, u[b]);
-        v[b] = f2_fma(w1, pw, v[b]);
+        sa[b] = f2_add(sa[b], pw);
+        v[b] = f2_fma(wf, pw, v[b]);
 #pragma unroll
         for (int j = 2; j < q; ++j) {
             pw = f2_mul(pw, s[q - 1]);
-            u[b + j - 1] = f2_fma(w0, pw, u[b + j - 1]);
-            v[b + j - 1] = f2_fma(w1, pw, v[b + j - 1]);
+            sa[b + j - 1] = f2_add(sa[b + j - 1], pw);
+            v[b + j - 1] = f2_fma(wf, pw, v[b + j - 1]);
         }
     }
 }
@@ -357,13 +357,14 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int il = 0; il < nc; ++il) {
             const float *r = win + il * MB + s_rel[il * 8 + warp] + lane;
             if constexpr (LINEAR) {
-                const ulonglong2 w =
-                    reinterpret_cast<const ulonglong2 *>(s_w4)[il * 8 + warp];  // {1-f,1-f},{f,f}
+                // {f, f}: the upper half of the entry {1-f, 1-f, f, f}
+                const f32x2_t wf =
+                    reinterpret_cast<const f32x2_t *>(s_w4)[(il * 8 + warp) * 2 + 1];
                 f32x2_t st[NP], s[NMAX];
 #pragma unroll
                 for (int q = 0; q < NP; ++q) st[q] = f2_pack(r[q * WS], r[q * WS + 32]);
                 expand_roots<NMAX>(st, s);
-                accumulate_orders_split<NMAX>(acc[0], vac, s, w.x, w.y);
+                accumulate_orders_sv<NMAX>(acc[0], vac, s, wf);
             } else {
 #pragma unroll
                 for (int k = 0; k < kPairs; ++k) {
@@ -406,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int dir = p.gdir[(size_t)g * 8 + warp];
     if (dir < 0) return;
     if constexpr (LINEAR) {
-        // sum[t] = U[t] + V[t + 1]: for lane l's t0 + l that is lane l + 1's
+        // sum[t] = S[t] - V[t] + V[t + 1]: V[t + 1] for lane l's t0 + l is lane l + 1's
         // first half (lane 31: lane 0's second half); for t0 + 32 + l, lane
         // l + 1's second half (lane 31: the sample past the tile, summed over
         // the lanes' microphones).
@@ -415,12 +416,13 @@ __global__ void __launch_bounds__(kThreads, 2)
             float ve = s_vext[q * 32];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) ve += __shfl_xor_sync(0xffffffffu, ve, o);
-            float ulo, uhi, vlo, vhi;
-            f2_unpack(acc[0][q], ulo, uhi);
+            float slo, shi, vlo, vhi;
+            f2_unpack(acc[0][q], slo, shi);
             f2_unpack(vac[q], vlo, vhi);
             const float nlo = __shfl_sync(0xffffffffu, vlo, (lane + 1) & 31);
             const float nhi = __shfl_sync(0xffffffffu, vhi, (lane + 1) & 31);
-            acc[0][q] = f2_pack(ulo + (lane < 31 ? nlo : nhi), uhi + (lane < 31 ? nhi : ve));
+            acc[0][q] = f2_pack((slo - vlo) + (lane < 31 ? nlo : nhi),
+                                (shi - vhi) + (lane < 31 ? nhi : ve));
         }
     }
 #pragma unroll
