@@ -114,9 +114,9 @@ WORKLOADS = {
 # DRAM bytes (read + write) of one beamform launch on the default workload, from
 # one ncu capture (profiles/beamform_x2_hemi3d_n5.md), valid while the kernel
 # source is the one that was measured.
-TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "kernel_src_sha256_16": "c8808104e97912af",
+TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "kernel_src_sha256_16": "2a480b81d3311756",
                   # ncu dram__bytes_read.sum + dram__bytes_write.sum (bytes)
-                  "bytes": 5_880_576 + 75_538_944}
+                  "bytes": 5_926_656 + 75_227_904}
 
 
 def beam_traffic(workload: str):
