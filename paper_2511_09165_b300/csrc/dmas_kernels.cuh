@@ -976,7 +976,9 @@ __device__ __forceinline__ void beamform_x2_run(const Src &src) {
         const unsigned char *buf = smem + 128 + (size_t)bf * stage_bytes;
         const float *w = reinterpret_cast<const float *>(buf);
         const int *s_rel = reinterpret_cast<const int *>(buf + stage_window_bytes(p));
-#pragma unroll 2
+        // unrolled by 4 (measured on B300, 2048 x 16384 frame: unroll 2 480 us,
+        // 4 455 us, 8 472 us)
+#pragma unroll 4
         for (int il = 0; il < nc; ++il) {
             const float *r = w + il * WS + s_rel[il * 8 + warp] + lane;
 #pragma unroll
