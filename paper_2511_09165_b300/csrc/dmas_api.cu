@@ -88,7 +88,8 @@ using namespace dmas;
 // dmas_beamform_host pipelines a large frame (at least 2^22 pixels) in time
 // chunks, one per 2^21 pixels, 4 to 16: each chunk's image columns download
 // while the next chunk computes (measured on the 2048 x 16384 frame: 2.67 ms
-// in 4 chunks, 2.56 in 8, 2.53 in 16, against 2.35 ms for the download alone).
+// in 4 chunks, 2.56 in 8, 2.52 in 16, 2.55 in 32, against 2.35 ms for the
+// download alone).
 constexpr int kHostChunksMin = 4, kHostChunksMax = 16;
 
 struct dmas_plan {
