@@ -248,6 +248,22 @@ def _explicit(frame, tau, fs, order, mode=dm.ROUND, **kw):
     return {"img": img.cpu().numpy(), "y": y.cpu().numpy(), "cf": cf.cpu().numpy()}
 
 
+@pytest.mark.parametrize("frac", [1e-4, 0.5, 0.9999])
+@pytest.mark.parametrize("order", [3, 5])
+def test_interpolation_weights_near_the_ends(frac, order):
+    """Interpolated delays whose fractions all sit near 0, at 1/2 or near 1: the
+    kernel forms the (1 - f)-weighted sums as plain minus f-weighted ones, which
+    near f = 1 is a difference of nearly equal sums."""
+    rng = np.random.default_rng(int(frac * 1e4) + order)
+    N, T, M, fs = 32, 1500, 24, 1000.0
+    frame = rng.standard_normal((N, T)).astype(np.float32)
+    tau = (rng.integers(-20, 21, size=(M, N)) + frac) / fs
+    g = _explicit(frame, tau, fs, order, dm.LINEAR, env_cutoff_hz=100.0, env_taps=15)
+    r = oracle.dmas(frame.astype(np.float64), tau, fs, order, oracle.LINEAR, use_cf=True,
+                    taps=oracle.fir_taps(fs, 100.0, 15))
+    assert_parity(g, r)
+
+
 @pytest.mark.parametrize("T", [1, 2, 37, 255, 256, 257])
 def test_short_frames(T):
     rng = np.random.default_rng(T)
