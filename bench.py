@@ -114,9 +114,9 @@ WORKLOADS = {
 # DRAM bytes (read + write) of one beamform launch on the default workload, from
 # one ncu capture (profiles/beamform_x2_hemi3d_n5.md), valid while the kernel
 # source is the one that was measured.
-TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "kernel_src_sha256_16": "ba4a54a117d7925e",
+TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "kernel_src_sha256_16": "dbe3b86f2c72cf5f",
                   # ncu dram__bytes_read.sum + dram__bytes_write.sum (bytes)
-                  "bytes": 5_880_064 + 74_960_128}
+                  "bytes": 5_880_576 + 74_890_240}
 
 
 def beam_traffic(workload: str):

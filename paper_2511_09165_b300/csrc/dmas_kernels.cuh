@@ -844,7 +844,9 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
 //
 // Src supplies the items: total(), entry(u) (batch entry of item u), par(e)
 // (its parameters) and first(e) (its first item).
-constexpr int kPersistItems = 8;  // work items per CTA of the persistent kernel
+// work items per CTA of the persistent kernel (measured on B300, 2048 x 16384
+// nearest-sample frame: 2 items 440 us, 4 443 us, 8 447-456 us, 16 468 us)
+constexpr int kPersistItems = 2;
 
 struct OneFrame {
     const BeamParams &p;
