@@ -111,22 +111,34 @@ WORKLOADS = {
 }
 
 
-# DRAM bytes (read + write) of one beamform launch on the default workload, from
-# one ncu capture (profiles/beamform_x2_hemi3d_n5.md), valid while the kernel
-# source is the one that was measured.
-TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "kernel_src_sha256_16": "dbe3b86f2c72cf5f",
+# DRAM bytes (read + write) of one beamform launch on the default workload,
+# from one ncu capture of that kernel (the profile summary of the
+# interpolated-delay pair kernel on the hemisphere frame), valid only while
+# the kernel source is the one that was measured; otherwise the line's
+# "traffic" is null and "traffic_note" says why.
+TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "ng": "f32", "kernel_src_sha256_16": "dbe3b86f2c72cf5f",
                   # ncu dram__bytes_read.sum + dram__bytes_write.sum (bytes)
                   "bytes": 5_880_576 + 74_890_240}
 
 
-def beam_traffic(workload: str):
+def beam_traffic(workload: str, ng: str = "cf32"):
     import hashlib
     src = os.path.join(ROOT, "paper_2511_09165_b300", "csrc", "dmas_kernels.cuh")
     with open(src, "rb") as f:
         sha = hashlib.sha256(f.read()).hexdigest()[:16]
-    if workload == TRAFFIC_RECORD["workload"] and sha == TRAFFIC_RECORD["kernel_src_sha256_16"]:
-        return TRAFFIC_RECORD["bytes"]
-    return None
+    if (workload == TRAFFIC_RECORD["workload"] and ng == TRAFFIC_RECORD.get("ng", "cf32")
+            and sha == TRAFFIC_RECORD["kernel_src_sha256_16"]):
+        return TRAFFIC_RECORD["bytes"], "one ncu capture of this kernel on this workload"
+    if workload != TRAFFIC_RECORD["workload"] or ng != TRAFFIC_RECORD.get("ng", "cf32"):
+        return None, ("no DRAM capture recorded for this workload; the recorded one is "
+                      f"{TRAFFIC_RECORD['workload']}")
+    return None, "the kernel source changed since its DRAM traffic was captured"
+
+
+NG_PREC = {"cf32": lambda dm: dm.NG_CF32, "f64": lambda dm: dm.NG_F64,
+           "f32": lambda dm: dm.NG_F32}
+NG_TEXT = {"cf32": "compensated FP32 (compensated Horner over Eqs. dmas2_impl..dmas5_impl)",
+           "f64": "FP64", "f32": "plain FP32 (variant)"}
 
 
 def algorithmic_ops_per_pixel(N: int, n: int, linear: bool) -> dict:
@@ -339,9 +351,10 @@ def run_ours(args, wl, scene) -> None:
     order = wl["order"]
     cf = wl.get("cf", True)
     mf = scenes.lfm_chirp(scene.fs).astype(np.float32) if wl.get("mf") else None
-    plan = dm.Plan(mic_xyz=scene.mic_xyz, dir_azel=scene.dir_azel, dir_unit=scene.dir_unit,
+    plan_kw = dict(mic_xyz=scene.mic_xyz, dir_azel=scene.dir_azel, dir_unit=scene.dir_unit,
                    n_samples=scene.n_samples, fs=scene.fs, c=scene.c, order=order,
                    delay_mode=dm.LINEAR if linear else dm.ROUND, cf=cf, mf_signal=mf)
+    plan = dm.Plan(ng_prec=NG_PREC[args.ng](dm), **plan_kw)
     info = plan.info()
     N, M, T = scene.n_mics, scene.n_dirs, scene.n_samples
     px = M * T
@@ -389,6 +402,23 @@ def run_ours(args, wl, scene) -> None:
     plan.set_profiling(False)
     stage = np.array(stage)
 
+    # the other Newton-Girard arithmetics on the same frame: beamform stage
+    # only (named variants, never the line's value)
+    ng_variants = {}
+    for name in NG_PREC:
+        if name == args.ng:
+            continue
+        vp = dm.Plan(ng_prec=NG_PREC[name](dm), **plan_kw)
+        vp.set_profiling(True)
+        vt = []
+        for _ in range(min(args.steps, 20)):
+            flush.zero_()
+            vp(frame, out=image, stream=stream)
+            vt.append(vp.stage_ms()[1])
+        vp.check()
+        vp.close()
+        ng_variants[name] = float(np.mean(vt[1:] if len(vt) > 1 else vt))
+
     # small frames: the same step replayed from a CUDA graph (the path only
     # enqueues kernels, so it captures), which removes the host launch gaps
     graph_ms = None
@@ -430,6 +460,15 @@ def run_ours(args, wl, scene) -> None:
     clocks.stop()
     plan.close()
 
+    # serving: a short leg of Poisson arrivals from the 16-sensor mix (the
+    # metric's latency half), through the continuous-batching server and the
+    # one-frame-per-launch baseline, latency to the device-resident image and
+    # to the image copied to host memory
+    serve = None
+    if args.serve_leg_seconds > 0 and args.workload == "hemi_3d_n5":
+        serve, _ = serving_measure([200.0], args.serve_leg_seconds, rank,
+                                   copy_back_modes=(False, True))
+
     if rank != 0:
         return
     ops = algorithmic_ops_per_pixel(N, order, linear)
@@ -441,6 +480,7 @@ def run_ours(args, wl, scene) -> None:
     # the whole per-pixel path (beamform + envelope, L taps), as one roofline
     path_ops = ops["beam_total"] + info.env_taps
     peaks = measured_peaks()
+    traffic = beam_traffic(args.workload, args.ng)
     roots_ms = float(np.mean(stage[:, 0]))
     roots_bytes = N * T * 4 + N * info.row * 4 * (2 if linear else 1)
     roots_gbs = roots_bytes / (roots_ms * 1e-3) / 1e9
@@ -453,7 +493,8 @@ def run_ours(args, wl, scene) -> None:
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "description": wl["text"],
                    "n_mics": N, "n_dirs": M, "n_samples": T, "order": order,
-                   "delays": wl["mode"], "cf": cf,
+                   "delays": wl["mode"], "cf": cf, "ng": args.ng,
+                   "newton_girard": NG_TEXT[args.ng],
                    "l2": "flushed (256 MB write) before every step",
                    "parallelism": f"replicas x{world}"},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
@@ -466,7 +507,7 @@ def run_ours(args, wl, scene) -> None:
                      "ops_per_pixel": ops, "pixels_per_launch": px,
                      "peak_source": f"{sms} SMs (device properties) x 128 FP32 lanes x "
                                     f"{SM_MAX_MHZ:.0f} MHz (max SM clock)",
-                     "traffic": beam_traffic(args.workload),
+                     "traffic": traffic[0], "traffic_note": traffic[1],
                      "algorithmic_bytes": px * 4 + N * T * 4 * (2 if linear else 1),
                      "path": {"stages": "beamform + envelope", "ops_per_pixel": path_ops,
                               "achieved": path_achieved, "frac": path_achieved / peak},
@@ -484,6 +525,18 @@ def run_ours(args, wl, scene) -> None:
         "plan": {"window": info.window, "mic_chunk": info.mic_chunk,
                  "groups": info.n_groups},
     }
+    line["ng_variants_beamform_ms"] = {
+        name: {"beamform_ms": ms, "frac": ops["beam_total"] * px / (ms * 1e-3) / 1e12 / peak}
+        for name, ms in ng_variants.items()}
+    if serve is not None:
+        at = serve["200_fps"]["server"]
+        line["serving_200fps"] = {
+            "p50_ms": at.get("p50_ms"), "p99_ms": at.get("p99_ms"),
+            "baseline_p50_ms": serve["200_fps"]["one_frame_per_launch"].get("p50_ms"),
+            "baseline_p99_ms": serve["200_fps"]["one_frame_per_launch"].get("p99_ms"),
+            "to_host_p50_ms": serve["200_fps_to_host"]["server"].get("p50_ms"),
+            "to_host_p99_ms": serve["200_fps_to_host"]["server"].get("p99_ms"),
+            "seconds": args.serve_leg_seconds, "detail": serve}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, order, linear, cf, mf is not None)
     print(json.dumps(line), flush=True)
@@ -492,13 +545,17 @@ def run_ours(args, wl, scene) -> None:
 # ---------------------------------------------------------------------------
 # serving: Poisson arrivals from 16 mixed sensors
 # ---------------------------------------------------------------------------
-def run_serving(args) -> None:
+def serving_measure(rates, seconds, rank=0, budget_gb=48, bulk_streams=3,
+                    copy_back_modes=(False,)):
+    """Poisson arrivals from the 16-sensor mix at each rate, through the
+    continuous-batching server and through the one-frame-per-launch baseline,
+    for each copy-back mode (False: latency to the image resident on the
+    device; True: to the image copied to pinned host memory).  Returns
+    (results, mix)."""
     import torch
     import paper_2511_09165_b300 as dm
     from paper_2511_09165_b300 import serving
 
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
     mix = scenes.serving_mix(seed=5 + rank)
     sensors = [serving.Sensor(dm.Plan(mic_xyz=s.mic_xyz, dir_azel=s.dir_azel,
                                       dir_unit=s.dir_unit, n_samples=s.n_samples, fs=s.fs,
@@ -510,16 +567,16 @@ def run_serving(args) -> None:
     torch.cuda.synchronize()
 
     def schedule(rate, seed):
-        offs, which = serving.poisson_arrivals(rate, args.serve_seconds, len(mix), seed)
+        offs, which = serving.poisson_arrivals(rate, seconds, len(mix), seed)
         rng = np.random.default_rng(seed + 1)
         frames = [int(rng.integers(len(host[w]))) for w in which]
         return offs, which, frames
 
-    def run_server(rate, seed):
+    def run_server(rate, seed, copy_back):
         offs, which, fidx = schedule(rate, seed)
         reqs = []
-        with serving.Server(sensors, budget_bytes=args.serve_budget_gb << 30, streams=2,
-                            bulk_streams=args.serve_bulk_streams) as srv:
+        with serving.Server(sensors, budget_bytes=budget_gb << 30, streams=2,
+                            bulk_streams=bulk_streams, copy_back=copy_back) as srv:
             t0 = time.perf_counter() + 0.05
             for o, w, f in zip(offs, which, fidx):
                 while time.perf_counter() < t0 + o:
@@ -529,12 +586,12 @@ def run_serving(args) -> None:
             nb = srv.batches
         return reqs, t0, nb
 
-    def run_baseline(rate, seed):
+    def run_baseline(rate, seed, copy_back):
         offs, which, fidx = schedule(rate, seed)
         t0 = time.perf_counter() + 0.05
         reqs = [serving.Request(int(w), host[w][f], t0 + o)
                 for o, w, f in zip(offs, which, fidx)]
-        serving.one_frame_per_launch(sensors, reqs)
+        serving.one_frame_per_launch(sensors, reqs, copy_back=copy_back)
         return reqs, t0
 
     fast = [sn.cost <= serving.FAST_COST for sn in sensors]
@@ -553,20 +610,33 @@ def run_serving(args) -> None:
             d["mean_batch"] = len(done) / max(batches, 1)
         return d
 
+    results = {}
+    for k, rate in enumerate(rates):
+        for cb in copy_back_modes:
+            reqs, t0, nb = run_server(rate, 100 + k, cb)
+            sv = summary(reqs, t0, nb)
+            reqs, t0 = run_baseline(rate, 100 + k, cb)
+            bl = summary(reqs, t0)
+            key = f"{rate:g}_fps" + ("_to_host" if cb else "")
+            results[key] = {"server": sv, "one_frame_per_launch": bl}
+    for sn in sensors:
+        sn.plan.close()
+    return results, mix
+
+
+def run_serving(args) -> None:
+    import torch
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
     clocks = ClockSampler(local)
     clocks.start()
     wall0 = time.time()
-    results = {}
-    for k, rate in enumerate(args.serve_rates):
-        reqs, t0, nb = run_server(rate, 100 + k)
-        sv = summary(reqs, t0, nb)
-        reqs, t0 = run_baseline(rate, 100 + k)
-        bl = summary(reqs, t0)
-        results[f"{rate:g}_fps"] = {"server": sv, "one_frame_per_launch": bl}
+    results, mix = serving_measure(args.serve_rates, args.serve_seconds, rank,
+                                   args.serve_budget_gb, args.serve_bulk_streams,
+                                   copy_back_modes=(False, True))
     wall1 = time.time()
     clocks.stop()
-    for sn in sensors:
-        sn.plan.close()
     if rank != 0:
         return
     top = results[f"{args.serve_rates[-1]:g}_fps"]["server"]
@@ -578,11 +648,13 @@ def run_serving(args) -> None:
         "data": "synthetic",
         "config": {"workload": "serving", "description":
                    "16 sensors (N in {32,64,128}, M in {91,2048,8192}, T in "
-                   "{4096,16384,32768}, n in {3,5}, nearest-sample delays, CF, envelope), "
-                   "small_2d-style echo frames, Poisson arrivals at " +
+                   "{4096,16384,32768}, n in {3,5}, nearest-sample delays, CF, envelope, "
+                   "compensated-FP32 Newton-Girard), small_2d-style echo frames, Poisson "
+                   "arrivals at " +
                    ", ".join(f"{r:g}" for r in args.serve_rates) + " frames/s for "
                    f"{args.serve_seconds:g} s each; latency = arrival to image resident "
-                   "on the device; value = delivered direction*samples/s at the highest rate",
+                   "on the device (keys *_to_host: to the image copied to pinned host "
+                   "memory); value = delivered direction*samples/s at the highest rate",
                    "budget_gb": args.serve_budget_gb, "streams": 2,
                    "bulk_streams": args.serve_bulk_streams,
                    "sensors": [f"N{s.n_mics} M{s.n_dirs} T{s.n_samples} n{s.order}"
@@ -858,6 +930,10 @@ def main() -> None:
     ap.add_argument("--serve-budget-gb", type=int, default=48)
     ap.add_argument("--serve-bulk-streams", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ng", choices=sorted(NG_PREC), default="cf32",
+                    help="Newton-Girard arithmetic: compensated FP32 (default), FP64, plain FP32")
+    ap.add_argument("--serve-leg-seconds", type=float, default=2.0,
+                    help="seconds of 200 frames/s serving in the default run (0: none)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

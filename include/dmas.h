@@ -64,11 +64,16 @@ typedef enum {
     DMAS_CH_BF16 = 2   /* roots stored as BF16 */
 } dmas_chan_prec;
 
-/* Arithmetic of the Newton-Girard step (power sums -> E_n). */
+/* Arithmetic of the Newton-Girard step (power sums -> E_n), the one step of
+ * the path whose alternating-sign cancellation needs more than FP32
+ * (Sec. II-C).  The default (zero) is compensated FP32. */
 typedef enum {
-    DMAS_NG_F32 = 0,   /* plain FP32 */
-    DMAS_NG_F64 = 1,   /* FP64 */
-    DMAS_NG_CF32 = 2   /* compensated FP32 (double-float: error-free sums and products) */
+    DMAS_NG_CF32 = 0,  /* compensated FP32: orders <= 5 by the compensated Horner
+                          scheme over Eqs. dmas2_impl..dmas5_impl, higher orders by
+                          the recurrence in double-float; as accurate as the same
+                          evaluation in twice FP32's precision, then rounded */
+    DMAS_NG_F64 = 1,   /* FP64 (B300's FP64 rate is a small fraction of FP32's) */
+    DMAS_NG_F32 = 2    /* plain FP32: a faster variant, not the default */
 } dmas_ng_prec;
 
 /* dmas_plan_desc.flags */
@@ -290,26 +295,31 @@ dmas_status dmas_selftest_wait_timeout(double limit_ms, void *stream);
 
 /*
  * Beamform one frame without allocating anything.  This entry point has no
- * counterpart in the paper; it exists for callers that must not allocate
- * device memory while they process frames: a real-time sonar loop where a
- * cudaMalloc (which can synchronise the whole device) would blow the frame
- * deadline, or a process whose GPU memory is already reserved by another
- * allocator so that a new cudaMalloc would fail.
+ * counterpart in the paper.  It is for callers that may allocate at set-up
+ * but must not allocate while they process frames: a real-time sonar loop
+ * with a fixed frame deadline, where a cudaMalloc (which can synchronise the
+ * whole device and take an unbounded time) would make it miss frames, or a
+ * host whose memory accounting forbids device allocations after start-up.
  *
  * It runs the same kernels as dmas_beamform with the same results, but its
- * scratch (the root channels, with DMAS_F_ENVELOPE the pre-envelope image,
- * and the beamform kernel's work counter) lives in one static device array of
- * DMAS_NOALLOC_SCRATCH_BYTES that
- * the library holds on every GPU it is loaded on until the process exits.
- * The plan itself is created beforehand with dmas_plan_create, which does
- * allocate (once, at set-up).
+ * per-call scratch (the root channels, with DMAS_F_ENVELOPE the pre-envelope
+ * image, and the beamform kernel's work counter) lives in one static device
+ * array of DMAS_NOALLOC_SCRATCH_BYTES that the library holds on every GPU it
+ * is loaded on until the process exits.  The plan itself is created
+ * beforehand with dmas_plan_create, which does allocate, once, at set-up: its
+ * tables and its own scratch for dmas_beamform (dmas_plan_workspace_bytes),
+ * so a plan used only through this call still holds that scratch, and the
+ * static array adds its 16 MiB on each device.
  *   d_frame : device [N][T] float32;  d_image : device [M][T] float32.
  * The plan's device must be the current device.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture.  Every call shares the one array: calls that
- * overlap on the GPU (other streams, other threads) race and corrupt each
- * other's results, so serialise them.  Nothing from an earlier call leaks into
- * a later one: each call rewrites every byte of scratch it reads.
+ * looks up the array's device address (cudaGetSymbolAddress) and keeps it for
+ * the life of the process: make that first call before any stream capture,
+ * and do not call cudaDeviceReset on that device afterwards (the kept address
+ * would then be stale).  Every call shares the one array: calls that overlap
+ * on the GPU (other streams, other threads) race and corrupt each other's
+ * results, so serialise them.  Nothing from an earlier call leaks into a
+ * later one: each call rewrites every byte of scratch it reads, the work
+ * counter included.
  * Errors: DMAS_EINVAL (NULL argument, plan on another device, or a plan whose
  * dmas_plan_workspace_bytes exceeds DMAS_NOALLOC_SCRATCH_BYTES; the reason is
  * in dmas_plan_last_error), DMAS_ECUDA.

@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_PKG, "_lib", "libdmas.so")
 
 ROUND, LINEAR = 0, 1
 CH_F32, CH_F16, CH_BF16 = 0, 1, 2
-NG_F32, NG_F64, NG_CF32 = 0, 1, 2
+NG_CF32, NG_F64, NG_F32 = 0, 1, 2  # compensated FP32 is the default
 F_CF, F_ENVELOPE = 1, 2
 V_PLAIN, V_CF = 1, 2  # dmas_beamform_orders: images without / with the coherence factor
 
@@ -177,7 +177,7 @@ class Plan:
                  c: float = 343.0, delay_mode: int = ROUND, cf: bool = True,
                  envelope: bool = True, cf_eps: float = 1e-30,
                  env_cutoff_hz: float = 5000.0, env_taps: int = 0,
-                 chan_prec: int = CH_F32, ng_prec: int = NG_F32, mf_signal=None):
+                 chan_prec: int = CH_F32, ng_prec: int = NG_CF32, mf_signal=None):
         xyz, azel, unit, dly = _f64(mic_xyz), _f64(dir_azel), _f64(dir_unit), _f64(delays_s)
         if dly is not None:
             M, N = dly.shape

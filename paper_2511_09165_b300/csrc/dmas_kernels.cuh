@@ -238,7 +238,8 @@ __global__ void __launch_bounds__(256) roots_batch_kernel(const __grid_constant_
 // ---------------------------------------------------------------------------
 // Newton-Girard: E_n from power sums P[1..n]
 // ---------------------------------------------------------------------------
-enum { NG_F32 = 0, NG_F64 = 1, NG_CF32 = 2 };
+// (the same numbering as dmas_ng_prec: compensated FP32 is zero, the default)
+enum { NG_CF32 = 0, NG_F64 = 1, NG_F32 = 2 };
 
 // The paper's pre-expanded equations for n <= 5, the recurrence
 // k e_k = sum_{i=1..k} (-1)^(i-1) e_{k-i} P_i above that.
@@ -316,9 +317,8 @@ __device__ __forceinline__ dfloat df_mul_f(dfloat x, float y) {
 // x / k for a small positive integer k, as x times the double-float
 // reciprocal of k (hi = 1/k rounded to float, lo = the rest; exact for powers
 // of two): relative error near 2^-44, in place of two IEEE divisions per
-// step (measured on B300, n = 5 interpolated 2048 x 16384 frame: the
-// compensated form's beamform 1141 us with the divisions and sums started at
-// zero, 946 us as here)
+// step (measured on B300 when this recurrence also served n = 5, interpolated
+// 2048 x 16384 frame: beamform 1141 us with the divisions, 946 us as here)
 template <int K>
 __device__ __forceinline__ dfloat df_div_int(dfloat x) {
     constexpr double r = 1.0 / (double)K;
@@ -327,7 +327,8 @@ __device__ __forceinline__ dfloat df_div_int(dfloat x) {
     return df_mul(x, dfloat{hi, lo});
 }
 
-// e_k = (sum_{i=1..k} (-1)^(i-1) e_{k-i} P_i) / k for k = K..ORDER
+// e_k = (sum_{i=1..k} (-1)^(i-1) e_{k-i} P_i) / k for k = K..ORDER, in
+// double-float (orders above 5)
 template <int K, int ORDER>
 __device__ __forceinline__ void cf32_step(dfloat (&e)[ORDER + 1], const float (&P)[ORDER + 1]) {
     if constexpr (K <= ORDER) {
@@ -342,12 +343,109 @@ __device__ __forceinline__ void cf32_step(dfloat (&e)[ORDER + 1], const float (&
     }
 }
 
+// ---- compensated Horner form of Eqs. dmas2_impl..dmas5_impl ---------------
+// Each pre-expanded equation is a polynomial in P_1 whose coefficients are
+// products of the other power sums:
+//   2 E_2   = P1^2 - P2
+//   6 E_3   = (P1^2 - 3 P2) P1 + 2 P3
+//   24 E_4  = ((P1^2 - 6 P2) P1 + 8 P3) P1 + 3 (P2^2 - 2 P4)
+//   120 E_5 = (((P1^2 - 10 P2) P1 + 20 P3) P1 + 15 (P2^2 - 2 P4)) P1
+//             + 4 (6 P5 - 5 P2 P3)
+// The coefficients are formed exactly as double-floats (error-free products
+// and sums), and the polynomial is evaluated by the compensated Horner scheme
+// (Graillat, Langlois and Louvet, 2005): every step's product and sum errors,
+// captured by TwoProduct and TwoSum, are summed into a correction polynomial
+// evaluated alongside in plain FP32.  The result is as accurate as Horner in
+// twice the working precision, rounded to FP32 (error ~ u |E_n| + u^2 times
+// the sum of the terms' magnitudes), at about 60 FP32 operations for n = 5
+// where the double-float recurrence above takes about 250.
+//
+// TwoSum with the operands ordered by magnitude (Dekker's FastTwoSum after a
+// compare and two selects): three FP32 additions on the FMA pipe, the compare
+// and selects on the integer/logic pipe, in place of Knuth's six additions.
+__device__ __forceinline__ dfloat two_sum_ordered(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const bool a_big = fabsf(a) >= fabsf(b);
+    const float big = a_big ? a : b, small = a_big ? b : a;
+    return {s, __fsub_rn(small, __fsub_rn(s, big))};
+}
+__device__ __forceinline__ dfloat two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+// k * (hi + lo) for a small integer k: exact product of hi, lo scaled
+__device__ __forceinline__ dfloat df_scale(float k, dfloat x) {
+    const dfloat p = two_prod(k, x.hi);
+    return {p.hi, __fmaf_rn(k, x.lo, p.lo)};
+}
+// One compensated Horner step: s <- s x + c (c = c.hi + c.lo), the rounding
+// errors of the product and the sum, plus c.lo, added into the correction
+// polynomial r <- r x + (errors).
+__device__ __forceinline__ void comp_horner_step(float &s, float &r, float x, dfloat c) {
+    const dfloat p = two_prod(s, x);
+    const dfloat t = two_sum_ordered(p.hi, c.hi);
+    s = t.hi;
+    r = __fmaf_rn(r, x, __fadd_rn(__fadd_rn(p.lo, t.lo), c.lo));
+}
+
+// (s + r) / D for the integer denominator D of the pre-expanded equation: a
+// product with the rounded reciprocal, then one residual correction.
+template <int D>
+__device__ __forceinline__ float comp_finish(float s, float r) {
+    constexpr float inv = (float)(1.0 / (double)D);
+    const float v = __fadd_rn(s, r);
+    const float q = __fmul_rn(v, inv);
+    return __fmaf_rn(__fmaf_rn(-q, (float)D, v), inv, q);
+}
+
 template <int ORDER>
 __device__ __forceinline__ float newton_girard_cf32(const float (&P)[ORDER + 1]) {
-    dfloat e[ORDER + 1];
-    e[0] = {1.0f, 0.0f};
-    cf32_step<1, ORDER>(e, P);
-    return __fadd_rn(e[ORDER].hi, e[ORDER].lo);
+    if constexpr (ORDER == 1) {
+        return P[1];
+    } else if constexpr (ORDER <= 5) {
+        const float x = P[1];
+        // leading step x * x + c_{n-2}
+        const dfloat xx = two_prod(x, x);
+        dfloat c;
+        if constexpr (ORDER == 2) c = {-P[2], 0.0f};
+        else if constexpr (ORDER == 3) c = two_prod(-3.0f, P[2]);
+        else if constexpr (ORDER == 4) c = two_prod(-6.0f, P[2]);
+        else c = two_prod(-10.0f, P[2]);
+        const dfloat t = two_sum_ordered(xx.hi, c.hi);
+        float s = t.hi;
+        float r = __fadd_rn(__fadd_rn(xx.lo, t.lo), c.lo);
+        if constexpr (ORDER == 2) {
+            return comp_finish<2>(s, r);
+        } else if constexpr (ORDER == 3) {
+            comp_horner_step(s, r, x, dfloat{__fmul_rn(2.0f, P[3]), 0.0f});
+            return comp_finish<6>(s, r);
+        } else {
+            // P2^2 - 2 P4 as a double-float
+            const dfloat q = two_prod(P[2], P[2]);
+            const dfloat d0 = two_sum_ordered(q.hi, __fmul_rn(-2.0f, P[4]));
+            const dfloat d = {d0.hi, __fadd_rn(q.lo, d0.lo)};
+            if constexpr (ORDER == 4) {
+                comp_horner_step(s, r, x, two_prod(8.0f, P[3]));
+                comp_horner_step(s, r, x, df_scale(3.0f, d));
+                return comp_finish<24>(s, r);
+            } else {
+                comp_horner_step(s, r, x, two_prod(20.0f, P[3]));
+                comp_horner_step(s, r, x, df_scale(15.0f, d));
+                // 4 (6 P5 - 5 P2 P3): both products exact, their difference by TwoSum
+                const dfloat g6 = two_prod(6.0f, P[5]);
+                const dfloat m5 = df_scale(5.0f, two_prod(P[2], P[3]));
+                const dfloat g = two_sum_ordered(g6.hi, -m5.hi);
+                const float glo = __fadd_rn(__fsub_rn(g6.lo, m5.lo), g.lo);
+                comp_horner_step(s, r, x, dfloat{__fmul_rn(4.0f, g.hi), __fmul_rn(4.0f, glo)});
+                return comp_finish<120>(s, r);
+            }
+        }
+    } else {
+        dfloat e[ORDER + 1];
+        e[0] = {1.0f, 0.0f};
+        cf32_step<1, ORDER>(e, P);
+        return __fadd_rn(e[ORDER].hi, e[ORDER].lo);
+    }
 }
 
 template <int ORDER, int NGP>

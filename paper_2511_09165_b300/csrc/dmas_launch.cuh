@@ -99,8 +99,8 @@ cudaError_t launch_beam_ng(const BeamParams &p, int ngp, unsigned grid, size_t s
                            cudaStream_t s) {
     switch (ngp) {
         case NG_F64: return launch_beam_variant<ORDER, LINEAR, CH, NG_F64>(p, grid, smem, s);
-        case NG_CF32: return launch_beam_variant<ORDER, LINEAR, CH, NG_CF32>(p, grid, smem, s);
-        default: return launch_beam_variant<ORDER, LINEAR, CH, NG_F32>(p, grid, smem, s);
+        case NG_F32: return launch_beam_variant<ORDER, LINEAR, CH, NG_F32>(p, grid, smem, s);
+        default: return launch_beam_variant<ORDER, LINEAR, CH, NG_CF32>(p, grid, smem, s);
     }
 }
 
@@ -151,10 +151,10 @@ cudaError_t launch_beam_batch_ng(const BeamBatch &b, int ngp, unsigned grid,
     switch (ngp) {
         case NG_F64:
             return launch_beam_batch_variant<ORDER, LINEAR, CH, NG_F64>(b, grid, smem, s);
-        case NG_CF32:
-            return launch_beam_batch_variant<ORDER, LINEAR, CH, NG_CF32>(b, grid, smem, s);
-        default:
+        case NG_F32:
             return launch_beam_batch_variant<ORDER, LINEAR, CH, NG_F32>(b, grid, smem, s);
+        default:
+            return launch_beam_batch_variant<ORDER, LINEAR, CH, NG_CF32>(b, grid, smem, s);
     }
 }
 

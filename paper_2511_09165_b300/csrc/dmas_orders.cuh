@@ -457,8 +457,8 @@ cudaError_t launch_orders_ng(const OrdersParams &p, int ngp, unsigned grid, size
                              cudaStream_t s) {
     switch (ngp) {
         case NG_F64: return launch_orders_variant<NMAX, LINEAR, NG_F64>(p, grid, smem, s);
-        case NG_CF32: return launch_orders_variant<NMAX, LINEAR, NG_CF32>(p, grid, smem, s);
-        default: return launch_orders_variant<NMAX, LINEAR, NG_F32>(p, grid, smem, s);
+        case NG_F32: return launch_orders_variant<NMAX, LINEAR, NG_F32>(p, grid, smem, s);
+        default: return launch_orders_variant<NMAX, LINEAR, NG_CF32>(p, grid, smem, s);
     }
 }
 

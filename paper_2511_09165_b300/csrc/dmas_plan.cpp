@@ -148,7 +148,8 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
     if (d.delay_mode != DMAS_DELAY_ROUND && d.delay_mode != DMAS_DELAY_LINEAR)
         return fail("unknown delay_mode");
     if (d.chan_prec < DMAS_CH_F32 || d.chan_prec > DMAS_CH_BF16) return fail("unknown chan_prec");
-    if (d.ng_prec < DMAS_NG_F32 || d.ng_prec > DMAS_NG_CF32) return fail("unknown ng_prec");
+    if (d.ng_prec != DMAS_NG_CF32 && d.ng_prec != DMAS_NG_F64 && d.ng_prec != DMAS_NG_F32)
+        return fail("unknown ng_prec");
     if (d.flags & ~(DMAS_F_CF | DMAS_F_ENVELOPE)) return fail("unknown flag bits");
     if (!finite(d.cf_eps)) return fail("cf_eps must be finite");
     if (d.mf_len < 0 || d.mf_len > kMfMaxLen || (d.mf_len > 0) != (d.mf_signal != nullptr))

@@ -280,10 +280,11 @@ class Server:
                 self._cv.notify_all()
 
 
-def one_frame_per_launch(sensors, requests, device=None):
+def one_frame_per_launch(sensors, requests, device=None, copy_back: bool = False):
     """Baseline: every frame alone through dmas_beamform, in arrival order, on
     one stream.  Blocks until each frame's arrival time; returns the requests
-    with t_done filled."""
+    with t_done filled (the image resident on the device, or with copy_back
+    copied to pinned host memory)."""
     import torch
     dev = torch.device("cuda") if device is None else torch.device(device)
     stream = torch.cuda.Stream(device=dev)
@@ -299,6 +300,10 @@ def one_frame_per_launch(sensors, requests, device=None):
             f = torch.empty((p.n_mics, p.n_samples), device=dev)
             f.copy_(r.frame, non_blocking=True)
             img = p(f, stream=stream)
+            if copy_back:
+                h = torch.empty(img.shape, dtype=torch.float32, pin_memory=True)
+                h.copy_(img, non_blocking=True)
+                img = h
             ev = torch.cuda.Event()
             ev.record(stream)
             pending.append((ev, r))

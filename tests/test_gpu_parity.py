@@ -36,6 +36,14 @@ def passive(N=100, T=700, n_az=16, n_el=8):
     return scenes.passive(seed=4, n_mics=N, n_samples=T, n_az=n_az, n_el=n_el)
 
 
+# Newton-Girard arithmetic: compensated FP32 (the default), FP64, plain FP32
+NG = {"cf32": "NG_CF32", "f64": "NG_F64", "f32": "NG_F32"}
+
+
+def ng_prec(name):
+    return getattr(dm, NG[name])
+
+
 def run_gpu(scene, order, mode, want_y=True, want_cf=True, **kw):
     plan = gpu_plan(dm, scene, order, mode, **kw)
     frame = torch.from_numpy(scene.frame).cuda()
@@ -127,20 +135,23 @@ def test_every_order_round(order):
     assert_parity(g, r)
 
 
+@pytest.mark.parametrize("ng", ["cf32", "f64", "f32"])
 @pytest.mark.parametrize("order", [1, 2, 3, 4, 5])
-def test_every_order_linear(order):
+def test_every_order_linear(order, ng):
+    """The interpolated-delay pair kernel (the benchmark's) at every order it
+    serves, with each Newton-Girard arithmetic: 1500 samples (ragged last
+    tile) x 200 directions (ragged last group)."""
     sc = hemi(1500, 200)
-    g = run_gpu(sc, order, dm.LINEAR)
+    g = run_gpu(sc, order, dm.LINEAR, ng_prec=ng_prec(ng))
     r = oracle_run(sc, order, oracle.LINEAR)
     assert_parity(g, r)
 
 
-@pytest.mark.parametrize("ng", ["f64", "cf32"])
-@pytest.mark.parametrize("order", [3, 5, 7])
+@pytest.mark.parametrize("ng", ["cf32", "f64", "f32"])
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 7])
 def test_newton_girard_precisions(ng, order):
     sc = small_2d(1000)
-    ngp = {"f64": dm.NG_F64, "cf32": dm.NG_CF32}[ng]
-    g = run_gpu(sc, order, dm.ROUND, ng_prec=ngp)
+    g = run_gpu(sc, order, dm.ROUND, ng_prec=ng_prec(ng))
     r = oracle_run(sc, order, oracle.ROUND)
     assert_parity(g, r)
 
@@ -248,9 +259,10 @@ def _explicit(frame, tau, fs, order, mode=dm.ROUND, **kw):
     return {"img": img.cpu().numpy(), "y": y.cpu().numpy(), "cf": cf.cpu().numpy()}
 
 
+@pytest.mark.parametrize("ng", ["cf32", "f64"])
 @pytest.mark.parametrize("frac", [1e-4, 0.5, 0.9999])
 @pytest.mark.parametrize("order", [3, 5])
-def test_interpolation_weights_near_the_ends(frac, order):
+def test_interpolation_weights_near_the_ends(frac, order, ng):
     """Interpolated delays whose fractions all sit near 0, at 1/2 or near 1: the
     kernel forms the (1 - f)-weighted sums as plain minus f-weighted ones, which
     near f = 1 is a difference of nearly equal sums."""
@@ -258,7 +270,8 @@ def test_interpolation_weights_near_the_ends(frac, order):
     N, T, M, fs = 32, 1500, 24, 1000.0
     frame = rng.standard_normal((N, T)).astype(np.float32)
     tau = (rng.integers(-20, 21, size=(M, N)) + frac) / fs
-    g = _explicit(frame, tau, fs, order, dm.LINEAR, env_cutoff_hz=100.0, env_taps=15)
+    g = _explicit(frame, tau, fs, order, dm.LINEAR, env_cutoff_hz=100.0, env_taps=15,
+                  ng_prec=ng_prec(ng))
     r = oracle.dmas(frame.astype(np.float64), tau, fs, order, oracle.LINEAR, use_cf=True,
                     taps=oracle.fir_taps(fs, 100.0, 15))
     assert_parity(g, r)
@@ -353,11 +366,11 @@ def test_host_buffers_and_batch_equal_device_path():
     p2.close()
 
 
-def sampled_rows_parity(sc, order, gpu_mode, oracle_mode, cf=True):
+def sampled_rows_parity(sc, order, gpu_mode, oracle_mode, cf=True, **kw):
     """Whole frame on the GPU in the benchmark's launch configuration; blocks
     of 8 rows sampled across the direction range, plus the rows around the
     image peak, compared with the oracle."""
-    plan = gpu_plan(dm, sc, order, gpu_mode, cf=cf)
+    plan = gpu_plan(dm, sc, order, gpu_mode, cf=cf, **kw)
     x = torch.from_numpy(sc.frame).cuda()
     y = torch.empty((sc.n_dirs, sc.n_samples), device="cuda")
     img = plan(x, y=y)
@@ -402,10 +415,13 @@ def test_host_path_in_time_chunks_equals_device_path(mode, kw, M):
     assert np.array_equal(got, ref)
 
 
-def test_full_size_hemisphere_sampled_rows():
+@pytest.mark.parametrize("ng", ["cf32", "f64"])
+def test_full_size_hemisphere_sampled_rows(ng):
     """The timed workload: 2048 directions x 16384 samples, linear delays,
-    n = 5, CF, envelope."""
-    sampled_rows_parity(scenes.hemi_3d(seed=2), 5, dm.LINEAR, oracle.LINEAR)
+    n = 5, CF, envelope; compensated FP32 (the benchmark's) and FP64
+    Newton-Girard."""
+    sampled_rows_parity(scenes.hemi_3d(seed=2), 5, dm.LINEAR, oracle.LINEAR,
+                        ng_prec=ng_prec(ng))
 
 
 def test_full_size_hemisphere_nearest_sampled_rows():

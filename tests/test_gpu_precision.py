@@ -61,3 +61,40 @@ def test_precision_table():
     for r in rows:
         print(f" {r[0]}  {r[1]:8s}  {r[2]:4s}  {r[3]:11.3e}  {r[4]:13.3e}  {r[5]:6.4f}  "
               f"{r[6]:7.5f}  {r[7]:10.3e}")
+
+
+# Roots chosen as signed powers of two (so every delayed root, its powers and
+# the FP32 power sums are exact) whose fifth elementary symmetric polynomial is
+# E_5 = 480 while the terms of Eq. dmas5_impl reach 9e9: a pixel where the
+# alternating sum cancels about five decimal digits.  The same set is pinned
+# on the CPU in tests/test_ng_conditioning.py.
+ILL_ROOTS_N5 = [4, -8, 4, -4, -2, -4, -16, -16, -4, 16, 8, 1, 8, 8, 0, 8, 0, 8, 2, -4, -2, 0,
+                2, 0, -8, -16, -16, -16, 1, -16, 8, -16]
+
+
+@pytest.mark.parametrize("mode", ["round", "linear"])
+def test_newton_girard_cancellation_needs_compensation(mode):
+    """Every pixel of this frame sees the same 32 roots (the frame is constant
+    in time and every delay is zero), so y = E_5 = 480 everywhere.  Compensated
+    FP32 and FP64 Newton-Girard reproduce it to the 1e-5 gate; plain FP32,
+    whose rounding errors scale with the 9e9 terms, misses it by orders of
+    magnitude.  Nearest-sample and interpolated (fraction 0) delays run the two
+    pair kernels."""
+    roots = np.array(ILL_ROOTS_N5, dtype=np.float64)
+    T, M = 300, 16
+    frame = np.repeat((roots ** 5)[:, None], T, axis=1).astype(np.float32)
+    tau = np.zeros((M, roots.size))
+    errs = {}
+    for name, ngp in (("cf32", dm.NG_CF32), ("f64", dm.NG_F64), ("f32", dm.NG_F32)):
+        plan = dm.Plan(delays_s=tau, n_samples=T, fs=1000.0, order=5,
+                       delay_mode=dm.LINEAR if mode == "linear" else dm.ROUND, cf=False,
+                       envelope=False, ng_prec=ngp)
+        y = plan(torch.from_numpy(frame).cuda())
+        torch.cuda.synchronize()
+        plan.check()
+        plan.close()
+        y = y.cpu().numpy().astype(np.float64)
+        errs[name] = float(np.max(np.abs(y - 480.0)) / 480.0)
+    print(f"\n{mode}: relative error of E_5 = 480: {errs}")
+    assert errs["cf32"] <= 1e-5 and errs["f64"] <= 1e-5
+    assert errs["f32"] > 1e-3

@@ -1,13 +1,16 @@
-"""dmas_beamform_noalloc: beamforming for callers that must not allocate
-device memory while processing frames (a real-time loop that cannot afford a
-cudaMalloc, which may synchronise the device, or a process whose GPU memory is
-already reserved by another allocator).  Its scratch is a static device array
+"""dmas_beamform_noalloc: beamforming for callers that may allocate at set-up
+but must not allocate device memory while processing frames (a real-time loop
+with a frame deadline cannot afford a cudaMalloc, which may synchronise the
+device and take an unbounded time).  Its scratch is a static device array
 inside the library.
 
-The test calls the entry point through the C ABI twice in a row, on two
-different frames, and compares each result with dmas_beamform on the same
-plan and frame.  It lives in its own file, collected last, and passes both
-alone in a fresh process and after the rest of the suite.
+The tests call the entry point through the C ABI twice in a row, on two
+different frames, and compare each result with dmas_beamform on the same plan
+and frame: once with nearest-sample delays, once with interpolated delays
+(whose kernel reads the root rows through a tensor map built over whichever
+scratch the call uses, so alternating the two entry points on one plan must
+rebuild it each time).  They live in their own file, collected last, and pass
+both alone in a fresh process and after the rest of the suite.
 """
 import ctypes
 
@@ -47,6 +50,28 @@ def test_noalloc_matches_beamform_on_two_calls_in_a_row():
         w, g = want.cpu().numpy(), got.cpu().numpy()
         assert np.all(np.isfinite(g))
         assert eps_peak(g, w) <= TOL_F32
+    plan.close()
+
+
+def test_noalloc_interpolated_delays_alternating_with_beamform():
+    lib = dm.load_library()
+    sc = scenes.hemi_3d(seed=2, n_samples=2048, n_dirs=256)   # linear delays, 2 MiB y
+    plan = dm.Plan(mic_xyz=sc.mic_xyz, dir_unit=sc.dir_unit, n_samples=sc.n_samples,
+                   fs=sc.fs, c=sc.c, order=5, delay_mode=dm.LINEAR)
+    assert plan.workspace_bytes() <= 16 << 20
+    frames = [torch.from_numpy(sc.frame).cuda(),
+              torch.from_numpy(scenes.hemi_3d(seed=12, n_samples=2048, n_dirs=256).frame).cuda()]
+    for frame in frames:
+        want = plan(frame).clone()                  # plan scratch
+        got = torch.full_like(want, float("nan"))
+        assert _call_noalloc(lib, plan, frame, got) == 0   # static scratch
+        again = plan(frame)                         # plan scratch again
+        torch.cuda.synchronize()
+        plan.check()
+        w, g, a = want.cpu().numpy(), got.cpu().numpy(), again.cpu().numpy()
+        assert np.all(np.isfinite(g))
+        assert eps_peak(g, w) <= TOL_F32
+        assert np.array_equal(a, w)
     plan.close()
 
 
