@@ -729,7 +729,7 @@ def run_sweep(args) -> None:
 
 
 # ---------------------------------------------------------------------------
-# image SNR against microphone SNR (the paper's Sec. IV-A experiment, Table I)
+# image SNR against microphone SNR (the paper's Sec. III-A experiment, Table I)
 # ---------------------------------------------------------------------------
 IMAGE_SNR_MIC_DB = [-40.0, -30.0, -20.0, -10.0, 0.0, 10.0]
 
@@ -812,7 +812,7 @@ def run_orders(args) -> None:
     steps = max(5, min(args.steps, 30))
     paper = args.workload == "orders_paper"
     if paper:
-        # the paper's real-world imaging setting (Sec. IV-B): 3601 azimuths at
+        # the paper's real-world imaging setting (Sec. III-B): 3601 azimuths at
         # 0.05 deg, 163840 samples, the eRTIS chirp and its matched filter
         sc = scenes.small_2d(seed=1, n_samples=163840, n_dirs=3601, pulse="chirp")
         mf = scenes.lfm_chirp(sc.fs).astype(np.float32)

@@ -1,4 +1,4 @@
-"""The paper's qualitative image-quality claims (Sec. IV-A, Table I), checked
+"""The paper's qualitative image-quality claims (Sec. III-A, Table I), checked
 on a seeded point-target scene: at 0 dB microphone SNR the image SNR (mean
 off-target level of the normalised image) rises with the DMAS order and the
 coherence factor raises it at every order; without noise, the dynamic range

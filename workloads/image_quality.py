@@ -1,6 +1,6 @@
 """Image-quality measures of an acoustic image (post-processing only).
 
-The image SNR follows the paper's simulation analysis (Sec. IV-A, Table I):
+The image SNR follows the paper's simulation analysis (Sec. III-A, Table I):
 the image is normalised to a maximum of one, E_off is the mean over the
 off-target pixels, and SNR_image = 20 log10(1 / E_off).  Which pixels count
 as on target is not stated there; here it is the window within max_az_deg of
@@ -8,7 +8,7 @@ the target's azimuth and within max_range_m of its range (one-way range
 c t).  The peak-to-sidelobe ratio is 20 log10(1 / max over the same
 off-target pixels) of the normalised image.
 
-The directional point-spread function (Sec. IV-A, the noise-free point
+The directional point-spread function (Sec. III-A, the noise-free point
 target) is the image's maximum over t per direction, normalised to one; its
 dynamic range is read here as 20 log10(1 / median over the directions outside
 the main lobe), the depth of its typical side-lobe floor (the paper reads the
