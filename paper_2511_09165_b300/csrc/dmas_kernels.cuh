@@ -787,6 +787,17 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
     const int t0 = tile * kTile;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    // The stage's copies are issued by every warp (warp w: microphones w,
+    // w + 8, ..., one per lane), the first chunk's window starts read before
+    // the barrier is even initialised, the tables first.  (Measured on B300,
+    // 2048 x 16384 frame, compensated Newton-Girard: 785 -> 773 us against
+    // all copies issued by warp 0 after the barrier set-up.  A per-CTA
+    // %globaltimer probe of that earlier form: 0.2 us to the barrier, 0.5 us
+    // for the window starts, 1.4 us issuing the 35 copies, 0.2 us until they
+    // landed, 5.1 us of microphone loop, 0.9 us of epilogue.)
+    const int *gws = p.gws + (size_t)g * p.N;
+    int x_first = 0;
+    if (warp + 8 * lane < min(NC, p.N)) x_first = gws[warp + 8 * lane];
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
@@ -808,29 +819,30 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
     uint32_t parity = 0;
     for (int c0 = 0; c0 < p.N; c0 += NC) {
         const int nc = min(NC, p.N - c0);
-        if (c0 > 0) __syncthreads();  // every warp is done with the previous chunk
-        if (warp == 0) {
-            const uint32_t row_bytes = (uint32_t)(WS * 4);
-            const uint32_t tab_bytes = (uint32_t)(nc * 8 * 4);
-            if (lane == 0) mbar_arrive_expect_tx(bar, 2 * nc * row_bytes + 6 * tab_bytes);
-            __syncwarp();
-            const int *gws = p.gws + (size_t)g * p.N;
-            for (int il = lane; il < nc; il += 32) {
-                const int i = c0 + il;
-                const int x = p.padl + t0 + gws[i];  // a multiple of 8 samples (32 bytes)
-                if (p.use_tma) {
-                    tma_load_3d(win + il * MBf, &p.tmap, x, i, 0, bar);
-                } else {
-                    const size_t o = (size_t)i * p.row + x;
-                    bulk_g2s(win + il * MBf, chan0 + o, row_bytes, bar);
-                    bulk_g2s(win + il * MBf + WS, chan1 + o, row_bytes, bar);
-                }
-            }
-            if (lane == 0) {
-                const size_t to = ((size_t)g * p.N + c0) * 8;
-                bulk_g2s(s_rel, p.rel + to, tab_bytes, bar);
-                bulk_g2s(s_sel, p.sel + to, tab_bytes, bar);
-                bulk_g2s(s_w4, p.w4 + to * 4, 4 * tab_bytes, bar);
+        const uint32_t row_bytes = (uint32_t)(WS * 4);
+        const uint32_t tab_bytes = (uint32_t)(nc * 8 * 4);
+        if (c0 > 0) {
+            __syncthreads();  // every warp is done with the previous chunk
+            if (warp + 8 * lane < nc) x_first = gws[c0 + warp + 8 * lane];
+        }
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect_tx(bar, 2 * nc * row_bytes + 6 * tab_bytes);
+            const size_t to = ((size_t)g * p.N + c0) * 8;
+            bulk_g2s(s_rel, p.rel + to, tab_bytes, bar);
+            bulk_g2s(s_sel, p.sel + to, tab_bytes, bar);
+            bulk_g2s(s_w4, p.w4 + to * 4, 4 * tab_bytes, bar);
+        }
+        __syncthreads();  // the byte count is set before any copy can land
+        for (int il = warp + 8 * lane; il < nc; il += kThreads) {
+            const int i = c0 + il;
+            // a multiple of 8 samples (32 bytes)
+            const int x = p.padl + t0 + (il < kThreads ? x_first : gws[i]);
+            if (p.use_tma) {
+                tma_load_3d(win + il * MBf, &p.tmap, x, i, 0, bar);
+            } else {
+                const size_t o = (size_t)i * p.row + x;
+                bulk_g2s(win + il * MBf, chan0 + o, row_bytes, bar);
+                bulk_g2s(win + il * MBf + WS, chan1 + o, row_bytes, bar);
             }
         }
         const bool ok = mbar_wait_sleep_bounded(bar, parity);
