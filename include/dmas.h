@@ -285,6 +285,19 @@ dmas_status dmas_plan_stage_ms(dmas_plan *plan, float *roots_ms, float *beam_ms,
                                float *env_ms);
 
 /*
+ * Scheduling of the tensor-core envelope (a serving knob; results do not
+ * change).  By default its launch has one CTA per SM, each looping over its
+ * share of the frame's tiles, so a big frame's envelope holds every SM until
+ * it ends.  With tiles_per_cta > 0 the launch has at least
+ * ceil(tiles / tiles_per_cta) CTAs, each retiring after at most that many
+ * tiles, so kernels on higher-priority streams reach the SMs within a few
+ * tiles' time.  0 restores the default.  Not synchronised with calls in
+ * flight: set it before enqueueing work.  Errors: DMAS_EINVAL (NULL plan or a
+ * negative count).
+ */
+dmas_status dmas_plan_set_envelope_tile_cap(dmas_plan *plan, int tiles_per_cta);
+
+/*
  * Self-test of the kernels' bounded waits: launches one CTA that waits on a
  * shared-memory barrier no copy ever completes, with a limit of `limit_ms`
  * milliseconds (1 .. 10000).  The kernel gives up, sets its error word and

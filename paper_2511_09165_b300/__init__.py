@@ -38,6 +38,7 @@ EXPORTS = [
     "dmas_plan_get_info", "dmas_plan_get_delays", "dmas_plan_get_taps", "dmas_plan_check",
     "dmas_plan_last_error", "dmas_plan_set_profiling", "dmas_plan_stage_ms",
     "dmas_selftest_wait_timeout", "dmas_beamform_noalloc", "dmas_status_string",
+    "dmas_plan_set_envelope_tile_cap",
     "dmas_version",
 ]
 
@@ -104,6 +105,7 @@ def load_library(path: str | None = None):
             "dmas_plan_check": ([vp], i),
             "dmas_plan_last_error": ([vp], ctypes.c_char_p),
             "dmas_plan_set_profiling": ([vp, i], i),
+            "dmas_plan_set_envelope_tile_cap": ([vp, i], i),
             "dmas_plan_stage_ms": ([vp, fp, fp, fp], i),
             "dmas_selftest_wait_timeout": ([ctypes.c_double, vp], i),
             "dmas_beamform_noalloc": ([vp, vp, vp, vp], i),
@@ -275,6 +277,13 @@ class Plan:
         st = self._lib.dmas_plan_set_profiling(self.handle, int(bool(enable)))
         if st != 0:
             self._raise(st, "dmas_plan_set_profiling")
+
+    def set_envelope_tile_cap(self, tiles_per_cta: int) -> None:
+        """At most this many tensor-core envelope tiles per CTA (0: one CTA per
+        SM over all tiles), so higher-priority streams reach the SMs sooner."""
+        st = self._lib.dmas_plan_set_envelope_tile_cap(self.handle, int(tiles_per_cta))
+        if st != 0:
+            self._raise(st, "dmas_plan_set_envelope_tile_cap")
 
     def stage_ms(self):
         """(roots, beamform, envelope) milliseconds of the last profiled call."""

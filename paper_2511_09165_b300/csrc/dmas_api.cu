@@ -107,6 +107,9 @@ struct dmas_plan {
     float *d_mf = nullptr;            // matched filter: the emitted signal [mf_len], or null
     size_t mf_bytes = 0;              // matched-filtered frame in the scratch (0: no filter)
     int num_sms = 148;
+    // tensor-core envelope: at most this many tiles per CTA (0: one CTA per SM
+    // over all tiles); see dmas_plan_set_envelope_tile_cap
+    int env_tile_cap = 0;
     cudaStream_t last_stream = nullptr;
     std::string last_error;
     // stage profiling
@@ -263,6 +266,16 @@ std::vector<float> tc_tap_arrays(const HostPlan &hp) {
         }
     }
     return out;
+}
+
+// CTAs of a tensor-core envelope launch over `tiles` tiles: one per SM, each
+// looping over its share, or with a cap of `cap` tiles per CTA (cap > 0) at
+// least ceil(tiles / cap), so CTAs retire every `cap` tiles and kernels on
+// higher-priority streams reach the SMs sooner.
+unsigned env_grid(unsigned tiles, int num_sms, int cap) {
+    unsigned g = std::min<unsigned>(tiles, (unsigned)num_sms);
+    if (cap > 0) g = std::max<unsigned>(g, (tiles + (unsigned)cap - 1) / (unsigned)cap);
+    return g;
 }
 
 cudaError_t launch_env_tc(const EnvTcParams &ep, unsigned grid, size_t smem, cudaStream_t s) {
@@ -585,7 +598,7 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
     ep.n_stages = env_tc_stages(hp);
     ep.taps = p->d_taps_tc;
     ep.err = p->d_err;
-    e = launch_env_tc(ep, std::min<unsigned>(ep.total_tiles, (unsigned)p->num_sms), p->smem_env, s);
+    e = launch_env_tc(ep, env_grid(ep.total_tiles, p->num_sms, p->env_tile_cap), p->smem_env, s);
     if (e != cudaSuccess) return cuda_fail(p, e, "envelope_tc_kernel launch");
     mark(p, 3, s);
     p->env_ran = true;
@@ -661,7 +674,7 @@ dmas_status enqueue_host_chunks(dmas_plan *p, const float *d_frame, float *d_ima
             ep.n_stages = env_tc_stages(hp);
             ep.taps = p->d_taps_tc;
             ep.err = p->d_err;
-            e = launch_env_tc(ep, std::min<unsigned>(ep.total_tiles, (unsigned)p->num_sms),
+            e = launch_env_tc(ep, env_grid(ep.total_tiles, p->num_sms, p->env_tile_cap),
                               p->smem_env, s);
             if (e != cudaSuccess) return cuda_fail(p, e, "envelope_tc_kernel launch");
         }
@@ -821,7 +834,12 @@ dmas_status enqueue_batch(const std::vector<BatchEntry> &v, cudaStream_t s) {
             ep.n_stages = env_tc_stages(a);
             ep.taps = pa->d_taps_tc;
             ep.err = pa->d_err;
-            e = launch_env_tc(ep, std::min<unsigned>(tiles, (unsigned)pa->num_sms), pa->smem_env, s);
+            int cap = 0;  // the smallest cap any entry asks for
+            for (int k = 0; k < ep.count; ++k) {
+                const int c = v[cls[b0 + k]].plan->env_tile_cap;
+                if (c > 0 && (cap == 0 || c < cap)) cap = c;
+            }
+            e = launch_env_tc(ep, env_grid(tiles, pa->num_sms, cap), pa->smem_env, s);
             if (e != cudaSuccess) return cuda_fail(v[cls[b0]].plan, e, "envelope batch");
         }
     }
@@ -956,7 +974,7 @@ dmas_status enqueue_orders(dmas_plan *p, const float *d_frame, unsigned mask, in
             ep.n_stages = env_tc_stages(hp);
             ep.taps = p->d_taps_tc;
             ep.err = p->d_err;
-            e = launch_env_tc(ep, std::min<unsigned>(ep.total_tiles, (unsigned)p->num_sms),
+            e = launch_env_tc(ep, env_grid(ep.total_tiles, p->num_sms, p->env_tile_cap),
                               p->smem_env, s);
             if (e != cudaSuccess) return cuda_fail(p, e, "envelope_tc_kernel launch");
         }
@@ -1247,6 +1265,12 @@ dmas_status dmas_plan_check(dmas_plan *p) {
 const char *dmas_plan_last_error(const dmas_plan *p) {
     if (!p) return "";
     return p->last_error.c_str();
+}
+
+dmas_status dmas_plan_set_envelope_tile_cap(dmas_plan *p, int tiles_per_cta) {
+    if (!p || tiles_per_cta < 0) return DMAS_EINVAL;
+    p->env_tile_cap = tiles_per_cta;
+    return DMAS_OK;
 }
 
 dmas_status dmas_plan_set_profiling(dmas_plan *p, int enable) {

@@ -67,6 +67,31 @@ class Sensor:
 # Frames of at most this cost (microphones x directions x samples) take the
 # fast lane.
 FAST_COST = 1.3e9
+# Tensor-core envelope tiles per CTA for the bulk lane's plans
+BULK_ENV_TILE_CAP = 16
+
+
+class PinnedPool:
+    """Page-locked host buffers reused by shape: allocating pinned memory
+    takes milliseconds per gigabyte, so copies back to the host draw on this
+    pool instead of allocating per frame."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        self._free: dict = collections.defaultdict(list)
+        self._mu = threading.Lock()
+
+    def get(self, shape):
+        with self._mu:
+            lst = self._free.get(tuple(shape))
+            if lst:
+                return lst.pop()
+        return self.torch.empty(tuple(shape), dtype=self.torch.float32, pin_memory=True)
+
+    def put(self, t) -> None:
+        with self._mu:
+            self._free[tuple(t.shape)].append(t)
 
 
 class _Lane:
@@ -108,7 +133,8 @@ class Server:
     def __init__(self, sensors, device=None, budget_bytes: int = 32 << 30,
                  max_batch: int = 64, streams: int = 2, copy_back: bool = False,
                  fast_cost: float = FAST_COST, bulk_batch: int = 1,
-                 bulk_streams: int | None = 3):
+                 bulk_streams: int | None = 3, bulk_env_tile_cap: int = BULK_ENV_TILE_CAP,
+                 pinned: PinnedPool | None = None):
         import torch
         self.torch = torch
         self.sensors = list(sensors)
@@ -131,6 +157,12 @@ class Server:
         self._threads = []
         self.batches = 0
         self.completed: list[Request] = []
+        self.pinned = pinned if pinned is not None else (PinnedPool() if copy_back else None)
+        # big frames' envelopes retire their CTAs every few tiles, so the fast
+        # lane's kernels reach the SMs without waiting for a whole envelope
+        for sn in self.sensors:
+            if sn.cost > self.fast_cost and hasattr(sn.plan, "set_envelope_tile_cap"):
+                sn.plan.set_envelope_tile_cap(bulk_env_tile_cap)
 
     def _lane_of(self, sensor: int) -> _Lane:
         return self.fast if self.sensors[sensor].cost <= self.fast_cost else self.bulk
@@ -235,8 +267,7 @@ class Server:
             beamform_batch(plans, frames, images, workspace=ws, stream=stream)
             hosts = None
             if self.copy_back:
-                hosts = [torch.empty(im.shape, dtype=torch.float32, pin_memory=True)
-                         for im in images]
+                hosts = [self.pinned.get(im.shape) for im in images]
                 for h, im in zip(hosts, images):
                     h.copy_(im, non_blocking=True)
             ev = torch.cuda.Event()
@@ -271,6 +302,8 @@ class Server:
                 r.batch_size = len(batch)
                 if r.keep_image:
                     r.image = hosts[k] if hosts is not None else images[k]
+                elif hosts is not None:
+                    self.pinned.put(hosts[k])
             with self._cv:
                 for r in batch:
                     self._reserved -= self.sensors[r.sensor].device_bytes
@@ -280,40 +313,57 @@ class Server:
                 self._cv.notify_all()
 
 
-def one_frame_per_launch(sensors, requests, device=None, copy_back: bool = False):
+def one_frame_per_launch(sensors, requests, device=None, copy_back: bool = False,
+                         pinned: PinnedPool | None = None):
     """Baseline: every frame alone through dmas_beamform, in arrival order, on
     one stream.  Blocks until each frame's arrival time; returns the requests
     with t_done filled (the image resident on the device, or with copy_back
-    copied to pinned host memory)."""
+    copied to pinned host memory: one buffer per sensor from `pinned`, reused
+    frame after frame since the one stream orders the copies, unless the
+    request keeps its image)."""
     import torch
     dev = torch.device("cuda") if device is None else torch.device(device)
     stream = torch.cuda.Stream(device=dev)
     pending = collections.deque()
+    if copy_back and pinned is None:
+        pinned = PinnedPool()
+    per_sensor = {}
+
+    def finish(ev, q, h):
+        q.t_done = time.perf_counter()
+
     with torch.cuda.stream(stream):
         for r in requests:
             while time.perf_counter() < r.t_arrival:
                 while pending and pending[0][0].query():
-                    ev, q = pending.popleft()
-                    q.t_done = time.perf_counter()
+                    finish(*pending.popleft())
                 time.sleep(0.0002)
             p = sensors[r.sensor].plan
             f = torch.empty((p.n_mics, p.n_samples), device=dev)
             f.copy_(r.frame, non_blocking=True)
             img = p(f, stream=stream)
+            h = None
             if copy_back:
-                h = torch.empty(img.shape, dtype=torch.float32, pin_memory=True)
+                if r.keep_image:
+                    h = pinned.get(img.shape)
+                else:
+                    h = per_sensor.get(r.sensor)
+                    if h is None:
+                        h = per_sensor[r.sensor] = pinned.get(img.shape)
                 h.copy_(img, non_blocking=True)
                 img = h
             ev = torch.cuda.Event()
             ev.record(stream)
-            pending.append((ev, r))
+            pending.append((ev, r, h))
             r.batch_size = 1
             if r.keep_image:
                 r.image = img
     while pending:
-        ev, q = pending.popleft()
+        ev, q, h = pending.popleft()
         ev.synchronize()
-        q.t_done = time.perf_counter()
+        finish(ev, q, h)
+    for h in per_sensor.values():
+        pinned.put(h)
     return requests
 
 

@@ -151,3 +151,24 @@ def test_frame_path_replays_from_a_cuda_graph():
     torch.cuda.synchronize()
     assert torch.equal(image, ref)
     plan.close()
+
+
+@pytest.mark.parametrize("cap", [1, 3, 16])
+def test_envelope_tile_cap_changes_scheduling_not_results(cap):
+    """dmas_plan_set_envelope_tile_cap retires the tensor-core envelope's CTAs
+    every `cap` tiles; the image is bitwise the uncapped one, alone and in a
+    batch."""
+    sc = scenes.hemi_3d(seed=2, n_samples=4100, n_dirs=1200)   # tensor-core envelope
+    plan = _plan(sc, 5, dm.LINEAR)
+    x = torch.from_numpy(sc.frame).cuda()
+    want = plan(x).clone()
+    plan.set_envelope_tile_cap(cap)
+    got = plan(x).clone()
+    b1, b2 = dm.beamform_batch([plan, plan], [x, x])
+    plan.set_envelope_tile_cap(0)
+    again = plan(x)
+    torch.cuda.synchronize()
+    plan.check()
+    plan.close()
+    assert torch.equal(got, want) and torch.equal(b1, want) and torch.equal(b2, want)
+    assert torch.equal(again, want)
