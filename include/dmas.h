@@ -46,7 +46,9 @@ typedef enum {
     DMAS_ENOMEM = 2,   /* a device or host allocation failed */
     DMAS_ECUDA = 3,    /* a CUDA runtime call or kernel launch failed (see dmas_plan_last_error) */
     DMAS_EBUSY = 4,    /* reserved for the serving layer: no capacity right now */
-    DMAS_ETIMEOUT = 5  /* a device-side bounded wait expired (error word set by a kernel) */
+    DMAS_ETIMEOUT = 5, /* a device-side bounded wait expired (error word set by a kernel) */
+    DMAS_EBOUNDS = 6   /* host-checked build (libdmas_checked.so) only: a kernel index fell
+                          outside its buffer and the access was skipped (a library bug) */
 } dmas_status;
 
 /* How tau_{i,psi} * fs is turned into a sample position (Eq. signal_delay). */
@@ -264,8 +266,17 @@ dmas_status dmas_plan_get_taps(const dmas_plan *plan, float *taps);
 
 /*
  * Synchronise the plan's last stream and read the device error word that the
- * kernels set when a bounded wait expired.  Returns DMAS_OK, DMAS_ETIMEOUT or
+ * kernels set when a bounded wait expired (or, in the host-checked build, when
+ * an index test failed).  Returns DMAS_OK, DMAS_ETIMEOUT, DMAS_EBOUNDS or
  * DMAS_ECUDA; clears the error word.
+ *
+ * Host-checked build: built beside libdmas.so as libdmas_checked.so (the same
+ * sources compiled with DMAS_CHECKED), in which the beamform, every-order and
+ * envelope kernels test every shared- and global-memory index they compute
+ * (staged windows against their rows and shared-memory blocks, gathers
+ * against their microphone's window, table copies, image rows) before the
+ * access; a failing test skips the access and sets the error word, so an
+ * indexing bug shows up as DMAS_EBOUNDS on a small case instead of a fault.
  */
 dmas_status dmas_plan_check(dmas_plan *plan);
 

@@ -20,6 +20,17 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libdmas.so")
+# the host-checked build: every kernel index tested before its access
+CHECKED_LIB_PATH = os.path.join(_PKG, "_lib", "libdmas_checked.so")
+
+
+def _default_lib_path() -> str:
+    """libdmas.so, or with DMAS_LIBRARY=checked the host-checked build (any
+    other value is taken as a path)."""
+    v = os.environ.get("DMAS_LIBRARY", "")
+    if v == "checked":
+        return CHECKED_LIB_PATH
+    return v or LIB_PATH
 
 ROUND, LINEAR = 0, 1
 CH_F32, CH_F16, CH_BF16 = 0, 1, 2
@@ -28,7 +39,7 @@ F_CF, F_ENVELOPE = 1, 2
 V_PLAIN, V_CF = 1, 2  # dmas_beamform_orders: images without / with the coherence factor
 
 STATUS = {0: "DMAS_OK", 1: "DMAS_EINVAL", 2: "DMAS_ENOMEM", 3: "DMAS_ECUDA",
-          4: "DMAS_EBUSY", 5: "DMAS_ETIMEOUT"}
+          4: "DMAS_EBUSY", 5: "DMAS_ETIMEOUT", 6: "DMAS_EBOUNDS"}
 
 # Every symbol include/dmas.h declares.
 EXPORTS = [
@@ -83,7 +94,7 @@ def load_library(path: str | None = None):
     with _lock:
         if _lib is not None:
             return _lib
-        p = path or LIB_PATH
+        p = path or _default_lib_path()
         if not os.path.exists(p):
             raise RuntimeError(
                 f"{p} is missing; build it with `python -m paper_2511_09165_b300.build`")

@@ -475,6 +475,7 @@ BeamParams beam_params(const dmas_plan *p, void *scratch, float *ybuf, float *d_
     bp.window = hp.window;
     bp.mic_chunk = hp.mic_chunk;
     bp.n_groups = hp.n_groups;
+    bp.M = hp.M;
     bp.n_tiles = hp.n_tiles;
     bp.item0 = 0;
     bp.n_items = (unsigned)((size_t)hp.n_groups * hp.n_tiles);
@@ -581,6 +582,7 @@ dmas_status enqueue_frame(dmas_plan *p, const float *d_frame, float *d_image, fl
         fp.count = 1;
         fp.H = (hp.L - 1) / 2;
         fp.taps = p->d_taps;
+        fp.err = p->d_err;
         fp.job[0] = fir_job(p, ybuf, d_image, 0);
         envelope_fir_kernel<<<fir_ctas(p), kFirTile, 0, s>>>(fp);
         if ((e = cudaGetLastError()) != cudaSuccess)
@@ -657,6 +659,7 @@ dmas_status enqueue_host_chunks(dmas_plan *p, const float *d_frame, float *d_ima
             fp.count = 1;
             fp.H = H;
             fp.taps = p->d_taps;
+            fp.err = p->d_err;
             fp.job[0] = fir_job(p, ybuf, d_image, 0);
             fp.job[0].tt0 = u_lo;
             fp.job[0].t_tiles = u_hi - u_lo;
@@ -815,6 +818,7 @@ dmas_status enqueue_batch(const std::vector<BatchEntry> &v, cudaStream_t s) {
             }
             fp.H = (a.L - 1) / 2;
             fp.taps = v[cls[b0]].plan->d_taps;
+            fp.err = v[cls[b0]].plan->d_err;
             envelope_fir_kernel<<<ctas, kFirTile, 0, s>>>(fp);
             if ((e = cudaGetLastError()) != cudaSuccess)
                 return cuda_fail(v[cls[b0]].plan, e, "envelope fir batch");
@@ -961,6 +965,7 @@ dmas_status enqueue_orders(dmas_plan *p, const float *d_frame, unsigned mask, in
             fp.count = 1;
             fp.H = (hp.L - 1) / 2;
             fp.taps = p->d_taps;
+            fp.err = p->d_err;
             fp.job[0] = fir_job(p, ybuf, d_images, 0, rows);
             envelope_fir_kernel<<<fir_ctas(p, rows), kFirTile, 0, s>>>(fp);
             if ((e = cudaGetLastError()) != cudaSuccess)
@@ -998,6 +1003,7 @@ const char *dmas_status_string(dmas_status s) {
         case DMAS_ECUDA: return "CUDA error";
         case DMAS_EBUSY: return "busy";
         case DMAS_ETIMEOUT: return "device wait timed out";
+        case DMAS_EBOUNDS: return "kernel index out of bounds (host-checked build)";
     }
     return "unknown status";
 }
@@ -1256,6 +1262,10 @@ dmas_status dmas_plan_check(dmas_plan *p) {
         return cuda_fail(p, e, "error word read");
     if (word) {
         cudaMemset(p->d_err, 0, sizeof(unsigned));
+        if (word & kErrBounds) {
+            p->last_error = "a kernel index fell outside its buffer (host-checked build)";
+            return DMAS_EBOUNDS;
+        }
         p->last_error = "a device wait timed out";
         return DMAS_ETIMEOUT;
     }

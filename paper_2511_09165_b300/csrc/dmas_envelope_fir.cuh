@@ -28,6 +28,7 @@ struct EnvFirParams {
     int count;
     int H;
     const float *taps;  // [2H + 1] (device)
+    unsigned *err;      // error word (host-checked build)
     EnvFirJob job[kBatchMax];
 };
 
@@ -41,6 +42,7 @@ __global__ void __launch_bounds__(kFirTile) envelope_fir_kernel(const __grid_con
     const int row = (int)(local / (unsigned)jb.t_tiles);
     const int t0 = (jb.tt0 + (int)(local - (unsigned)row * (unsigned)jb.t_tiles)) * kFirTile;
     const int H = p.H, L = 2 * H + 1;
+    if (!checked_ok(H >= 0 && H <= kFirMaxH && row < jb.M, p.err)) return;
     const float *yrow = jb.y + (size_t)row * jb.T;
     for (int i = threadIdx.x; i < L; i += kFirTile) s_h[i] = p.taps[i];
     for (int i = threadIdx.x; i < kFirTile + 2 * H; i += kFirTile) {

@@ -250,11 +250,19 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
     unsigned char *base = env_smem + ((1024u - (smem_addr(env_smem) & 1023u)) & 1023u);
     float *s_taps = reinterpret_cast<float *>(base);                               // [2][4][Z]
     unsigned char *stages = base + (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023);  // [S]
-    const unsigned n_tiles = (blockIdx.x < p.total_tiles)
+    // host-checked build: the taps and the stages inside the dynamic shared
+    // memory (otherwise the CTA does no tile)
+    const bool layout_ok =
+        checked_ok(p.n_stages >= 2 && p.n_stages <= kTcStages &&
+                       smem_in(s_taps, (uint32_t)(8 * Z * 4)) &&
+                       smem_in(stages, (uint32_t)p.n_stages * (uint32_t)kTcStageBytes),
+                   p.err);
+    const unsigned n_tiles = (layout_ok && blockIdx.x < p.total_tiles)
                                  ? (p.total_tiles - 1 - blockIdx.x) / gridDim.x + 1
                                  : 0;
 
-    for (int i = tid; i < 8 * Z; i += kTcThreadsWS) s_taps[i] = p.taps[i];
+    if (layout_ok)
+        for (int i = tid; i < 8 * Z; i += kTcThreadsWS) s_taps[i] = p.taps[i];
     if (warp == 9) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_addr(&tmem_slot)),

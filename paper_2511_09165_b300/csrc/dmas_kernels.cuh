@@ -32,6 +32,7 @@ namespace dmas {
 constexpr int kThreads = 256;      // 8 warps, one direction each
 constexpr int kPix = 8;            // scalar kernel: output samples per lane (tile 32 x kPix)
 constexpr unsigned kErrTimeout = 1u;
+constexpr unsigned kErrBounds = 2u;   // host-checked build: an index left its buffer
 constexpr unsigned kWorkSlots = 64;  // beamform work counters per frame (one per launch)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
@@ -40,6 +41,47 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---------------------------------------------------------------------------
+// Host-checked build (compiled with DMAS_CHECKED; libdmas_checked.so): the
+// kernels test their shared- and global-memory indices before each access.
+// A failed test sets kErrBounds in the plan's error word (dmas_plan_check
+// reports DMAS_EBOUNDS) and the access is skipped, so the kernel neither
+// faults nor traps.  In the normal build every test is a compile-time true and
+// costs nothing.
+// ---------------------------------------------------------------------------
+#ifdef DMAS_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+__device__ __forceinline__ bool checked_ok(bool ok, unsigned *err) {
+    if constexpr (kChecked) {
+        if (!ok) {
+            if (err) atomicOr(err, kErrBounds);
+            return false;
+        }
+    }
+    return true;
+}
+
+// The CTA's dynamic shared memory (every kernel's extern __shared__ array
+// starts there) and its size at launch.
+extern __shared__ __align__(128) unsigned char dmas_dyn_smem[];
+__device__ __forceinline__ uint32_t dyn_smem_size() {
+    uint32_t v;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+// [a, a + bytes) lies inside the dynamic shared memory (a: shared address)
+__device__ __forceinline__ bool smem_in(uint32_t a, uint32_t bytes) {
+    const uint32_t base = smem_addr(dmas_dyn_smem);
+    return a >= base && a + bytes <= base + dyn_smem_size();
+}
+__device__ __forceinline__ bool smem_in(const void *p, uint32_t bytes) {
+    return smem_in(smem_addr(p), bytes);
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -59,6 +101,16 @@ __device__ __forceinline__ void fence_mbar_init() {
 
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Count `bytes` as arrived on the barrier without a copy (the host-checked
+// build skips a copy whose range failed its test, and the phase must still
+// complete).
+__device__ __forceinline__ void mbar_complete_tx_local(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(
+                     smem_addr(bar)),
                  "r"(bytes)
                  : "memory");
 }
@@ -487,6 +539,7 @@ struct BeamParams {
     float *cf;           // [M][T] or nullptr
     unsigned *err;       // error word
     int N, T, row, padl, window, mic_chunk, n_groups, n_tiles;
+    int M;               // directions (rows of y)
     unsigned item0;      // first work item (time tile x n_groups + group) of this launch
     unsigned n_items;    // work items of this launch
     float n_mics_f, cf_eps;
@@ -568,13 +621,26 @@ __device__ __forceinline__ void beamform_body(const BeamParams &p, unsigned bloc
             __syncwarp();
             for (int il = lane; il < nc; il += 32) {
                 const int i = c0 + il;
-                const CH *src =
-                    chan + (size_t)i * p.row + p.padl + t0 + p.gws[(size_t)g * p.N + i];
-                bulk_g2s(win + (size_t)il * WS, src, row_bytes, bar);
+                const int x = p.padl + t0 + p.gws[(size_t)g * p.N + i];
+                const CH *src = chan + (size_t)i * p.row + x;
+                if (checked_ok(x >= 0 && x + WS <= p.row && smem_in(win + (size_t)il * WS, row_bytes),
+                               p.err))
+                    bulk_g2s(win + (size_t)il * WS, src, row_bytes, bar);
+                else
+                    mbar_complete_tx_local(bar, row_bytes);
             }
             if (lane == 0) {
-                bulk_g2s(s_rel, p.rel + ((size_t)g * p.N + c0) * 8, tab_bytes, bar);
-                if (LINEAR) bulk_g2s(s_frac, p.frac + ((size_t)g * p.N + c0) * 8, tab_bytes, bar);
+                const bool tabs_ok = checked_ok(
+                    ((size_t)g * p.N + c0 + nc) <= (size_t)p.n_groups * p.N &&
+                        smem_in(s_rel, tab_bytes) && (!LINEAR || smem_in(s_frac, tab_bytes)),
+                    p.err);
+                if (tabs_ok) {
+                    bulk_g2s(s_rel, p.rel + ((size_t)g * p.N + c0) * 8, tab_bytes, bar);
+                    if (LINEAR)
+                        bulk_g2s(s_frac, p.frac + ((size_t)g * p.N + c0) * 8, tab_bytes, bar);
+                } else {
+                    mbar_complete_tx_local(bar, tab_bytes * (LINEAR ? 2u : 1u));
+                }
             }
         }
         const bool ok = mbar_wait_bounded(bar, parity);
@@ -597,6 +663,8 @@ __device__ __forceinline__ void beamform_body(const BeamParams &p, unsigned bloc
         for (int il = 0; il < nc; ++il) {
             const int off = s_rel[il * 8 + warp];
             const CH *rowp = win + (size_t)il * WS + off + lane;
+            if (!checked_ok(off >= 0 && off + 31 + 32 * (kPix - 1) + (LINEAR ? 1 : 0) < WS, p.err))
+                continue;
             if constexpr (LINEAR) {
                 const float f = s_frac[il * 8 + warp];
                 const float w0 = 1.0f - f;
@@ -616,7 +684,7 @@ __device__ __forceinline__ void beamform_body(const BeamParams &p, unsigned bloc
     }
 
     const int dir = p.gdir[(size_t)g * 8 + warp];
-    if (dir < 0) return;
+    if (dir < 0 || !checked_ok(dir < p.M, p.err)) return;
     float *yrow = p.y + (size_t)dir * p.T;
     float *cfrow = p.cf ? p.cf + (size_t)dir * p.T : nullptr;
 #pragma unroll
@@ -828,16 +896,26 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
         if (threadIdx.x == 0) {
             mbar_arrive_expect_tx(bar, 2 * nc * row_bytes + 6 * tab_bytes);
             const size_t to = ((size_t)g * p.N + c0) * 8;
-            bulk_g2s(s_rel, p.rel + to, tab_bytes, bar);
-            bulk_g2s(s_sel, p.sel + to, tab_bytes, bar);
-            bulk_g2s(s_w4, p.w4 + to * 4, 4 * tab_bytes, bar);
+            if (checked_ok(((size_t)g * p.N + c0 + nc) <= (size_t)p.n_groups * p.N &&
+                               smem_in(s_rel, tab_bytes) && smem_in(s_sel, tab_bytes) &&
+                               smem_in(s_w4, 4 * tab_bytes),
+                           p.err)) {
+                bulk_g2s(s_rel, p.rel + to, tab_bytes, bar);
+                bulk_g2s(s_sel, p.sel + to, tab_bytes, bar);
+                bulk_g2s(s_w4, p.w4 + to * 4, 4 * tab_bytes, bar);
+            } else {
+                mbar_complete_tx_local(bar, 6 * tab_bytes);
+            }
         }
         __syncthreads();  // the byte count is set before any copy can land
         for (int il = warp + 8 * lane; il < nc; il += kThreads) {
             const int i = c0 + il;
             // a multiple of 8 samples (32 bytes)
             const int x = p.padl + t0 + (il < kThreads ? x_first : gws[i]);
-            if (p.use_tma) {
+            if (!checked_ok(x >= 0 && x + WS <= p.row && smem_in(win + il * MBf, 2 * row_bytes),
+                            p.err)) {
+                mbar_complete_tx_local(bar, 2 * row_bytes);
+            } else if (p.use_tma) {
                 tma_load_3d(win + il * MBf, &p.tmap, x, i, 0, bar);
             } else {
                 const size_t o = (size_t)i * p.row + x;
@@ -865,6 +943,13 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
 #pragma unroll 4
         for (int il = 0; il < nc; ++il) {
             const uint32_t a = base + (uint32_t)s_sel[il * 8 + warp];
+            if constexpr (kChecked) {  // the lane's pairs inside microphone il's block
+                const uint32_t blk = smem_addr(win) + (uint32_t)(il * MBf * 4);
+                if (!checked_ok(a >= blk && a + 256 * (kPairs - 1) + 8 <= blk + MBf * 4 &&
+                                    smem_in(wq + 128 * il, 8),
+                                p.err))
+                    continue;
+            }
             const f32x2_t wf = lds_f32x2(wq + 128 * il);
 #pragma unroll
             for (int k = 0; k < kPairs; ++k)
@@ -876,16 +961,18 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
             float ve[NA];
 #pragma unroll
             for (int q = 0; q < NA; ++q) ve[q] = s_vext[q * 32];
-            for (int il = lane; il < nc; il += 32)
-                accumulate_v<ORDER>(ve, win[il * MBf + s_rel[il * 8 + warp] + kTile],
-                                    s_w4[(il * 8 + warp) * 4 + 2]);
+            for (int il = lane; il < nc; il += 32) {
+                const int o = s_rel[il * 8 + warp] + kTile;
+                if (checked_ok(o >= 0 && o < WS, p.err))
+                    accumulate_v<ORDER>(ve, win[il * MBf + o], s_w4[(il * 8 + warp) * 4 + 2]);
+            }
 #pragma unroll
             for (int q = 0; q < NA; ++q) s_vext[q * 32] = ve[q];
         }
     }
 
     const int dir = p.gdir[(size_t)g * 8 + warp];
-    if (dir < 0) return;
+    if (dir < 0 || !checked_ok(dir < p.M, p.err)) return;
     // sum[t] = S[t] - V[t] + V[t + 1].  For the pair (t, t+1): V[t+1] is the pair's
     // own second half; V[t+2] the next lane's first half (lane 31: lane 0's of
     // the next pair, or vext after the last).
@@ -1055,10 +1142,21 @@ __device__ __forceinline__ void beamform_x2_run(const Src &src) {
         const int t0 = tile * kTile;
         for (int il = lane; il < nc; il += 32) {
             const int i = cc + il;
-            bulk_g2s(w + il * q.window, chan + (size_t)i * q.row + q.padl + t0 + gws[i],
-                     row_bytes, &bar[bf]);
+            const int x = q.padl + t0 + gws[i];
+            if (checked_ok(x >= 0 && x + q.window <= q.row && smem_in(w + il * q.window, row_bytes),
+                           q.err))
+                bulk_g2s(w + il * q.window, chan + (size_t)i * q.row + x, row_bytes, &bar[bf]);
+            else
+                mbar_complete_tx_local(&bar[bf], row_bytes);
         }
-        if (lane == 0) bulk_g2s(rel, q.rel + ((size_t)g * q.N + cc) * 8, tab_bytes, &bar[bf]);
+        if (lane == 0) {
+            if (checked_ok(((size_t)g * q.N + cc + nc) <= (size_t)q.n_groups * q.N &&
+                               smem_in(rel, tab_bytes),
+                           q.err))
+                bulk_g2s(rel, q.rel + ((size_t)g * q.N + cc) * 8, tab_bytes, &bar[bf]);
+            else
+                mbar_complete_tx_local(&bar[bf], tab_bytes);
+        }
     };
 
     if (threadIdx.x == 0) {
@@ -1116,14 +1214,16 @@ __device__ __forceinline__ void beamform_x2_run(const Src &src) {
         // 4 455 us, 8 472 us)
 #pragma unroll 4
         for (int il = 0; il < nc; ++il) {
-            const float *r = w + il * WS + s_rel[il * 8 + warp] + lane;
+            const int off = s_rel[il * 8 + warp];
+            const float *r = w + il * WS + off + lane;
+            if (!checked_ok(off >= 0 && off + 31 + 64 * (kPairs - 1) + 32 < WS, p.err)) continue;
 #pragma unroll
             for (int k = 0; k < kPairs; ++k)
                 accumulate2<ORDER, false>(acc[k], f2_pack(r[64 * k], r[64 * k + 32]), 0ull);
         }
 
         const int dir = last_chunk ? p.gdir[(size_t)g * 8 + warp] : -1;
-        if (dir >= 0) {
+        if (dir >= 0 && checked_ok(dir < p.M, p.err)) {
             float *yrow = p.y + (size_t)dir * p.T;
             float *cfrow = p.cf ? p.cf + (size_t)dir * p.T : nullptr;
 #pragma unroll

@@ -294,8 +294,14 @@ __global__ void __launch_bounds__(kThreads, 2)
         mbar_arrive_expect_tx(&bar[ci & 1], (uint32_t)NP * nc * row_bytes + tab_bytes +
                                                 (LINEAR ? 4u * tab_bytes : 0u));
         const size_t to = ((size_t)g * p.N + c0) * 8;
-        bulk_g2s(rel, p.rel + to, tab_bytes, &bar[ci & 1]);
-        if (LINEAR) bulk_g2s(w4, p.w4 + to * 4, 4 * tab_bytes, &bar[ci & 1]);
+        if (checked_ok(((size_t)g * p.N + c0 + nc) <= (size_t)p.n_groups * p.N &&
+                           smem_in(rel, tab_bytes) && (!LINEAR || smem_in(w4, 4 * tab_bytes)),
+                       p.err)) {
+            bulk_g2s(rel, p.rel + to, tab_bytes, &bar[ci & 1]);
+            if (LINEAR) bulk_g2s(w4, p.w4 + to * 4, 4 * tab_bytes, &bar[ci & 1]);
+        } else {
+            mbar_complete_tx_local(&bar[ci & 1], tab_bytes * (LINEAR ? 5u : 1u));
+        }
     };
     auto window_start = [&](int ci) -> int {
         const int il = warp + 8 * lane;
@@ -310,7 +316,11 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int i = c0 + il;
             // a multiple of 8 samples (32 bytes)
             const int x = p.padl + t0 + (il < kThreads ? x_lane : gws[i]);
-            if (p.use_tma) {
+            if (!checked_ok(x >= 0 && x + WS <= p.row &&
+                                smem_in(win + il * MB, (uint32_t)NP * row_bytes),
+                            p.err)) {
+                mbar_complete_tx_local(&bar[ci & 1], (uint32_t)NP * row_bytes);
+            } else if (p.use_tma) {
                 tma_load_3d(win + il * MB, &p.tmap, x, i, 0, &bar[ci & 1]);
             } else {
                 const float *src = p.chan + (size_t)i * p.row + x;
@@ -369,7 +379,9 @@ __global__ void __launch_bounds__(kThreads, 2)
 
 #pragma unroll 4
         for (int il = 0; il < nc; ++il) {
-            const float *r = win + il * MB + s_rel[il * 8 + warp] + lane;
+            const int off = s_rel[il * 8 + warp];
+            const float *r = win + il * MB + off + lane;
+            if (!checked_ok(off >= 0 && off + 31 + 64 * (kPairs - 1) + 32 < WS, p.err)) continue;
             if constexpr (LINEAR) {
                 // {f, f}: the upper half of the entry {1-f, 1-f, f, f}
                 const f32x2_t wf =
@@ -398,6 +410,9 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
                 for (int q = 0; q < NA; ++q) ve[q] = s_vext[q * 32];
                 for (int il = lane; il < nc; il += 32) {
+                    if (!checked_ok(s_rel[il * 8 + warp] >= 0 && s_rel[il * 8 + warp] + kTile < WS,
+                                    p.err))
+                        continue;
                     const float *r = win + il * MB + s_rel[il * 8 + warp] + kTile;
                     float st[NP], sv[NMAX];
 #pragma unroll
@@ -423,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 
     const int dir = p.gdir[(size_t)g * 8 + warp];
-    if (dir < 0) return;
+    if (dir < 0 || !checked_ok((size_t)dir * p.T < p.img, p.err)) return;
     if constexpr (LINEAR) {
         // sum[t] = S[t] - V[t] + V[t + 1]: V[t + 1] for lane l's t0 + l is lane l + 1's
         // first half (lane 31: lane 0's second half); for t0 + 32 + l, lane

@@ -41,8 +41,18 @@ def test_exports_every_declared_symbol(lib):
     assert decl == set(dm.EXPORTS)
 
 
+def test_checked_build_exports_the_same_symbols():
+    """The host-checked variant (DMAS_CHECKED) links and exports the same ABI."""
+    path = dm_build.build(checked=True)
+    chk = ctypes.CDLL(path)
+    for name in sorted(declared_symbols()):
+        assert hasattr(chk, name), name
+    chk.dmas_status_string.restype = ctypes.c_char_p
+    assert b"host-checked" in chk.dmas_status_string(6)
+
+
 def test_status_strings_and_version(lib):
-    for code in range(6):
+    for code in range(7):
         assert lib.dmas_status_string(code)
     assert lib.dmas_status_string(99) == b"unknown status"
     assert lib.dmas_version() >= 100
