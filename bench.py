@@ -116,9 +116,9 @@ WORKLOADS = {
 # interpolated-delay pair kernel on the hemisphere frame), valid only while
 # the kernel source is the one that was measured; otherwise the line's
 # "traffic" is null and "traffic_note" says why.
-TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "ng": "f32", "kernel_src_sha256_16": "dbe3b86f2c72cf5f",
+TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "ng": "cf32", "kernel_src_sha256_16": "9a0b58816dd7eb46",
                   # ncu dram__bytes_read.sum + dram__bytes_write.sum (bytes)
-                  "bytes": 5_880_576 + 74_890_240}
+                  "bytes": 5_882_368 + 75_608_320}
 
 
 def beam_traffic(workload: str, ng: str = "cf32"):
@@ -130,8 +130,9 @@ def beam_traffic(workload: str, ng: str = "cf32"):
             and sha == TRAFFIC_RECORD["kernel_src_sha256_16"]):
         return TRAFFIC_RECORD["bytes"], "one ncu capture of this kernel on this workload"
     if workload != TRAFFIC_RECORD["workload"] or ng != TRAFFIC_RECORD.get("ng", "cf32"):
-        return None, ("no DRAM capture recorded for this workload; the recorded one is "
-                      f"{TRAFFIC_RECORD['workload']}")
+        return None, ("no DRAM capture recorded for this workload and Newton-Girard form; "
+                      f"the recorded one is {TRAFFIC_RECORD['workload']} with "
+                      f"{TRAFFIC_RECORD.get('ng', 'cf32')}")
     return None, "the kernel source changed since its DRAM traffic was captured"
 
 
