@@ -749,7 +749,7 @@ def run_sweep(args) -> None:
 # ---------------------------------------------------------------------------
 # image SNR against microphone SNR (the paper's Sec. III-A experiment, Table I)
 # ---------------------------------------------------------------------------
-IMAGE_SNR_MIC_DB = [-40.0, -30.0, -20.0, -10.0, 0.0, 10.0]
+IMAGE_SNR_MIC_DB = [-40.0, -30.0, -20.0, -10.0, 0.0, 10.0, 20.0, 40.0]
 
 
 def run_image_snr(args) -> None:
@@ -770,7 +770,8 @@ def run_image_snr(args) -> None:
         for n in (1, 2, 3, 4, 5):
             for cf in (False, True):
                 plan = dm.Plan(mic_xyz=sc.mic_xyz, dir_azel=sc.dir_azel, n_samples=sc.n_samples,
-                               fs=sc.fs, c=sc.c, order=n, delay_mode=dm.LINEAR, cf=cf)
+                               fs=sc.fs, c=sc.c, order=n, delay_mode=dm.LINEAR, cf=cf,
+                               ng_prec=NG_PREC[args.ng](dm))
                 img = plan(x).cpu().numpy()
                 plan.check()
                 plan.close()
@@ -794,7 +795,8 @@ def run_image_snr(args) -> None:
         "config": {"workload": "image_snr", "description":
                    "one reflector at broadside, 1 m, echo amplitude 1 at the 32 mics "
                    "(12 cm disc), white noise eta = 10^(-SNR/20), 181 azimuths x 2048 "
-                   "samples, linear delays, 181-tap envelope; image normalised to max 1, "
+                   "samples, linear delays, 181-tap envelope, Newton-Girard " + args.ng +
+                   "; image normalised to max 1, "
                    "SNR_image = 20 log10(1 / mean off-target level), target window "
                    "+-10 deg x +-0.15 m"},
         "table": rows,
