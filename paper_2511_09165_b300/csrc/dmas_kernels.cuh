@@ -1222,6 +1222,23 @@ __device__ __forceinline__ void beamform_x2_run(const Src &src) {
                 accumulate2<ORDER, false>(acc[k], f2_pack(r[64 * k], r[64 * k + 32]), 0ull);
         }
 
+        // hand the buffer back (the epilogue below reads registers only); the
+        // last warp out stages the stage after next
+        __syncwarp();
+        int before = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            before = atomicAdd(&done_cnt[bf], 1);
+            __threadfence_block();
+        }
+        __syncwarp();
+        before = __shfl_sync(0xffffffffu, before, 0);
+        if (before == kWarps - 1) {
+            if (lane == 0) done_cnt[bf] = 0;
+            __threadfence_block();
+            fence_proxy_async_smem();  // the warps' reads before the copy's writes
+            stage_next(bf, stage + 2, false);
+        }
         const int dir = last_chunk ? p.gdir[(size_t)g * 8 + warp] : -1;
         if (dir >= 0 && checked_ok(dir < p.M, p.err)) {
             float *yrow = p.y + (size_t)dir * p.T;
@@ -1245,22 +1262,6 @@ __device__ __forceinline__ void beamform_x2_run(const Src &src) {
                     if (cfrow) cfrow[t] = cf;
                 }
             }
-        }
-        // hand the buffer back; the last warp out stages the stage after next
-        __syncwarp();
-        int before = 0;
-        if (lane == 0) {
-            __threadfence_block();
-            before = atomicAdd(&done_cnt[bf], 1);
-            __threadfence_block();
-        }
-        __syncwarp();
-        before = __shfl_sync(0xffffffffu, before, 0);
-        if (before == kWarps - 1) {
-            if (lane == 0) done_cnt[bf] = 0;
-            __threadfence_block();
-            fence_proxy_async_smem();  // the warps' reads before the copy's writes
-            stage_next(bf, stage + 2, false);
         }
         if (*abort_flag) break;
     }
