@@ -71,27 +71,62 @@ FAST_COST = 1.3e9
 BULK_ENV_TILE_CAP = 16
 
 
+# Device-to-host copies of big images go out in pieces of this many bytes, so
+# the copy engine can interleave the small frames' copies (issued on other
+# streams) between them instead of queueing them behind a whole gigabyte.
+COPY_PIECE_BYTES = 32 << 20
+
+
+def _copy_in_pieces(dst, src) -> None:
+    """dst.copy_(src) (non-blocking) in COPY_PIECE_BYTES pieces."""
+    d, s = dst.view(-1), src.view(-1)
+    step = max(1, COPY_PIECE_BYTES // 4)
+    for a in range(0, s.numel(), step):
+        d[a:a + step].copy_(s[a:a + step], non_blocking=True)
+
+
 class PinnedPool:
     """Page-locked host buffers reused by shape: allocating pinned memory
     takes milliseconds per gigabyte, so copies back to the host draw on this
-    pool instead of allocating per frame."""
+    pool instead of allocating per frame.  When every buffer of a shape is in
+    use, get() waits (up to `wait_s`) for one to come back before it
+    allocates another."""
 
-    def __init__(self):
+    def __init__(self, wait_s: float = 2.0):
         import torch
         self.torch = torch
+        self.wait_s = float(wait_s)
         self._free: dict = collections.defaultdict(list)
-        self._mu = threading.Lock()
+        self._owned: dict = collections.defaultdict(int)
+        self._cv = threading.Condition()
+
+    def _alloc(self, shape):
+        t = self.torch.empty(shape, dtype=self.torch.float32, pin_memory=True)
+        with self._cv:
+            self._owned[shape] += 1
+        return t
 
     def get(self, shape):
-        with self._mu:
-            lst = self._free.get(tuple(shape))
-            if lst:
-                return lst.pop()
-        return self.torch.empty(tuple(shape), dtype=self.torch.float32, pin_memory=True)
+        shape = tuple(shape)
+        with self._cv:
+            if not self._free[shape] and self._owned[shape] > 0:
+                self._cv.wait_for(lambda: bool(self._free[shape]), timeout=self.wait_s)
+            if self._free[shape]:
+                return self._free[shape].pop()
+        return self._alloc(shape)
 
     def put(self, t) -> None:
-        with self._mu:
+        with self._cv:
             self._free[tuple(t.shape)].append(t)
+            self._cv.notify_all()
+
+    def reserve(self, shape, count: int) -> None:
+        """Hold at least `count` buffers of this shape (allocated now)."""
+        shape = tuple(shape)
+        with self._cv:
+            have = self._owned[shape]
+        for _ in range(max(0, count - have)):
+            self.put(self._alloc(shape))
 
 
 class _Lane:
@@ -158,6 +193,14 @@ class Server:
         self.batches = 0
         self.completed: list[Request] = []
         self.pinned = pinned if pinned is not None else (PinnedPool() if copy_back else None)
+        if copy_back:
+            # page-locking takes milliseconds per gigabyte: hold enough host
+            # images now for the frames that can be in flight at once (a big
+            # frame per bulk stream, small ones in the fast lane's batches)
+            for sn in self.sensors:
+                small = sn.cost <= self.fast_cost
+                want = 4 if small else len(self.bulk.streams) + 1
+                self.pinned.reserve(sn.image_shape, want)
         # big frames' envelopes retire their CTAs every few tiles, so the fast
         # lane's kernels reach the SMs without waiting for a whole envelope
         for sn in self.sensors:
@@ -269,7 +312,7 @@ class Server:
             if self.copy_back:
                 hosts = [self.pinned.get(im.shape) for im in images]
                 for h, im in zip(hosts, images):
-                    h.copy_(im, non_blocking=True)
+                    _copy_in_pieces(h, im)
             ev = torch.cuda.Event()
             ev.record(stream)
         self.batches += 1
