@@ -548,6 +548,81 @@ def run_ours(args, wl, scene) -> None:
 
 
 # ---------------------------------------------------------------------------
+# one frame split by directions across the ranks (strong scaling)
+# ---------------------------------------------------------------------------
+def run_split(args, wl, scene) -> None:
+    """Each rank beamforms a contiguous slice of the direction grid of the same
+    frame: per step the frame is broadcast from rank 0 (NCCL), every rank runs
+    its slice's plan, and the slices are gathered to rank 0 into the image."""
+    import torch
+    import paper_2511_09165_b300 as dm
+    from paper_2511_09165_b300.split import SplitBeamformer, direction_slices, plan_rows, \
+        slice_grid
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    td = dist_init(world, "nccl")
+    linear = wl["mode"] == "linear"
+    M, T, N = scene.n_dirs, scene.n_samples, scene.n_mics
+    lo, hi = direction_slices(M, world)[rank]
+    azel, unit, _ = slice_grid(scene.dir_azel, scene.dir_unit, None, lo, hi)
+    plan = dm.Plan(mic_xyz=scene.mic_xyz, dir_azel=azel, dir_unit=unit, n_samples=T,
+                   fs=scene.fs, c=scene.c, order=wl["order"],
+                   delay_mode=dm.LINEAR if linear else dm.ROUND, cf=wl.get("cf", True),
+                   ng_prec=NG_PREC[args.ng](dm)) if hi > lo else None
+    sb = SplitBeamformer(rank, world, M, plan_rows(plan) if plan else None, device=dev)
+    frame = torch.from_numpy(scene.frame).to(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
+
+    def step():
+        if world > 1:
+            return sb(frame, src=0, dst=0)
+        return plan(frame)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    dist_barrier(td)
+    torch.cuda.synchronize(dev)
+    wall0 = time.time()
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        dist_barrier(td)
+        t0 = time.perf_counter()
+        step()
+        torch.cuda.synchronize(dev)
+        times.append(time.perf_counter() - t0)
+    dist_barrier(td)
+    wall1 = time.time()
+    clocks.stop()
+    total = dist_max(td, sum(times), dev)
+    if plan is not None:
+        plan.check()
+        plan.close()
+    if rank != 0:
+        return
+    ms = 1e3 * total / args.steps
+    print(json.dumps({
+        "metric": METRIC, "value": M * T / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "description": wl["text"], "n_mics": N,
+                   "n_dirs": M, "n_samples": T, "ng": args.ng,
+                   "parallelism": f"directions split x{world} (frame broadcast, rows gathered "
+                                  "to rank 0, both inside the timed step)",
+                   "l2": "flushed (256 MB write) before every step",
+                   "timing": "host wall clock around each synchronised step, max over ranks"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": clocks.summary(wall0, wall1),
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
 # serving: Poisson arrivals from 16 mixed sensors
 # ---------------------------------------------------------------------------
 def serving_measure(rates, seconds, rank=0, budget_gb=48, bulk_streams=3,
@@ -953,6 +1028,9 @@ def main() -> None:
     ap.add_argument("--serve-env-cap", type=int, default=16,
                     help="tensor-core envelope tiles per CTA for the bulk lane (0: no cap)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--split", action="store_true",
+                    help="under torchrun: one frame split by directions across the ranks "
+                         "(strong scaling) instead of one frame per rank")
     ap.add_argument("--ng", choices=sorted(NG_PREC), default="cf32",
                     help="Newton-Girard arithmetic: compensated FP32 (default), FP64, plain FP32")
     ap.add_argument("--serve-leg-seconds", type=float, default=2.0,
@@ -992,6 +1070,8 @@ def main() -> None:
     scene = wl["scene"]()
     if args.impl == "reference":
         run_reference(args, wl, scene)
+    elif args.split:
+        run_split(args, wl, scene)
     else:
         run_ours(args, wl, scene)
 
