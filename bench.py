@@ -116,9 +116,9 @@ WORKLOADS = {
 # interpolated-delay pair kernel on the hemisphere frame), valid only while
 # the kernel source is the one that was measured; otherwise the line's
 # "traffic" is null and "traffic_note" says why.
-TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "ng": "cf32", "kernel_src_sha256_16": "9a0b58816dd7eb46",
+TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "ng": "cf32", "kernel_src_sha256_16": "8c62741118ec0b31",
                   # ncu dram__bytes_read.sum + dram__bytes_write.sum (bytes)
-                  "bytes": 5_882_368 + 75_608_320}
+                  "bytes": 5_878_528 + 75_590_912}
 
 
 def beam_traffic(workload: str, ng: str = "cf32"):
