@@ -102,7 +102,7 @@ struct dmas_plan {
     size_t chan_bytes = 0, ybuf_bytes = 0, table_bytes = 0;
     float *d_io_frame = nullptr, *d_io_image = nullptr;  // dmas_beamform_host staging
     size_t smem_beam = 0, smem_env = 0;
-    float *d_taps_tc = nullptr;       // envelope taps as TF32 hi/lo phase arrays [2][4][Z]
+    float *d_taps_tc = nullptr;       // envelope tap operand, TF32 hi/lo (tc_tap_arrays)
     float *d_taps = nullptr;          // envelope taps [L] (CUDA-core FIR for small frames)
     float *d_mf = nullptr;            // matched filter: the emitted signal [mf_len], or null
     size_t mf_bytes = 0;              // matched-filtered frame in the scratch (0: no filter)
@@ -216,24 +216,19 @@ size_t beam_smem_bytes(const HostPlan &hp) {
     return 128 + win + tabs;
 }
 
-// Dynamic shared memory the tensor-core envelope may take (its opt-in below;
-// the kernel also has ~1 KB of static shared memory).
-constexpr size_t kEnvSmemMax = 222 * 1024;
-
 // Shared-memory stages of the tensor-core envelope: as many as fit beside the
-// taps (long filters have long tap arrays), at most kTcStages.
+// tap operand (kEnvSmemMax, its opt-in below), at most kTcStages.
 int env_tc_stages(const HostPlan &hp) {
     if (hp.L == 0) return 0;
-    const size_t taps = ((size_t)8 * tc_Z((hp.L - 1) / 2) * 4 + 1023) & ~(size_t)1023;
-    const size_t room = kEnvSmemMax - 1024 - taps;
-    return (int)std::min<size_t>((size_t)kTcStages, room / kTcStageBytes);
+    const int taps = tc_align1k(tc_tap_bytes((hp.L - 1) / 2));
+    const int room = kEnvSmemMax - 1024 - taps;
+    return std::min(kTcStages, room / kTcStageBytes);
 }
 
 size_t env_smem_bytes(const HostPlan &hp) {
     if (hp.L == 0) return 0;
-    const int Z = tc_Z((hp.L - 1) / 2);
     // + 1 KB: the kernel aligns its stages to 1024 bytes (the 128-byte swizzle period)
-    return 1024 + (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023) +
+    return 1024 + (size_t)tc_align1k(tc_tap_bytes((hp.L - 1) / 2)) +
            (size_t)env_tc_stages(hp) * kTcStageBytes;
 }
 
@@ -247,12 +242,32 @@ float tf32_host(float x) {
     return y;
 }
 
-// Phase arrays of the tensor-core envelope: copy r holds, at index z, the tap
-// that multiplies |y[t0 - HA + u]| for output 4q + r where z = u + 4 q' and
-// q' = Nq - 1 - q:  g~[z - 4 (Nq - 1) - r],  g~[w] = h[2H - (w - (HA - H))]
-// (e[t] = sum_k h[k] |y[t - k]|), split into TF32 hi and lo parts.
+// The tensor-core envelope's tap operand, split into TF32 hi and lo parts.
+// g~[w] = h[2H - (w - (HA - H))] (e[t] = sum_k h[k] |y[t - k]|) is the tap
+// that multiplies |y[t0 - HA + u]| for output t0 + j at w = u - j.
+//  Toeplitz form: T[u'][n] = g~[u' - n] (u' = 0..KB-1, n = 0..31) in the
+//  canonical K-major layout, float index (n / 8) 8 KB + (u' / 4) 32 +
+//  (n % 8) 4 + u' % 4; hi at 0, lo at 32 KB.
+//  Phase form: copy r holds, at index z, the tap for output 4q + r where
+//  z = u + 4 q' and q' = Nq - 1 - q:  g~[z - 4 (Nq - 1) - r].
 std::vector<float> tc_tap_arrays(const HostPlan &hp) {
     const int H = (hp.L - 1) / 2, HA = tc_halo(H), Z = tc_Z(H);
+    if (tc_toeplitz(H)) {
+        const int KB = tc_KB(H);
+        std::vector<float> out((size_t)64 * KB, 0.0f);
+        for (int n = 0; n < 32; ++n) {
+            for (int u = 0; u < KB; ++u) {
+                const int x = u - n - (HA - H);
+                if (x < 0 || x > 2 * H) continue;
+                const float gv = hp.taps[2 * H - x];
+                const float hi = tf32_host(gv);
+                const size_t i = (size_t)(n / 8) * 8 * KB + (size_t)(u / 4) * 32 + (n % 8) * 4 + u % 4;
+                out[i] = hi;
+                out[(size_t)32 * KB + i] = gv - hi;
+            }
+        }
+        return out;
+    }
     std::vector<float> out((size_t)8 * Z, 0.0f);
     for (int r = 0; r < 4; ++r) {
         for (int z = 0; z < Z; ++z) {
@@ -278,18 +293,25 @@ unsigned env_grid(unsigned tiles, int num_sms, int cap) {
     return g;
 }
 
-cudaError_t launch_env_tc(const EnvTcParams &ep, unsigned grid, size_t smem, cudaStream_t s) {
+template <bool TOEP>
+cudaError_t launch_env_tc_form(const EnvTcParams &ep, unsigned grid, size_t smem,
+                               cudaStream_t s) {
     static std::once_flag once;
     static cudaError_t attr = cudaSuccess;
     std::call_once(once, [&] {
         // the kernel also has ~1 KB of static shared memory (barriers, TMEM slot)
-        attr = cudaFuncSetAttribute(envelope_tc_kernel,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kEnvSmemMax);
+        attr = cudaFuncSetAttribute(envelope_tc_kernel<TOEP>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, kEnvSmemMax);
     });
     if (attr != cudaSuccess) return attr;
-    envelope_tc_kernel<<<grid, kTcThreadsWS, smem, s>>>(ep);
+    envelope_tc_kernel<TOEP><<<grid, kTcThreadsWS, smem, s>>>(ep);
     return cudaGetLastError();
+}
+
+// the tap operand's form is a function of the filter length alone
+cudaError_t launch_env_tc(const EnvTcParams &ep, unsigned grid, size_t smem, cudaStream_t s) {
+    return tc_toeplitz(ep.H) ? launch_env_tc_form<true>(ep, grid, smem, s)
+                             : launch_env_tc_form<false>(ep, grid, smem, s);
 }
 
 // cuTensorMapEncodeTiled, looked up once through the runtime.

@@ -7,16 +7,28 @@
 //   B[u][j] = g~[u - j]                        (a band: the taps slid by j)
 // where HA = H rounded up to 4 (so every load starts 16-byte aligned) and g~ is
 // g shifted by HA - H and zero outside the taps.  A is K-major (rows of y are
-// contiguous in t).  B is K-major too, but its rows are the tap vector slid by
-// one sample each, and a shared-memory matrix descriptor can only step rows by
-// 16 bytes (4 samples): so the J outputs are taken as 4 phases r (j = 4q + r),
-// and phase r's J/4 columns, in reverse order of q, are rows of a tap array
-// that step by exactly 16 bytes -- one descriptor over one array per phase, no
-// Toeplitz matrix materialised.  Phase r accumulates into TMEM columns
-// [r J/4, (r + 1) J/4) of its accumulator.  A shorter tile wastes less of K on
-// the band's zeros (each output needs 2H + 1 of its tile's K = J + 2 HA):
-// measured on B300, J = 128 is fastest (J = 256: 131 us, 192: 120 us, 128:
-// 110 us, 64: 161 us for a 2048 x 16384 frame).
+// contiguous in t).  B is K-major too.  The J outputs are issued as four MMAs
+// of N = 32 columns each, in one of two forms:
+//
+//  * Toeplitz blocks (filters up to ~340 taps): block b covers the consecutive
+//    outputs j = 32 b + n (n = 0..31), whose band is only the 32 + 2 HA rows
+//    u = 32 b + u' (u' = 0..31 + 2 HA) of B, where B[u][j] = T[u'][n] =
+//    g~[u' - n] -- the same matrix T for every block.  T (hi and lo parts) is
+//    stored once per CTA in the canonical K-major layout (core matrices of
+//    8 columns x 4 rows, 128 bytes; K-adjacent core matrices 128 bytes apart,
+//    8-column groups 32 (32 + 2 HA) bytes apart), so block b's MMA at tile
+//    k-step s reads T from row 8 s - 32 b.  Each block multiplies 32 + 2 HA
+//    rows of K instead of the tile's whole J + 2 HA: for 181 taps 216 of 312
+//    (27 of 39 k-steps), and its columns are outputs in order.
+//  * Phases (longer filters, whose T does not fit beside the stages): a
+//    shared-memory matrix descriptor can only step rows by 16 bytes (4 samples),
+//    so the outputs are taken as 4 phases r (j = 4q + r), and phase r's J/4
+//    columns, in reverse order of q, are rows of a tap array that step by
+//    exactly 16 bytes -- one descriptor over one array per phase, no matrix
+//    materialised, every MMA over the tile's whole K.  Phase r accumulates into
+//    TMEM columns [r J/4, (r + 1) J/4).  Measured on B300 in this form, J = 128
+//    is the fastest tile (J = 256: 131 us, 192: 120 us, 128: 110 us, 64: 161 us
+//    for a 2048 x 16384 frame).
 //
 // FP32 accuracy from TF32 products: A = A_hi + A_lo and g = g_hi + g_lo with
 // the _hi parts rounded to TF32; each k-step issues A_hi.B_hi + A_hi.B_lo +
@@ -40,8 +52,8 @@
 // kTcStages: as many as fit beside the taps); 4 split warps
 // (one row per thread, the warp's TMEM lane quarter) read |y| rounded to TF32
 // and the remainder and store them (tcgen05.st) into one of two A stages in
-// TMEM (hi, lo: 2 x 64 columns); four MMA warps issue the k-block's 8 k-steps
-// x (one phase each) x 3 MMAs into one of two accumulators (4 x J/4 columns)
+// TMEM (hi, lo: 2 x 64 columns); four MMA warps (one block or phase each)
+// issue the k-block's k-steps x 3 MMAs into one of two accumulators (J columns)
 // and commit them to the A stage's and, after a tile's last k-block, the
 // accumulator's mbarrier; 4 epilogue warps read their row of a finished
 // accumulator (TMEM lane = row) and store 8 consecutive outputs (one 32-byte
@@ -63,10 +75,29 @@ constexpr int kTcAtomK = 32;         // samples per 128-byte swizzle atom column
 constexpr int kTcAtomBytes = kTcRows * 128;  // one atom column of 128 rows
 constexpr int kTcBufBytes = kTcRows * kTcKB * 4;  // one of A_hi / A_lo for a k-block
 
+constexpr int kTcStageBytes = kTcBufBytes;  // |y| of one k-block, FP32
+constexpr int kTcStages = 6;  // most shared-memory stages (fewer for long filters)
+// dynamic shared memory the kernel may take (it also has ~1 KB of static)
+constexpr int kEnvSmemMax = 222 * 1024;
+
 __host__ __device__ inline int tc_halo(int H) { return (H + 3) & ~3; }
 __host__ __device__ inline int tc_K(int H) { return kTcJ + 2 * tc_halo(H); }
 // length of one phase tap array (floats), a multiple of 8
 __host__ __device__ inline int tc_Z(int H) { return (tc_K(H) + 4 * (kTcNq - 1) + 7) & ~7; }
+// rows of the Toeplitz block matrix T (the K one block of 32 outputs spans)
+__host__ __device__ inline int tc_KB(int H) { return kTcNq + 2 * tc_halo(H); }
+// bytes of the tap operand in shared memory: T hi and lo, 32 columns x KB
+// rows of 4 bytes each; or the 8 phase arrays
+__host__ __device__ inline int tc_toep_bytes(int H) { return 2 * 32 * 4 * tc_KB(H); }
+__host__ __device__ inline int tc_phase_bytes(int H) { return 8 * 4 * tc_Z(H); }
+__host__ __device__ inline int tc_align1k(int b) { return (b + 1023) & ~1023; }
+// The Toeplitz form whenever T leaves room for 4 stages of |y|
+__host__ __device__ inline bool tc_toeplitz(int H) {
+    return kEnvSmemMax - 1024 - tc_align1k(tc_toep_bytes(H)) >= 4 * kTcStageBytes;
+}
+__host__ __device__ inline int tc_tap_bytes(int H) {
+    return tc_toeplitz(H) ? tc_toep_bytes(H) : tc_phase_bytes(H);
+}
 
 struct EnvTcJob {
     // 2-D view of y for the TMA engine when T % 4 == 0: dims (T, M), box
@@ -87,7 +118,9 @@ struct EnvTcParams {
     unsigned total_tiles;
     int H;
     int n_stages;       // shared-memory stages of |y|, 2..kTcStages
-    const float *taps;  // [2][4][Z]: hi then lo, phase r = 0..3 (device)
+    // the tap operand, tc_tap_bytes(H) bytes (device): T hi then T lo in the
+    // Toeplitz form's core-matrix layout, else the phase arrays [2][4][Z]
+    const float *taps;
     unsigned *err;
     EnvTcJob job[kBatchMax];
 };
@@ -202,16 +235,21 @@ __device__ __forceinline__ TcTile tc_tile(const EnvTcParams &p, unsigned tile) {
 // (TMEM lane quarters), 8 producer, 9.. MMA issue (lane 0 of each; warp 9 also
 // allocates TMEM).  A tcgen05.mma costs its issuing thread tens of cycles, so
 // the phases are spread over kTcMmaWarps issuing warps.
-constexpr int kTcStages = 6;  // most shared-memory stages (fewer for long filters)
 constexpr int kTcMmaWarps = 4;
 constexpr int kTcPhasesPerWarp = 4 / kTcMmaWarps;
 constexpr int kTcWarps = 9 + kTcMmaWarps;
 constexpr int kTcThreadsWS = kTcWarps * 32;
-constexpr int kTcStageBytes = kTcBufBytes;  // |y| of one k-block, FP32
 constexpr uint32_t kTcAccCols = 4 * kTcNq;  // one accumulator (4 phases)
 constexpr uint32_t kTcACol0 = 2 * kTcAccCols;  // first TMEM column of the A stages
 constexpr uint32_t kTcACols = 2 * kTcKB;    // one A stage: hi then lo
 constexpr int kTcAStages = (512 - (int)kTcACol0) / (int)kTcACols;  // A stages in TMEM
+// Toeplitz form: one accumulator (J columns, block b at 32 b) with a full and
+// an empty barrier per block, so a block's MMA warp starts the next tile as
+// soon as the epilogue has read that block; the freed columns hold a third A
+// stage, which lets the MMA warps drift apart by up to three k-blocks (their
+// k-steps per k-block differ: each block's band covers a different part of K)
+constexpr int kTcAStagesT = (512 - kTcJ) / (int)kTcACols;
+constexpr int kTcAStagesMax = kTcAStagesT > kTcAStages ? kTcAStagesT : kTcAStages;
 
 __device__ __forceinline__ void tc_mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b,
                                           uint32_t idesc, uint32_t accumulate) {
@@ -236,11 +274,16 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) 
         : "memory");
 }
 
+template <bool TOEP>
 __global__ void __launch_bounds__(kTcThreadsWS, 1)
     envelope_tc_kernel(const __grid_constant__ EnvTcParams p) {
     extern __shared__ __align__(128) unsigned char env_smem[];
     __shared__ uint64_t full[kTcStages], empty[kTcStages];
-    __shared__ uint64_t a_full[kTcAStages], a_empty[kTcAStages], acc_full[2], acc_empty[2];
+    __shared__ uint64_t a_full[kTcAStagesMax], a_empty[kTcAStagesMax], acc_full[4], acc_empty[4];
+    // A stages and their first TMEM column, accumulator barriers
+    constexpr int nA = TOEP ? kTcAStagesT : kTcAStages;
+    constexpr uint32_t acol0 = TOEP ? (uint32_t)kTcJ : kTcACol0;
+    constexpr int n_acc_bars = TOEP ? kTcMmaWarps : 2;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -248,13 +291,14 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
     const int n_kb = (K + kTcKB - 1) / kTcKB;
     // the dynamic window starts 1024-aligned (its size has 1 KB to spare)
     unsigned char *base = env_smem + ((1024u - (smem_addr(env_smem) & 1023u)) & 1023u);
-    float *s_taps = reinterpret_cast<float *>(base);                               // [2][4][Z]
-    unsigned char *stages = base + (((size_t)8 * Z * 4 + 1023) & ~(size_t)1023);  // [S]
+    const int tap_bytes = TOEP ? tc_toep_bytes(H) : tc_phase_bytes(H);
+    float *s_taps = reinterpret_cast<float *>(base);  // T hi, T lo; or [2][4][Z]
+    unsigned char *stages = base + tc_align1k(tap_bytes);  // [S]
     // host-checked build: the taps and the stages inside the dynamic shared
     // memory (otherwise the CTA does no tile)
     const bool layout_ok =
         checked_ok(p.n_stages >= 2 && p.n_stages <= kTcStages &&
-                       smem_in(s_taps, (uint32_t)(8 * Z * 4)) &&
+                       smem_in(s_taps, (uint32_t)tap_bytes) &&
                        smem_in(stages, (uint32_t)p.n_stages * (uint32_t)kTcStageBytes),
                    p.err);
     const unsigned n_tiles = (layout_ok && blockIdx.x < p.total_tiles)
@@ -262,7 +306,8 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                                  : 0;
 
     if (layout_ok)
-        for (int i = tid; i < 8 * Z; i += kTcThreadsWS) s_taps[i] = p.taps[i];
+        for (int i = tid; i < tap_bytes / 16; i += kTcThreadsWS)
+            reinterpret_cast<float4 *>(s_taps)[i] = reinterpret_cast<const float4 *>(p.taps)[i];
     if (warp == 9) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_addr(&tmem_slot)),
@@ -275,12 +320,13 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
             mbar_init(&full[s], 1);     // producer lane 0 (+ bytes or cp.async arrivals)
             mbar_init(&empty[s], 128);  // split threads, once they have read the stage
         }
-        for (int a = 0; a < kTcAStages; ++a) {
+        for (int a = 0; a < nA; ++a) {
             mbar_init(&a_full[a], 128);          // split threads, after their TMEM stores
             mbar_init(&a_empty[a], kTcMmaWarps); // MMA commits of the k-block that read it
         }
-        for (int a = 0; a < 2; ++a) {
-            mbar_init(&acc_full[a], kTcMmaWarps);  // MMA commits after a tile's last k-block
+        for (int a = 0; a < n_acc_bars; ++a) {
+            // MMA commits after a tile's last k-block (Toeplitz: the block's own warp)
+            mbar_init(&acc_full[a], TOEP ? 1 : kTcMmaWarps);
             mbar_init(&acc_empty[a], 128);         // epilogue threads
         }
         abort_flag = 0;
@@ -354,14 +400,14 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
         for (unsigned i = 0; i < n_tiles; ++i) {
             for (int kb = 0; kb < n_kb; ++kb, ++g) {
                 const int s = (int)(g % (unsigned)p.n_stages);
-                const int t = (int)(g % (unsigned)kTcAStages);
-                const unsigned use = g / (unsigned)kTcAStages;
+                const int t = (int)(g % (unsigned)nA);
+                const unsigned use = g / (unsigned)nA;
                 if (!wait(&full[s], (g / (unsigned)p.n_stages) & 1u)) goto done;
-                // the MMAs of the k-block kTcAStages back have finished reading A stage t
+                // the MMAs of the k-block nA back have finished reading A stage t
                 if (use > 0 && !wait(&a_empty[t], (use - 1) & 1u)) goto done;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const float *ay = reinterpret_cast<const float *>(stages + (size_t)s * kTcStageBytes);
-                const uint32_t acol = kTcACol0 + (uint32_t)t * kTcACols;
+                const uint32_t acol = acol0 + (uint32_t)t * kTcACols;
 #pragma unroll
                 for (int half = 0; half < kTcKB / 32; ++half) {
                     float h[32], l[32];
@@ -393,59 +439,150 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
         const int r0 = (warp - 9) * kTcPhasesPerWarp;  // this warp's phases
         const uint32_t idesc = tc_idesc(kTcRows, kTcNq);
         const uint32_t taps_base = smem_addr(s_taps);
-        unsigned g = 0;
-        for (unsigned i = 0; i < n_tiles; ++i) {
-            const int a = (int)(i & 1u);
-            // the epilogue must have drained this accumulator (tile i - 2)
-            if (i >= 2 && !wait(&acc_empty[a], ((i >> 1) - 1) & 1u)) goto done;
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t dacc = tmem + (uint32_t)a * kTcAccCols;
-            for (int kb = 0; kb < n_kb; ++kb, ++g) {
-                const int t = (int)(g % (unsigned)kTcAStages);
-                if (!wait(&a_full[t], (g / (unsigned)kTcAStages) & 1u)) goto done;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                if (lane == 0) {
-                    const int u0 = kb * kTcKB;
-                    const int nks = min(kTcKB, K - u0) / 8;
-                    // A: 8 TMEM columns per k-step (hi, then lo 64 columns on);
-                    // B: the phase's tap array, 8 samples (32 B) per k-step, in
-                    // 16-byte descriptor units
-                    const uint32_t a_hi = tmem + kTcACol0 + (uint32_t)t * kTcACols;
-                    uint64_t dbh0[kTcPhasesPerWarp], dbl0[kTcPhasesPerWarp];
+        // Toeplitz form: this warp's block b = r0 of 32 outputs is active for
+        // the tile's k-steps [4 b, 4 b + KB / 8); T hi at taps_base, T lo
+        // 128 KB bytes on; 8-column groups 32 KB bytes apart
+        const int KB = tc_KB(H);
+        const int s_lo = 4 * r0, s_hi = s_lo + KB / 8;
+        const uint32_t t_sbo = 32u * (uint32_t)KB;
+        const uint32_t t_lo = taps_base + 128u * (uint32_t)KB;
+        if constexpr (TOEP) {
+            const int kb_first = s_lo / (kTcKB / 8), kb_last = (s_hi - 1) / (kTcKB / 8);
+            const uint32_t d = tmem + (uint32_t)(r0 * kTcNq);  // block r0 of the accumulator
+            unsigned g = 0;
+            for (unsigned i = 0; i < n_tiles; ++i) {
+                for (int kb = 0; kb < n_kb; ++kb, ++g) {
+                    const int t = (int)(g % (unsigned)nA);
+                    if (!wait(&a_full[t], (g / (unsigned)nA) & 1u)) goto done;
+                    // the epilogue must have read this block of the previous tile
+                    if (kb == kb_first && i >= 1 && !wait(&acc_empty[r0], (i - 1) & 1u))
+                        goto done;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (lane == 0) {
+                        const uint32_t a_hi = tmem + acol0 + (uint32_t)t * kTcACols;
 #pragma unroll
-                    for (int rr = 0; rr < kTcPhasesPerWarp; ++rr) {
-                        const int r = r0 + rr;
-                        dbh0[rr] = smem_desc(taps_base + (uint32_t)(r * Z * 4 + u0 * 4), 16, 128);
-                        dbl0[rr] = smem_desc(taps_base + (uint32_t)((4 + r) * Z * 4 + u0 * 4), 16, 128);
-                    }
-                    const uint32_t acc0 = kb > 0 ? 1u : 0u;
-#pragma unroll
-                    for (int ks = 0; ks < kTcKB / 8; ++ks) {
-                        if (ks < nks) {
-                            const uint32_t ah = a_hi + (uint32_t)(8 * ks);
-                            const uint32_t al = ah + (uint32_t)kTcKB;
-#pragma unroll
-                            for (int rr = 0; rr < kTcPhasesPerWarp; ++rr) {
-                                const uint32_t d = dacc + (uint32_t)((r0 + rr) * kTcNq);
-                                const uint64_t dbh = dbh0[rr] + (uint64_t)(2 * ks);
-                                const uint64_t dbl = dbl0[rr] + (uint64_t)(2 * ks);
-                                tc_mma_ts(d, ah, dbh, idesc, (ks > 0) ? 1u : acc0);
+                        for (int ks = 0; ks < kTcKB / 8; ++ks) {
+                            const int st = kb * (kTcKB / 8) + ks;  // k-step of the tile
+                            if (st >= s_lo && st < s_hi) {
+                                const uint32_t ah = a_hi + (uint32_t)(8 * ks);
+                                const uint32_t al = ah + (uint32_t)kTcKB;
+                                // rows u' = 8 st - 32 b .. + 7 of T: (u' / 4) x 128 bytes
+                                const uint32_t off = 32u * (uint32_t)(8 * st - 32 * r0);
+                                const uint64_t dbh = smem_desc(taps_base + off, 128, t_sbo);
+                                const uint64_t dbl = smem_desc(t_lo + off, 128, t_sbo);
+                                tc_mma_ts(d, ah, dbh, idesc, st > s_lo ? 1u : 0u);
                                 tc_mma_ts(d, ah, dbl, idesc, 1u);
                                 tc_mma_ts(d, al, dbh, idesc, 1u);
                             }
                         }
+                        tc_commit(&a_empty[t]);                      // A stage t may be refilled
+                        if (kb == kb_last) tc_commit(&acc_full[r0]);  // the block is complete
                     }
-                    tc_commit(&a_empty[t]);                    // A stage t may be refilled
-                    if (kb == n_kb - 1) tc_commit(&acc_full[a]);  // the tile is complete
+                    __syncwarp();
                 }
-                __syncwarp();
+            }
+        } else {
+            unsigned g = 0;
+            for (unsigned i = 0; i < n_tiles; ++i) {
+                const int a = (int)(i & 1u);
+                // the epilogue must have drained this accumulator (tile i - 2)
+                if (i >= 2 && !wait(&acc_empty[a], ((i >> 1) - 1) & 1u)) goto done;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dacc = tmem + (uint32_t)a * kTcAccCols;
+                for (int kb = 0; kb < n_kb; ++kb, ++g) {
+                    const int t = (int)(g % (unsigned)kTcAStages);
+                    if (!wait(&a_full[t], (g / (unsigned)kTcAStages) & 1u)) goto done;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    if (lane == 0) {
+                        const int u0 = kb * kTcKB;
+                        const int nks = min(kTcKB, K - u0) / 8;
+                        // A: 8 TMEM columns per k-step (hi, then lo 64 columns on);
+                        // B: the phase's tap array, 8 samples (32 B) per k-step, in
+                        // 16-byte descriptor units
+                        const uint32_t a_hi = tmem + kTcACol0 + (uint32_t)t * kTcACols;
+                        uint64_t dbh0[kTcPhasesPerWarp], dbl0[kTcPhasesPerWarp];
+#pragma unroll
+                        for (int rr = 0; rr < kTcPhasesPerWarp; ++rr) {
+                            const int r = r0 + rr;
+                            dbh0[rr] = smem_desc(taps_base + (uint32_t)(r * Z * 4 + u0 * 4), 16, 128);
+                            dbl0[rr] = smem_desc(taps_base + (uint32_t)((4 + r) * Z * 4 + u0 * 4), 16, 128);
+                        }
+                        const uint32_t acc0 = kb > 0 ? 1u : 0u;
+#pragma unroll
+                        for (int ks = 0; ks < kTcKB / 8; ++ks) {
+                            if (ks < nks) {
+                                const uint32_t ah = a_hi + (uint32_t)(8 * ks);
+                                const uint32_t al = ah + (uint32_t)kTcKB;
+#pragma unroll
+                                for (int rr = 0; rr < kTcPhasesPerWarp; ++rr) {
+                                    const uint32_t d = dacc + (uint32_t)((r0 + rr) * kTcNq);
+                                    const uint64_t dbh = dbh0[rr] + (uint64_t)(2 * ks);
+                                    const uint64_t dbl = dbl0[rr] + (uint64_t)(2 * ks);
+                                    tc_mma_ts(d, ah, dbh, idesc, (ks > 0) ? 1u : acc0);
+                                    tc_mma_ts(d, ah, dbl, idesc, 1u);
+                                    tc_mma_ts(d, al, dbh, idesc, 1u);
+                                }
+                            }
+                        }
+                        tc_commit(&a_empty[t]);                    // A stage t may be refilled
+                        if (kb == n_kb - 1) tc_commit(&acc_full[a]);  // the tile is complete
+                    }
+                    __syncwarp();
+                }
             }
         }
     } else if (warp >= 4 && warp < 8) {
         // ------------------------------ epilogue -----------------------------
         const int m = (warp & 3) * 32 + lane;  // TMEM lane = row of the tile
         const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
-        for (unsigned i = 0; i < n_tiles; ++i) {
+        for (unsigned i = 0; TOEP && i < n_tiles; ++i) {
+            // Toeplitz form: block b (accumulator columns 32 b..) holds outputs
+            // t0 + 32 b ..; it is read, handed back to its MMA warp, then stored
+            const TcTile tl = tc_tile(p, blockIdx.x + i * gridDim.x);
+            const EnvTcJob &jb = *tl.job;
+            const bool vec = (jb.T & 3) == 0;
+            const bool vec8 = (jb.T & 7) == 0 && (reinterpret_cast<uintptr_t>(jb.img) & 31) == 0;
+            const int row = tl.row0 + m;
+            const bool row_ok = row < jb.M;
+            float *irow = jb.img + (size_t)(row_ok ? row : 0) * jb.T;
+#pragma unroll 1
+            for (int b = 0; b < kTcMmaWarps; ++b) {
+                if (!wait(&acc_full[b], i & 1u)) goto done;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                float v[2][16];
+                tmem_ld16(lane_base + (uint32_t)(b * kTcNq), v[0]);
+                tmem_ld16(lane_base + (uint32_t)(b * kTcNq + 16), v[1]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                mbar_arrive(&acc_empty[b]);
+                const int tq = tl.t0 + b * kTcNq;
+                if (row_ok && vec8 && tq + kTcNq <= jb.T) {
+#pragma unroll
+                    for (int r = 0; r < 2; ++r)
+#pragma unroll
+                        for (int k = 0; k < 16; k += 8)
+                            st_global_v8(irow + tq + 16 * r + k, v[r][k], v[r][k + 1],
+                                         v[r][k + 2], v[r][k + 3], v[r][k + 4], v[r][k + 5],
+                                         v[r][k + 6], v[r][k + 7]);
+                } else if (row_ok) {
+#pragma unroll
+                    for (int r = 0; r < 2; ++r)
+#pragma unroll
+                        for (int k = 0; k < 16; k += 4) {
+                            const int t = tq + 16 * r + k;
+                            if (vec && t + 3 < jb.T) {
+                                *reinterpret_cast<float4 *>(irow + t) =
+                                    make_float4(v[r][k], v[r][k + 1], v[r][k + 2], v[r][k + 3]);
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 4; ++e)
+                                    if (t + e < jb.T) irow[t + e] = v[r][k + e];
+                            }
+                        }
+                }
+            }
+        }
+        for (unsigned i = 0; !TOEP && i < n_tiles; ++i) {
             const int a = (int)(i & 1u);
             const TcTile tl = tc_tile(p, blockIdx.x + i * gridDim.x);
             const EnvTcJob &jb = *tl.job;
