@@ -10,7 +10,7 @@
 // contiguous in t).  B is K-major too.  The J outputs are issued as four MMAs
 // of N = 32 columns each, in one of two forms:
 //
-//  * Toeplitz blocks (filters up to ~340 taps): block b covers the consecutive
+//  * Toeplitz blocks (filters up to 337 taps): block b covers the consecutive
 //    outputs j = 32 b + n (n = 0..31), whose band is only the 32 + 2 HA rows
 //    u = 32 b + u' (u' = 0..31 + 2 HA) of B, where B[u][j] = T[u'][n] =
 //    g~[u' - n] -- the same matrix T for every block.  T (hi and lo parts) is
