@@ -128,9 +128,9 @@ struct dmas_plan {
     // buffer, the interpolated-delay beamform's view of its root rows), reused
     // while the buffer is the same: encoding is host work on every call
     mutable std::mutex map_mu;
-    mutable CUtensorMap env_map{}, beam_map{};
-    mutable const void *env_map_ptr = nullptr, *beam_map_ptr = nullptr;
-    mutable int env_map_rows = -1;
+    mutable CUtensorMap env_map{}, beam_map{}, env_omap{};
+    mutable const void *env_map_ptr = nullptr, *beam_map_ptr = nullptr, *env_omap_ptr = nullptr;
+    mutable int env_map_rows = -1, env_omap_rows = -1;
 };
 
 namespace {
@@ -220,16 +220,18 @@ size_t beam_smem_bytes(const HostPlan &hp) {
 // tap operand (kEnvSmemMax, its opt-in below), at most kTcStages.
 int env_tc_stages(const HostPlan &hp) {
     if (hp.L == 0) return 0;
-    const int taps = tc_align1k(tc_tap_bytes((hp.L - 1) / 2));
-    const int room = kEnvSmemMax - 1024 - taps;
+    const int H = (hp.L - 1) / 2;
+    const int taps = tc_align1k(tc_tap_bytes(H));
+    const int room = kEnvSmemMax - 1024 - taps - tc_out_bytes(H);
     return std::min(kTcStages, room / kTcStageBytes);
 }
 
 size_t env_smem_bytes(const HostPlan &hp) {
     if (hp.L == 0) return 0;
     // + 1 KB: the kernel aligns its stages to 1024 bytes (the 128-byte swizzle period)
-    return 1024 + (size_t)tc_align1k(tc_tap_bytes((hp.L - 1) / 2)) +
-           (size_t)env_tc_stages(hp) * kTcStageBytes;
+    const int H = (hp.L - 1) / 2;
+    return 1024 + (size_t)tc_align1k(tc_tap_bytes(H)) + (size_t)env_tc_stages(hp) * kTcStageBytes +
+           (size_t)tc_out_bytes(H);
 }
 
 // TF32 rounding (nearest, ties away from zero) of a finite float, as cvt.rna.
@@ -360,6 +362,29 @@ EnvTcJob env_job(const dmas_plan *p, const float *ybuf, float *d_image, unsigned
                 p->env_map = j.tmap;
                 p->env_map_ptr = ybuf;
                 p->env_map_rows = rows;
+            }
+        }
+    }
+    // the image as a tensor-store target (Toeplitz form)
+    j.use_tma_store = 0;
+    if (tc_toeplitz((p->hp.L - 1) / 2) && (p->hp.T & 3) == 0 && ((uintptr_t)d_image & 15) == 0) {
+        std::lock_guard<std::mutex> lock(p->map_mu);
+        if (p->env_omap_ptr == d_image && p->env_omap_rows == rows) {
+            j.omap = p->env_omap;
+            j.use_tma_store = 1;
+        } else if (EncodeTiledFn enc = encode_tiled()) {
+            cuuint64_t dims[2] = {(cuuint64_t)p->hp.T, (cuuint64_t)rows};
+            cuuint64_t strides[1] = {(cuuint64_t)p->hp.T * 4};
+            cuuint32_t box[2] = {kTcNq, kTcRows};
+            cuuint32_t es[2] = {1, 1};
+            if (enc(&j.omap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)d_image, dims, strides,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS) {
+                j.use_tma_store = 1;
+                p->env_omap = j.omap;
+                p->env_omap_ptr = d_image;
+                p->env_omap_rows = rows;
             }
         }
     }

@@ -10,7 +10,7 @@
 // contiguous in t).  B is K-major too.  The J outputs are issued as four MMAs
 // of N = 32 columns each, in one of two forms:
 //
-//  * Toeplitz blocks (filters up to 337 taps): block b covers the consecutive
+//  * Toeplitz blocks (filters up to 209 taps): block b covers the consecutive
 //    outputs j = 32 b + n (n = 0..31), whose band is only the 32 + 2 HA rows
 //    u = 32 b + u' (u' = 0..31 + 2 HA) of B, where B[u][j] = T[u'][n] =
 //    g~[u' - n] -- the same matrix T for every block.  T (hi and lo parts) is
@@ -91,25 +91,35 @@ __host__ __device__ inline int tc_KB(int H) { return kTcNq + 2 * tc_halo(H); }
 __host__ __device__ inline int tc_toep_bytes(int H) { return 2 * 32 * 4 * tc_KB(H); }
 __host__ __device__ inline int tc_phase_bytes(int H) { return 8 * 4 * tc_Z(H); }
 __host__ __device__ inline int tc_align1k(int b) { return (b + 1023) & ~1023; }
-// The Toeplitz form whenever T leaves room for 4 stages of |y|
+// The Toeplitz form whenever T and the two store buffers leave room for 4
+// stages of |y|
 __host__ __device__ inline bool tc_toeplitz(int H) {
-    return kEnvSmemMax - 1024 - tc_align1k(tc_toep_bytes(H)) >= 4 * kTcStageBytes;
+    return kEnvSmemMax - 1024 - tc_align1k(tc_toep_bytes(H)) - 2 * kTcRows * kTcNq * 4 >=
+           4 * kTcStageBytes;
 }
 __host__ __device__ inline int tc_tap_bytes(int H) {
     return tc_toeplitz(H) ? tc_toep_bytes(H) : tc_phase_bytes(H);
 }
+// Toeplitz form: two store buffers (one block of 32 outputs x 128 rows each,
+// 128-byte swizzled) between the epilogue and the tensor stores
+constexpr int kTcOutBytes = kTcRows * kTcNq * 4;
+__host__ __device__ inline int tc_out_bytes(int H) { return tc_toeplitz(H) ? 2 * kTcOutBytes : 0; }
 
 struct EnvTcJob {
     // 2-D view of y for the TMA engine when T % 4 == 0: dims (T, M), box
     // {32 samples, 128 rows} with the 128-byte swizzle, landing as one atom
     // column of A; out-of-range coordinates filled with zeros.
     CUtensorMap tmap;
+    // 2-D view of the image for tensor stores (Toeplitz form): dims (T, M),
+    // box {32 outputs, 128 rows}, 128-byte swizzle; valid when use_tma_store
+    CUtensorMap omap;
     const float *y;   // [M][T]
     float *img;       // [M][T]
     int M, T;
     int tt0;          // first time tile (kTcJ outputs) of this job
     int t_tiles;      // time tiles of this job (all: ceil(T / kTcJ))
     int use_tma;      // T % 4 == 0 and the map was encoded
+    int use_tma_store;  // T % 4 == 0, img 16-byte aligned and omap encoded
     unsigned first;   // first tile of this job in the launch
 };
 
@@ -124,6 +134,7 @@ struct EnvTcParams {
     unsigned *err;
     EnvTcJob job[kBatchMax];
 };
+static_assert(sizeof(EnvTcParams) <= 32764, "kernel parameters exceed the launch limit");
 
 // Shared-memory matrix descriptor: start, leading and stride byte offsets,
 // version 1 (sm_100 family), base offset 0, layout (0 = no swizzle, 2 = the
@@ -210,6 +221,41 @@ __device__ __forceinline__ void st_global_v8(float *p, float a, float b, float c
                  : "memory");
 }
 
+// tensor store of one box from shared memory (bulk-group completion)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int c0,
+                                             int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(map),
+        "r"(smem_addr(src)), "r"(c0), "r"(c1)
+        : "memory");
+}
+__device__ __forceinline__ void bulk_commit() {
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// this thread's bulk groups but the newest N have finished reading shared memory
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void bulk_wait_all() {
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+// named barrier 1 over the 128 epilogue threads
+__device__ __forceinline__ void epi_sync() {
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+// named barrier 1 over the 128 epilogue threads, true iff every one passes true
+__device__ __forceinline__ bool epi_all(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 128, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+
 __device__ __forceinline__ void tc_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::
                      "r"(smem_addr(bar))
@@ -294,12 +340,15 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
     const int tap_bytes = TOEP ? tc_toep_bytes(H) : tc_phase_bytes(H);
     float *s_taps = reinterpret_cast<float *>(base);  // T hi, T lo; or [2][4][Z]
     unsigned char *stages = base + tc_align1k(tap_bytes);  // [S]
+    // Toeplitz form: the two store buffers after the stages (1024-aligned)
+    unsigned char *obuf = stages + (size_t)p.n_stages * kTcStageBytes;
     // host-checked build: the taps and the stages inside the dynamic shared
     // memory (otherwise the CTA does no tile)
     const bool layout_ok =
         checked_ok(p.n_stages >= 2 && p.n_stages <= kTcStages &&
                        smem_in(s_taps, (uint32_t)tap_bytes) &&
-                       smem_in(stages, (uint32_t)p.n_stages * (uint32_t)kTcStageBytes),
+                       smem_in(stages, (uint32_t)p.n_stages * (uint32_t)kTcStageBytes) &&
+                       (!TOEP || smem_in(obuf, 2u * kTcOutBytes)),
                    p.err);
     const unsigned n_tiles = (layout_ok && blockIdx.x < p.total_tiles)
                                  ? (p.total_tiles - 1 - blockIdx.x) / gridDim.x + 1
@@ -547,7 +596,8 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
             float *irow = jb.img + (size_t)(row_ok ? row : 0) * jb.T;
 #pragma unroll 1
             for (int b = 0; b < kTcMmaWarps; ++b) {
-                if (!wait(&acc_full[b], i & 1u)) goto done;
+                // every epilogue thread takes the same branch (named barriers follow)
+                if (!epi_all(wait(&acc_full[b], i & 1u))) goto done;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 float v[2][16];
                 tmem_ld16(lane_base + (uint32_t)(b * kTcNq), v[0]);
@@ -556,7 +606,25 @@ __global__ void __launch_bounds__(kTcThreadsWS, 1)
                 asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
                 mbar_arrive(&acc_empty[b]);
                 const int tq = tl.t0 + b * kTcNq;
-                if (row_ok && vec8 && tq + kTcNq <= jb.T) {
+                if (jb.use_tma_store) {
+                    // row m's 32 outputs into store buffer (4 i + b) & 1 at the
+                    // 128-byte swizzled chunk positions, then one tensor store of
+                    // the 32 x 128 box (rows past M and outputs past T clipped)
+                    unsigned char *ob = obuf + (size_t)((4 * i + b) & 1u) * kTcOutBytes;
+                    if (m == 0) bulk_wait_read<1>();  // the store two blocks back has read it
+                    epi_sync();
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        *reinterpret_cast<float4 *>(ob + m * 128 + (((c & 7) ^ (m & 7)) << 4)) =
+                            make_float4(v[c >> 2][4 * (c & 3)], v[c >> 2][4 * (c & 3) + 1],
+                                        v[c >> 2][4 * (c & 3) + 2], v[c >> 2][4 * (c & 3) + 3]);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    epi_sync();
+                    if (m == 0) {
+                        tma_store_2d(&jb.omap, ob, tq, tl.row0);
+                        bulk_commit();
+                    }
+                } else if (row_ok && vec8 && tq + kTcNq <= jb.T) {
 #pragma unroll
                     for (int r = 0; r < 2; ++r)
 #pragma unroll
@@ -638,6 +706,7 @@ done:
         }
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
+    if (TOEP && warp == 4 && lane == 0) bulk_wait_all();  // tensor stores in flight
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 9)

@@ -212,13 +212,13 @@ def test_generic_envelope_length():
 
 
 @pytest.mark.parametrize("T,M,taps", [(6001, 1200, None), (6000, 1201, None), (6004, 1200, 33),
-                                     (4096, 300, 337), (4096, 300, 339), (4096, 300, 1023)])
+                                     (4096, 300, 209), (4096, 300, 211), (4096, 300, 1023)])
 def test_tensor_core_envelope_ragged_tiles(T, M, taps):
     """Frames beyond 2e7 tap products (M T L) take the tensor-core FIR
     (smaller ones the CUDA-core FIR): ragged last row block and time tile,
     T % 4 != 0 (copy fallback) and T % 4 == 0 (TMA), another tap count, the
     longest filter whose Toeplitz block matrix still fits beside four stages
-    (337 taps), the shortest that takes the phase arrays instead (339), and the
+    (209 taps), the shortest that takes the phase arrays instead (211), and the
     longest filter (1023 taps)."""
     sc = hemi(T, M)
     kw = {} if taps is None else {"env_cutoff_hz": 1000.0 if taps > 500 else 20000.0,
