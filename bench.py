@@ -625,8 +625,8 @@ def run_split(args, wl, scene) -> None:
 # ---------------------------------------------------------------------------
 # serving: Poisson arrivals from 16 mixed sensors
 # ---------------------------------------------------------------------------
-def serving_measure(rates, seconds, rank=0, budget_gb=48, bulk_streams=3,
-                    to_host_rates=(), env_cap=None):
+def serving_measure(rates, seconds, rank=0, budget_gb=48, bulk_streams=1,
+                    to_host_rates=(), env_cap=None, bulk_depth=2):
     """Poisson arrivals from the 16-sensor mix at each rate, through the
     continuous-batching server and through the one-frame-per-launch baseline:
     latency to the image resident on the device (`rates`) and to the image
@@ -661,7 +661,7 @@ def serving_measure(rates, seconds, rank=0, budget_gb=48, bulk_streams=3,
         reqs = []
         with serving.Server(sensors, budget_bytes=budget_gb << 30, streams=2,
                             bulk_streams=bulk_streams, copy_back=copy_back,
-                            pinned=pinned,
+                            pinned=pinned, bulk_depth=bulk_depth,
                             bulk_env_tile_cap=serving.BULK_ENV_TILE_CAP if env_cap is None
                             else env_cap) as srv:
             t0 = time.perf_counter() + 0.05
@@ -724,7 +724,7 @@ def run_serving(args) -> None:
     results, mix = serving_measure(args.serve_rates, args.serve_seconds, rank,
                                    args.serve_budget_gb, args.serve_bulk_streams,
                                    to_host_rates=args.serve_to_host_rates,
-                                   env_cap=args.serve_env_cap)
+                                   env_cap=args.serve_env_cap, bulk_depth=args.serve_bulk_depth)
     wall1 = time.time()
     clocks.stop()
     if rank != 0:
@@ -749,6 +749,7 @@ def run_serving(args) -> None:
                    "delivered direction*samples/s at the highest device-resident rate",
                    "budget_gb": args.serve_budget_gb, "streams": 2,
                    "bulk_streams": args.serve_bulk_streams,
+                   "bulk_depth": args.serve_bulk_depth,
                    "bulk_envelope_tiles_per_cta": args.serve_env_cap,
                    "sensors": [f"N{s.n_mics} M{s.n_dirs} T{s.n_samples} n{s.order}"
                                for s in mix]},
@@ -1023,7 +1024,9 @@ def main() -> None:
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 1000.0])
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-budget-gb", type=int, default=48)
-    ap.add_argument("--serve-bulk-streams", type=int, default=3)
+    ap.add_argument("--serve-bulk-streams", type=int, default=1)
+    ap.add_argument("--serve-bulk-depth", type=int, default=2,
+                    help="big-frame batches in flight at once")
     ap.add_argument("--serve-to-host-rates", type=float, nargs="*", default=[100.0])
     ap.add_argument("--serve-env-cap", type=int, default=16,
                     help="tensor-core envelope tiles per CTA for the bulk lane (0: no cap)")

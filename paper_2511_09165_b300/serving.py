@@ -89,13 +89,16 @@ class PinnedPool:
     """Page-locked host buffers reused by shape: allocating pinned memory
     takes milliseconds per gigabyte, so copies back to the host draw on this
     pool instead of allocating per frame.  When every buffer of a shape is in
-    use, get() waits (up to `wait_s`) for one to come back before it
-    allocates another."""
+    use, get() allocates another at once if it is smaller than `wait_bytes`,
+    and otherwise waits (up to `wait_s`) for one to come back first (a caller
+    that waits holds up whatever it dispatches, so only the buffers that are
+    slow to allocate are worth waiting for)."""
 
-    def __init__(self, wait_s: float = 2.0):
+    def __init__(self, wait_s: float = 2.0, wait_bytes: int = 64 << 20):
         import torch
         self.torch = torch
         self.wait_s = float(wait_s)
+        self.wait_bytes = int(wait_bytes)
         self._free: dict = collections.defaultdict(list)
         self._owned: dict = collections.defaultdict(int)
         self._cv = threading.Condition()
@@ -108,8 +111,9 @@ class PinnedPool:
 
     def get(self, shape):
         shape = tuple(shape)
+        big = 4 * int(np.prod(shape)) >= self.wait_bytes
         with self._cv:
-            if not self._free[shape] and self._owned[shape] > 0:
+            if not self._free[shape] and self._owned[shape] > 0 and big:
                 self._cv.wait_for(lambda: bool(self._free[shape]), timeout=self.wait_s)
             if self._free[shape]:
                 return self._free[shape].pop()
@@ -130,10 +134,12 @@ class PinnedPool:
 
 
 class _Lane:
-    def __init__(self, name, streams, max_batch):
+    def __init__(self, name, streams, max_batch, depth=None):
         self.name = name
         self.streams = streams
         self.max_batch = max_batch
+        # batches in flight at once (several may queue on one stream)
+        self.depth = len(streams) if depth is None else max(1, int(depth))
         self.queue = collections.deque()
         self.in_flight = 0
         self.next_stream = 0
@@ -161,15 +167,23 @@ class Server:
     """fast_cost: frames with cost <= fast_cost use the fast lane (default:
     about 0.5 ms of GPU work, 1.3e9 mic x direction x samples).  `streams`
     is the fast lane's stream count, `bulk_streams` the bulk lane's (None:
-    the same); `bulk_batch` frames per bulk batch.  Defaults measured on B300
-    with the 16-sensor mix at 200 frames/s: one big frame per batch on three
-    low-priority streams kept the small frames' p99 lowest."""
+    the same), `bulk_depth` the big-frame batches in flight at once (None:
+    one per bulk stream; more queue on a stream, so the next big frame is
+    enqueued while the previous one runs); `bulk_batch` frames per bulk
+    batch.  Defaults measured on B300 with the 16-sensor mix at 200 frames/s:
+    one big frame per batch on one low-priority stream, two in flight, keeps
+    big frames first-in first-out as one stream does (three concurrent
+    streams stretched each big frame by the others' work: overall p99 +2 ms)
+    while the small frames overtake them on high-priority streams."""
+
+    # the server thread's sleep between scans of the batches in flight
+    poll_s = 50e-6
 
     def __init__(self, sensors, device=None, budget_bytes: int = 32 << 30,
                  max_batch: int = 64, streams: int = 2, copy_back: bool = False,
                  fast_cost: float = FAST_COST, bulk_batch: int = 1,
-                 bulk_streams: int | None = 3, bulk_env_tile_cap: int = BULK_ENV_TILE_CAP,
-                 pinned: PinnedPool | None = None):
+                 bulk_streams: int | None = 1, bulk_env_tile_cap: int = BULK_ENV_TILE_CAP,
+                 pinned: PinnedPool | None = None, bulk_depth: int | None = 2):
         import torch
         self.torch = torch
         self.sensors = list(sensors)
@@ -184,7 +198,7 @@ class Server:
         self.fast = _Lane("fast", [torch.cuda.Stream(device=self.device, priority=hi)
                                    for _ in range(n_fast)], int(max_batch))
         self.bulk = _Lane("bulk", [torch.cuda.Stream(device=self.device, priority=lo)
-                                   for _ in range(n_bulk)], max(1, int(bulk_batch)))
+                                   for _ in range(n_bulk)], max(1, int(bulk_batch)), bulk_depth)
         self._cv = threading.Condition()
         self._reserved = 0
         self._inflight_q: collections.deque = collections.deque()
@@ -195,12 +209,15 @@ class Server:
         self.pinned = pinned if pinned is not None else (PinnedPool() if copy_back else None)
         if copy_back:
             # page-locking takes milliseconds per gigabyte: hold enough host
-            # images now for the frames that can be in flight at once (a big
-            # frame per bulk stream, small ones in the fast lane's batches)
+            # images now for the frames that can be in flight at once (the
+            # bulk lane's depth of big frames, small ones in the fast lane's
+            # batches), counted per sensor and pooled per shape
+            want = collections.Counter()
             for sn in self.sensors:
                 small = sn.cost <= self.fast_cost
-                want = 4 if small else len(self.bulk.streams) + 1
-                self.pinned.reserve(sn.image_shape, want)
+                want[tuple(sn.image_shape)] += 4 if small else self.bulk.depth + 1
+            for shape, n in want.items():
+                self.pinned.reserve(shape, n)
         # big frames' envelopes retire their CTAs every few tiles, so the fast
         # lane's kernels reach the SMs without waiting for a whole envelope
         for sn in self.sensors:
@@ -213,8 +230,7 @@ class Server:
     # -- lifecycle -------------------------------------------------------
     def start(self):
         self._running = True
-        self._threads = [threading.Thread(target=self._dispatch, daemon=True),
-                         threading.Thread(target=self._complete, daemon=True)]
+        self._threads = [threading.Thread(target=self._loop, daemon=True)]
         for t in self._threads:
             t.start()
         return self
@@ -252,19 +268,21 @@ class Server:
                 self._cv.wait(timeout=min(left, 0.1))
         return True
 
-    # -- dispatcher: admission and batching -------------------------------
-    def _dispatch(self):
+    # -- the server's thread: completion, admission and batching ------------
+    def _loop(self):
+        """One thread completes finished batches, admits queued frames and
+        launches batches: with no second thread to hand the interpreter lock
+        to, a launch is not kept waiting behind a completion poll."""
         while True:
+            self._reap()
             with self._cv:
-                lane = None
-                while True:
-                    lane = next((ln for ln in (self.fast, self.bulk) if self._can_launch(ln)),
-                                None)
-                    if lane is not None or not self._running:
-                        break
-                    self._cv.wait(timeout=0.05)
+                lane = next((ln for ln in (self.fast, self.bulk) if self._can_launch(ln)), None)
                 if lane is None:
-                    return                          # stopped and nothing launchable
+                    if not self._inflight_q and not self._running:
+                        return                      # stopped, nothing in flight
+                    # poll the batches in flight; otherwise sleep until a submit
+                    self._cv.wait(timeout=self.poll_s if self._inflight_q else 0.05)
+                    continue
                 batch = []
                 while lane.queue and len(batch) < lane.max_batch:
                     req = lane.queue[0]
@@ -291,7 +309,7 @@ class Server:
             self._launch(batch, stream, lane)
 
     def _can_launch(self, lane) -> bool:
-        if not lane.queue or lane.in_flight >= len(lane.streams):
+        if not lane.queue or lane.in_flight >= lane.depth:
             return False
         head = self.sensors[lane.queue[0].sensor].device_bytes
         return head > self.budget or self._reserved + head <= self.budget
@@ -309,11 +327,11 @@ class Server:
             ws = torch.empty(batch_workspace_bytes(plans), device=self.device, dtype=torch.uint8)
             beamform_batch(plans, frames, images, workspace=ws, stream=stream)
             hosts = None
+            ev = torch.cuda.Event()
             if self.copy_back:
                 hosts = [self.pinned.get(im.shape) for im in images]
                 for h, im in zip(hosts, images):
                     _copy_in_pieces(h, im)
-            ev = torch.cuda.Event()
             ev.record(stream)
         self.batches += 1
         with self._cv:
@@ -321,25 +339,18 @@ class Server:
             self._cv.notify_all()
 
     # -- completion: latency and memory release ----------------------------
-    def _complete(self):
-        while True:
-            with self._cv:
-                while self._running and not self._inflight_q:
-                    self._cv.wait(timeout=0.05)
-                if not self._inflight_q:
-                    if not self._running:
-                        return
-                    continue
-                # any batch whose completion event has fired (fast lanes finish
-                # out of order with the bulk lane)
-                item = next((x for x in self._inflight_q if x[0].query()), None)
-                if item is not None:
-                    self._inflight_q.remove(item)
-            if item is None:
-                time.sleep(50e-6)
-                continue
-            ev, batch, frames, images, ws, hosts, lane = item
-            t = time.perf_counter()
+    def _reap(self):
+        """Every batch whose completion event has fired (fast lanes finish out
+        of order with the bulk lane): record its requests' latency, hand back
+        host buffers and release its share of the memory budget."""
+        with self._cv:
+            done = [x for x in self._inflight_q if x[0].query()]
+            for item in done:
+                self._inflight_q.remove(item)
+        if not done:
+            return
+        t = time.perf_counter()
+        for ev, batch, frames, images, ws, hosts, lane in done:
             for k, r in enumerate(batch):
                 r.t_done = t
                 r.batch_size = len(batch)
@@ -347,13 +358,14 @@ class Server:
                     r.image = hosts[k] if hosts is not None else images[k]
                 elif hosts is not None:
                     self.pinned.put(hosts[k])
-            with self._cv:
+        with self._cv:
+            for ev, batch, frames, images, ws, hosts, lane in done:
                 for r in batch:
                     self._reserved -= self.sensors[r.sensor].device_bytes
                     self.completed.append(r)
                     r.done.set()
                 lane.in_flight -= 1
-                self._cv.notify_all()
+            self._cv.notify_all()
 
 
 def one_frame_per_launch(sensors, requests, device=None, copy_back: bool = False,
