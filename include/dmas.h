@@ -243,6 +243,20 @@ dmas_status dmas_beamform_batch(int count, dmas_plan *const *plans,
                                 const float *const *d_frames, float *const *d_images,
                                 void *d_workspace, size_t workspace_bytes, void *stream);
 
+/*
+ * dmas_beamform_batch for frames held in host memory, in one call: each
+ * h_frames[k] (HOST, [N][T] float32 of plans[k]; page-locked for the copy to
+ * be asynchronous) is copied into the device buffer d_frames[k] on `stream`,
+ * the batch is enqueued there as dmas_beamform_batch does, and `done_event`
+ * (a cudaEvent_t the caller created, or NULL) is recorded after it.  The
+ * caller keeps h_frames[k] unchanged until the event has fired.  Errors as for
+ * dmas_beamform_batch; DMAS_EINVAL also for a NULL h_frames entry.
+ */
+dmas_status dmas_beamform_batch_upload(int count, dmas_plan *const *plans,
+                                       const float *const *h_frames, float *const *d_frames,
+                                       float *const *d_images, void *d_workspace,
+                                       size_t workspace_bytes, void *stream, void *done_event);
+
 /* Device bytes a batch of these plans needs (0 on a NULL argument). */
 size_t dmas_batch_workspace_bytes(int count, dmas_plan *const *plans);
 

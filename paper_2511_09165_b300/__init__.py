@@ -45,7 +45,8 @@ STATUS = {0: "DMAS_OK", 1: "DMAS_EINVAL", 2: "DMAS_ENOMEM", 3: "DMAS_ECUDA",
 EXPORTS = [
     "dmas_plan_create", "dmas_destroy", "dmas_beamform", "dmas_beamform_orders",
     "dmas_beamform_host",
-    "dmas_beamform_batch", "dmas_batch_workspace_bytes", "dmas_plan_workspace_bytes",
+    "dmas_beamform_batch", "dmas_beamform_batch_upload", "dmas_batch_workspace_bytes",
+    "dmas_plan_workspace_bytes",
     "dmas_plan_get_info", "dmas_plan_get_delays", "dmas_plan_get_taps", "dmas_plan_check",
     "dmas_plan_last_error", "dmas_plan_set_profiling", "dmas_plan_stage_ms",
     "dmas_selftest_wait_timeout", "dmas_beamform_noalloc", "dmas_status_string",
@@ -108,6 +109,7 @@ def load_library(path: str | None = None):
             "dmas_beamform_host": ([vp, vp, vp, vp], i),
             "dmas_beamform_orders": ([vp, vp, ctypes.c_uint, i, vp, vp, vp], i),
             "dmas_beamform_batch": ([i, vp, vp, vp, vp, sz, vp], i),
+            "dmas_beamform_batch_upload": ([i, vp, vp, vp, vp, vp, sz, vp, vp], i),
             "dmas_batch_workspace_bytes": ([i, vp], sz),
             "dmas_plan_workspace_bytes": ([vp], sz),
             "dmas_plan_get_info": ([vp, ctypes.POINTER(PlanInfo)], i),
@@ -407,6 +409,36 @@ def beamform_batch(plans, frames, images=None, workspace=None, stream=None):
                                  ctypes.c_void_p(_stream_handle(stream)))
     if st != 0:
         raise DmasError(st, "dmas_beamform_batch")
+    return images
+
+
+def beamform_batch_upload(plans, host_frames, frames, images, workspace, stream=None,
+                          done_event=None):
+    """beamform_batch for frames in (page-locked) host memory, in one call into
+    the library: host_frames[k] is copied into the device tensor frames[k] on
+    the stream, the batch runs, and `done_event` (a recorded-once
+    torch.cuda.Event, or None) is recorded after it."""
+    lib = load_library()
+    n = len(plans)
+    if not (n == len(host_frames) == len(frames) == len(images)):
+        raise ValueError("plans, host frames, frames and images differ in length")
+    import torch
+    for p, h, f, im in zip(plans, host_frames, frames, images):
+        if h.device.type != "cpu" or not h.is_contiguous() or h.dtype != torch.float32 \
+                or tuple(h.shape) != (p.n_mics, p.n_samples):
+            raise ValueError(f"host frame must be a contiguous CPU float32 {(p.n_mics, p.n_samples)}")
+        _check_tensor(f, (p.n_mics, p.n_samples), "frame")
+        _check_tensor(im, (p.n_dirs, p.n_samples), "image")
+    ph = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    hp = (ctypes.c_void_p * n)(*[h.data_ptr() for h in host_frames])
+    fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in frames])
+    ip = (ctypes.c_void_p * n)(*[im.data_ptr() for im in images])
+    ev = ctypes.c_void_p(done_event.cuda_event if done_event is not None else 0)
+    st = lib.dmas_beamform_batch_upload(n, ph, hp, fp, ip, ctypes.c_void_p(workspace.data_ptr()),
+                                        workspace.numel() * workspace.element_size(),
+                                        ctypes.c_void_p(_stream_handle(stream)), ev)
+    if st != 0:
+        raise DmasError(st, "dmas_beamform_batch_upload")
     return images
 
 

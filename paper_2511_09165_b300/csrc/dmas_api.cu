@@ -1264,6 +1264,27 @@ dmas_status dmas_beamform_batch(int count, dmas_plan *const *plans, const float 
     return enqueue_batch(v, s);
 }
 
+dmas_status dmas_beamform_batch_upload(int count, dmas_plan *const *plans,
+                                       const float *const *h_frames, float *const *d_frames,
+                                       float *const *d_images, void *d_workspace,
+                                       size_t workspace_bytes, void *stream, void *done_event) {
+    if (count < 1 || !plans || !h_frames || !d_frames) return DMAS_EINVAL;
+    for (int k = 0; k < count; ++k)
+        if (!plans[k] || !h_frames[k] || !d_frames[k]) return DMAS_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < count; ++k) {
+        const size_t bytes = (size_t)plans[k]->hp.N * plans[k]->hp.T * sizeof(float);
+        const cudaError_t e =
+            cudaMemcpyAsync(d_frames[k], h_frames[k], bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) return cuda_fail(plans[k], e, "frame upload");
+    }
+    const dmas_status st =
+        dmas_beamform_batch(count, plans, d_frames, d_images, d_workspace, workspace_bytes, stream);
+    if (st != DMAS_OK || !done_event) return st;
+    const cudaError_t e = cudaEventRecord((cudaEvent_t)done_event, s);
+    return e == cudaSuccess ? DMAS_OK : cuda_fail(plans[0], e, "completion event");
+}
+
 dmas_status dmas_plan_get_info(const dmas_plan *p, dmas_plan_info *info) {
     if (!p || !info) return DMAS_EINVAL;
     const HostPlan &hp = p->hp;

@@ -35,7 +35,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import beamform_batch, batch_workspace_bytes
+from . import beamform_batch_upload, batch_workspace_bytes
 
 
 @dataclass
@@ -202,6 +202,8 @@ class Server:
         self._cv = threading.Condition()
         self._reserved = 0
         self._inflight_q: collections.deque = collections.deque()
+        self._events: list = []      # completion events free for reuse
+        self._ws_bytes: dict = {}    # batch workspace bytes by sensor tuple
         self._running = False
         self._threads = []
         self.batches = 0
@@ -314,25 +316,39 @@ class Server:
         head = self.sensors[lane.queue[0].sensor].device_bytes
         return head > self.budget or self._reserved + head <= self.budget
 
+    def _event(self, stream):
+        """A completion event from the free list (created by one record)."""
+        if self._events:
+            return self._events.pop()
+        ev = self.torch.cuda.Event()
+        ev.record(stream)
+        return ev
+
     def _launch(self, batch, stream, lane):
         torch = self.torch
         with torch.cuda.stream(stream):
             plans = [self.sensors[r.sensor].plan for r in batch]
-            frames, images = [], []
-            for r, p in zip(batch, plans):
-                f = torch.empty((p.n_mics, p.n_samples), device=self.device)
-                f.copy_(r.frame, non_blocking=True)
-                frames.append(f)
-                images.append(torch.empty((p.n_dirs, p.n_samples), device=self.device))
-            ws = torch.empty(batch_workspace_bytes(plans), device=self.device, dtype=torch.uint8)
-            beamform_batch(plans, frames, images, workspace=ws, stream=stream)
+            key = tuple(r.sensor for r in batch)
+            ws_bytes = self._ws_bytes.get(key)
+            if ws_bytes is None:
+                ws_bytes = self._ws_bytes[key] = batch_workspace_bytes(plans)
+            frames = [torch.empty((p.n_mics, p.n_samples), device=self.device) for p in plans]
+            images = [torch.empty((p.n_dirs, p.n_samples), device=self.device) for p in plans]
+            ws = torch.empty(ws_bytes, device=self.device, dtype=torch.uint8)
             hosts = None
-            ev = torch.cuda.Event()
             if self.copy_back:
+                ev = torch.cuda.Event()
+                beamform_batch_upload(plans, [r.frame for r in batch], frames, images, ws,
+                                      stream=stream)
                 hosts = [self.pinned.get(im.shape) for im in images]
                 for h, im in zip(hosts, images):
                     _copy_in_pieces(h, im)
-            ev.record(stream)
+                ev.record(stream)
+            else:
+                # uploads, the batch and its completion event in one library call
+                ev = self._event(stream)
+                beamform_batch_upload(plans, [r.frame for r in batch], frames, images, ws,
+                                      stream=stream, done_event=ev)
         self.batches += 1
         with self._cv:
             self._inflight_q.append((ev, batch, frames, images, ws, hosts, lane))
@@ -365,6 +381,8 @@ class Server:
                     self.completed.append(r)
                     r.done.set()
                 lane.in_flight -= 1
+                if hosts is None:
+                    self._events.append(ev)
             self._cv.notify_all()
 
 
