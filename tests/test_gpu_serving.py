@@ -46,6 +46,18 @@ def test_batch_of_mixed_variants_is_bitwise_equal_to_single_calls():
     torch.cuda.synchronize()
     for k, im in zip(order, imgs):
         assert torch.equal(im, alone[k]), k
+    # the same batch from host frames in one call (upload, batch, completion event)
+    bp = [plans[k] for k in order]
+    hosts = [torch.from_numpy(scs[k].frame).pin_memory() for k in order]
+    dev = [torch.empty((p.n_mics, p.n_samples), device="cuda") for p in bp]
+    out = [torch.empty((p.n_dirs, p.n_samples), device="cuda") for p in bp]
+    ws = torch.empty(dm.batch_workspace_bytes(bp), device="cuda", dtype=torch.uint8)
+    done = torch.cuda.Event()
+    done.record()                           # the event exists before the call records it
+    dm.beamform_batch_upload(bp, hosts, dev, out, ws, done_event=done)
+    done.synchronize()
+    for k, im in zip(order, out):
+        assert torch.equal(im, alone[k]), k
     for p in plans:
         p.check()
         p.close()
