@@ -340,6 +340,44 @@ def test_sign_flip_is_exact_for_odd_orders():
     assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("mode", ["round", "linear"])
+def test_image_is_one_homogeneous_in_the_frame(mode):
+    """E_n of n-th roots has degree 1 in the samples, CF degree 0 and the
+    envelope is linear, so scaling the frame by a scales y and the image by a
+    (up to FP32 rounding of the roots)."""
+    sc = hemi(1500, 200)
+    dmode = dm.LINEAR if mode == "linear" else dm.ROUND
+    plan = gpu_plan(dm, sc, 5, dmode)
+    x = torch.from_numpy(sc.frame).cuda()
+    y1 = torch.empty((sc.n_dirs, sc.n_samples), device="cuda")
+    y2 = torch.empty_like(y1)
+    a = plan(x, y=y1).cpu().numpy()
+    b = plan(3.7 * x, y=y2).cpu().numpy()
+    plan.check()
+    plan.close()
+    assert eps_peak(y2.cpu().numpy(), 3.7 * y1.cpu().numpy()) <= TOL_F32
+    assert eps_peak(b, 3.7 * a) <= TOL_F32
+
+
+def test_microphone_order_does_not_change_the_image():
+    """The sums run over the microphones, so listing them in another order
+    changes the image only by FP32 rounding."""
+    sc = hemi(1500, 200)
+    tau = scene_tau(sc)
+    perm = np.random.default_rng(3).permutation(sc.mic_xyz.shape[0])
+    kw = dict(n_samples=sc.n_samples, fs=sc.fs, c=sc.c, order=5, delay_mode=dm.LINEAR)
+    p1 = dm.Plan(delays_s=tau, **kw)
+    p2 = dm.Plan(delays_s=np.ascontiguousarray(tau[:, perm]), **kw)
+    x = torch.from_numpy(sc.frame).cuda()
+    a = p1(x).cpu().numpy()
+    b = p2(x[torch.from_numpy(perm).cuda()].contiguous()).cpu().numpy()
+    p1.check()
+    p2.check()
+    p1.close()
+    p2.close()
+    assert eps_peak(b, a) <= TOL_F32
+
+
 def test_explicit_delays_equal_geometry():
     sc = small_2d(600)
     tau = scene_tau(sc)
