@@ -625,8 +625,8 @@ def run_split(args, wl, scene) -> None:
 # ---------------------------------------------------------------------------
 # serving: Poisson arrivals from 16 mixed sensors
 # ---------------------------------------------------------------------------
-def serving_measure(rates, seconds, rank=0, budget_gb=48, bulk_streams=1,
-                    to_host_rates=(), env_cap=None, bulk_depth=2):
+def serving_measure(rates, seconds, rank=0, budget_gb=48, to_host_rates=(), env_cap=None,
+                    bulk_depth=2):
     """Poisson arrivals from the 16-sensor mix at each rate, through the
     continuous-batching server and through the one-frame-per-launch baseline:
     latency to the image resident on the device (`rates`) and to the image
@@ -660,8 +660,7 @@ def serving_measure(rates, seconds, rank=0, budget_gb=48, bulk_streams=1,
         offs, which, fidx = schedule(rate, seed)
         reqs = []
         with serving.Server(sensors, budget_bytes=budget_gb << 30, streams=2,
-                            bulk_streams=bulk_streams, copy_back=copy_back,
-                            pinned=pinned, bulk_depth=bulk_depth,
+                            copy_back=copy_back, pinned=pinned, bulk_depth=bulk_depth,
                             bulk_env_tile_cap=serving.BULK_ENV_TILE_CAP if env_cap is None
                             else env_cap) as srv:
             t0 = time.perf_counter() + 0.05
@@ -722,7 +721,7 @@ def run_serving(args) -> None:
     clocks.start()
     wall0 = time.time()
     results, mix = serving_measure(args.serve_rates, args.serve_seconds, rank,
-                                   args.serve_budget_gb, args.serve_bulk_streams,
+                                   args.serve_budget_gb,
                                    to_host_rates=args.serve_to_host_rates,
                                    env_cap=args.serve_env_cap, bulk_depth=args.serve_bulk_depth)
     wall1 = time.time()
@@ -748,7 +747,7 @@ def run_serving(args) -> None:
                    " frames/s: to the image copied to pinned host memory); value = "
                    "delivered direction*samples/s at the highest device-resident rate",
                    "budget_gb": args.serve_budget_gb, "streams": 2,
-                   "bulk_streams": args.serve_bulk_streams,
+                   "bulk_streams": 1,
                    "bulk_depth": args.serve_bulk_depth,
                    "bulk_envelope_tiles_per_cta": args.serve_env_cap,
                    "sensors": [f"N{s.n_mics} M{s.n_dirs} T{s.n_samples} n{s.order}"
@@ -1024,7 +1023,6 @@ def main() -> None:
     ap.add_argument("--serve-rates", type=float, nargs="+", default=[200.0, 1000.0])
     ap.add_argument("--serve-seconds", type=float, default=5.0)
     ap.add_argument("--serve-budget-gb", type=int, default=48)
-    ap.add_argument("--serve-bulk-streams", type=int, default=1)
     ap.add_argument("--serve-bulk-depth", type=int, default=2,
                     help="big-frame batches in flight at once")
     ap.add_argument("--serve-to-host-rates", type=float, nargs="*", default=[100.0])

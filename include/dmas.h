@@ -366,6 +366,77 @@ dmas_status dmas_selftest_wait_timeout(double limit_ms, void *stream);
 dmas_status dmas_beamform_noalloc(dmas_plan *plan, const float *d_frame, float *d_image,
                                   void *stream);
 
+/*
+ * Serving runtime: frames from many sensors (each with its own plan) arrive
+ * over time; a native thread batches them and launches them, so no
+ * interpreter or caller thread sits between a frame's arrival and its launch.
+ * This has no counterpart in the paper.
+ *
+ * Two lanes.  Frames whose work N*M*T is at most fast_cost take the fast lane:
+ * fast_streams high-priority streams, up to max_batch frames (of any sensors)
+ * per batch, one batch in flight per stream.  The others take the bulk lane:
+ * one low-priority stream, one frame per batch, up to bulk_depth batches
+ * queued on it at once (first in, first out, like one stream of single-frame
+ * launches), overtaken on the SMs by the fast lane's kernels.  A frame is
+ * admitted when its device bytes (frame, image and scratch) fit in
+ * budget_bytes beside the frames in flight; a frame larger than the budget is
+ * rejected (status DMAS_ENOMEM in its completion).
+ *
+ * The server's thread uploads each admitted frame from h_frame (page-locked
+ * host memory for an asynchronous copy) into device memory it takes, with the
+ * frame's image and scratch, from stream-ordered pools (cudaMallocAsync: no
+ * device-wide synchronisation), runs the batch (dmas_beamform_batch_upload)
+ * and copies the image to h_image when that is not NULL.  A frame submitted
+ * with keep_image hands its device image to the caller in its completion
+ * (free it with dmas_server_image_free); otherwise the image is freed once
+ * the batch (and its copy) is done.  Times are CLOCK_MONOTONIC seconds.  The
+ * caller keeps h_frame and h_image alive and unchanged until the frame's
+ * completion.
+ */
+typedef struct dmas_server dmas_server;
+typedef struct {
+    int n_plans;
+    dmas_plan *const *plans;   /* HOST array: one plan per sensor, not owned */
+    double fast_cost;          /* N*M*T bound of the fast lane */
+    int fast_streams;          /* >= 1 */
+    int max_batch;             /* 1..64 frames per fast-lane batch */
+    int bulk_depth;            /* >= 1 bulk-lane batches in flight */
+    size_t budget_bytes;       /* device bytes of the frames in flight */
+} dmas_server_desc;
+typedef struct {
+    uint64_t ticket;           /* from dmas_server_submit */
+    int sensor;
+    int status;                /* DMAS_OK, DMAS_ENOMEM (rejected) or a launch error */
+    int batch_size;            /* frames in its batch */
+    double t_arrival, t_admitted, t_done;  /* t_done: completion observed */
+    float *d_image;            /* keep_image: the device image [M][T], else NULL */
+} dmas_server_done;
+
+/* Create a server on the current device and start its thread.  Errors:
+ * DMAS_EINVAL (bad desc), DMAS_ENOMEM, DMAS_ECUDA. */
+dmas_status dmas_server_create(const dmas_server_desc *desc, dmas_server **out);
+/* Queue one frame of sensor `sensor` that arrived at t_arrival; *ticket
+ * identifies its completion.  h_image (HOST [M][T] or NULL) receives a copy of
+ * the image; keep_image != 0 hands the device image over in the completion.
+ * Errors: DMAS_EINVAL, DMAS_EBUSY (server closing). */
+dmas_status dmas_server_submit(dmas_server *server, int sensor, const float *h_frame,
+                               float *h_image, int keep_image, double t_arrival,
+                               uint64_t *ticket);
+/* Free a device image a completion handed over, ordered after the work
+ * already enqueued on `stream` (NULL: the legacy default stream).  It may
+ * outlive the server that produced it.  NULL d_image is a no-op. */
+dmas_status dmas_server_image_free(float *d_image, void *stream);
+/* The next completion, waiting up to timeout_s seconds for one.  Errors:
+ * DMAS_ETIMEOUT (none yet), DMAS_EINVAL. */
+dmas_status dmas_server_wait(dmas_server *server, double timeout_s, dmas_server_done *out);
+/* Frames queued or in flight (completions not yet taken by dmas_server_wait
+ * are not counted). */
+int dmas_server_pending(dmas_server *server);
+/* Stop accepting frames, finish the ones queued and in flight, stop the
+ * thread and free everything; completions not yet taken are dropped.  NULL
+ * is a no-op. */
+dmas_status dmas_server_destroy(dmas_server *server);
+
 /* Static text for a status code. */
 const char *dmas_status_string(dmas_status status);
 

@@ -50,7 +50,8 @@ EXPORTS = [
     "dmas_plan_get_info", "dmas_plan_get_delays", "dmas_plan_get_taps", "dmas_plan_check",
     "dmas_plan_last_error", "dmas_plan_set_profiling", "dmas_plan_stage_ms",
     "dmas_selftest_wait_timeout", "dmas_beamform_noalloc", "dmas_status_string",
-    "dmas_plan_set_envelope_tile_cap",
+    "dmas_plan_set_envelope_tile_cap", "dmas_server_create", "dmas_server_submit",
+    "dmas_server_wait", "dmas_server_pending", "dmas_server_destroy", "dmas_server_image_free",
     "dmas_version",
 ]
 
@@ -123,6 +124,13 @@ def load_library(path: str | None = None):
             "dmas_selftest_wait_timeout": ([ctypes.c_double, vp], i),
             "dmas_beamform_noalloc": ([vp, vp, vp, vp], i),
             "dmas_status_string": ([i], ctypes.c_char_p),
+            "dmas_server_create": ([vp, ctypes.POINTER(vp)], i),
+            "dmas_server_submit": ([vp, i, vp, vp, i, ctypes.c_double,
+                                    ctypes.POINTER(ctypes.c_uint64)], i),
+            "dmas_server_image_free": ([vp, vp], i),
+            "dmas_server_wait": ([vp, ctypes.c_double, vp], i),
+            "dmas_server_pending": ([vp], i),
+            "dmas_server_destroy": ([vp], i),
             "dmas_version": ([], i),
         }
         for name, (args, res) in sig.items():

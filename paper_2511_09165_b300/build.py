@@ -39,7 +39,8 @@ def _nvcc() -> str:
 
 
 def sources() -> list[str]:
-    out = [os.path.join(CSRC, "dmas_api.cu"), os.path.join(CSRC, "dmas_plan.cpp")]
+    out = [os.path.join(CSRC, "dmas_api.cu"), os.path.join(CSRC, "dmas_plan.cpp"),
+           os.path.join(CSRC, "dmas_server.cpp")]
     out += [os.path.join(CSRC, f"beam_o{n}.cu") for n in range(1, 9)]
     extra = sorted(f for f in os.listdir(CSRC)
                    if f.endswith(".cu") and not f.startswith(("beam_o", "dmas_api")))

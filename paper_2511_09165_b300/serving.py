@@ -1,41 +1,42 @@
 """Continuous-batching server for sonar frames from several sensors.
 
 Each sensor has a resident plan (delay tables and taps on the device).  Frames
-arrive on the host at any time; the server
+arrive on the host at any time and are handed to the library's serving
+runtime (dmas_server_* in the C ABI), whose native thread
 
   * admits a frame when the device-memory budget has room for its frame,
-    image and scratch (otherwise it waits in the FIFO queue; a frame that can
-    never fit is rejected),
-  * gathers every admitted frame that is waiting into one batch (up to
-    `max_batch`) and runs it with one `dmas_beamform_batch` call: one launch
-    per kernel stage and variant for the whole batch,
-  * keeps up to `streams` batches in flight on separate CUDA streams, so
-    frames that arrive while earlier batches run are batched and overlap with
-    them on the GPU,
+    image and scratch (otherwise it waits in its lane's FIFO queue; a frame
+    that can never fit is rejected),
   * sorts frames into two lanes by their cost N * M * T: small frames go to a
     fast lane whose streams have high priority (the GPU schedules their CTAs
-    ahead of waiting CTAs of big frames) and are batched generously; big frames
-    go to a bulk lane in small batches, since batching them saves no launch
-    overhead worth having and a batch completes only when its last frame does,
+    ahead of waiting CTAs of big frames) and are batched generously (every
+    waiting small frame, up to `max_batch`, in one batch: one launch per
+    kernel stage and variant); big frames go one per batch to one
+    low-priority stream with `bulk_depth` batches queued on it, so they run
+    first in, first out while the small frames overtake them,
+  * uploads a batch's frames, runs it and records its completion event in one
+    library call, and notices completions by polling the events while
+    batches are in flight,
   * records, per frame, the time from its arrival to the completion of its
     batch on the device (the image is then resident in device memory; with
     `copy_back` the image is also copied to host memory first).
 
-The host threads only move pointers and events; every step of the
-beamforming path runs in the library's kernels.  Results do not depend on the
-batch a frame lands in: each entry uses its own scratch, so its image is
-bitwise identical to a `dmas_beamform` of that frame alone.
+Python only submits frames and collects completions: no interpreter lock sits
+between a frame's arrival and its launch.  Results do not depend on the batch
+a frame lands in: each entry uses its own scratch, so its image is bitwise
+identical to a `dmas_beamform` of that frame alone.
 """
 from __future__ import annotations
 
 import collections
+import ctypes
 import threading
 import time
 from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import beamform_batch_upload, batch_workspace_bytes
+from . import DmasError, load_library
 
 
 @dataclass
@@ -133,18 +134,6 @@ class PinnedPool:
             self.put(self._alloc(shape))
 
 
-class _Lane:
-    def __init__(self, name, streams, max_batch, depth=None):
-        self.name = name
-        self.streams = streams
-        self.max_batch = max_batch
-        # batches in flight at once (several may queue on one stream)
-        self.depth = len(streams) if depth is None else max(1, int(depth))
-        self.queue = collections.deque()
-        self.in_flight = 0
-        self.next_stream = 0
-
-
 @dataclass
 class Request:
     sensor: int
@@ -156,6 +145,7 @@ class Request:
     batch_size: int = 0
     image: object = None          # device tensor when keep_image, host tensor with copy_back
     rejected: bool = False
+    status: int = 0               # the library's status for this frame (0: done)
     done: threading.Event = field(default_factory=threading.Event)
 
     @property
@@ -163,61 +153,81 @@ class Request:
         return self.t_done - self.t_arrival
 
 
-class Server:
-    """fast_cost: frames with cost <= fast_cost use the fast lane (default:
-    about 0.5 ms of GPU work, 1.3e9 mic x direction x samples).  `streams`
-    is the fast lane's stream count, `bulk_streams` the bulk lane's (None:
-    the same), `bulk_depth` the big-frame batches in flight at once (None:
-    one per bulk stream; more queue on a stream, so the next big frame is
-    enqueued while the previous one runs); `bulk_batch` frames per bulk
-    batch.  Defaults measured on B300 with the 16-sensor mix at 200 frames/s:
-    one big frame per batch on one low-priority stream, two in flight, keeps
-    big frames first-in first-out as one stream does (three concurrent
-    streams stretched each big frame by the others' work: overall p99 +2 ms)
-    while the small frames overtake them on high-priority streams."""
+class _ServerDesc(ctypes.Structure):
+    _fields_ = [("n_plans", ctypes.c_int), ("plans", ctypes.c_void_p),
+                ("fast_cost", ctypes.c_double), ("fast_streams", ctypes.c_int),
+                ("max_batch", ctypes.c_int), ("bulk_depth", ctypes.c_int),
+                ("budget_bytes", ctypes.c_size_t)]
 
-    # the server thread's sleep between scans of the batches in flight
-    poll_s = 50e-6
+
+class _ServerDone(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("sensor", ctypes.c_int), ("status", ctypes.c_int),
+                ("batch_size", ctypes.c_int), ("t_arrival", ctypes.c_double),
+                ("t_admitted", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("d_image", ctypes.c_void_p)]
+
+
+class _DeviceImage:
+    """A device image the runtime handed over, exposed to torch through the
+    CUDA array interface; freed (ordered on the legacy default stream) when
+    the last tensor over it and this holder are gone."""
+
+    def __init__(self, lib, ptr: int, shape):
+        self._lib, self._ptr = lib, ptr
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f4",
+                                         "data": (ptr, False), "version": 2, "strides": None}
+
+    def __del__(self):
+        if self._ptr:
+            self._lib.dmas_server_image_free(ctypes.c_void_p(self._ptr), None)
+            self._ptr = 0
+
+
+_ETIMEOUT, _ENOMEM = 5, 2
+
+
+class Server:
+    """Serving through the library's native runtime (dmas_server_*).
+
+    fast_cost: frames with cost <= fast_cost use the fast lane (default:
+    about 0.5 ms of GPU work, 1.3e9 mic x direction x samples), `streams`
+    high-priority streams with one batch of up to `max_batch` frames in
+    flight on each; big frames take the bulk lane, one frame per batch on one
+    low-priority stream with up to `bulk_depth` batches queued on it.
+    Defaults measured on B300 with the 16-sensor mix at 200 frames/s: big
+    frames first in, first out, two in flight (three concurrent big-frame
+    streams stretched each big frame by the others' work: overall p99 +2 ms).
+    The runtime allocates each frame's image when it admits the frame; with
+    keep_image the completed request's `image` is that device tensor (freed
+    when the last reference goes), with `copy_back` a page-locked host buffer
+    from `pinned` that the image was copied into before the frame
+    completed."""
 
     def __init__(self, sensors, device=None, budget_bytes: int = 32 << 30,
                  max_batch: int = 64, streams: int = 2, copy_back: bool = False,
-                 fast_cost: float = FAST_COST, bulk_batch: int = 1,
-                 bulk_streams: int | None = 1, bulk_env_tile_cap: int = BULK_ENV_TILE_CAP,
-                 pinned: PinnedPool | None = None, bulk_depth: int | None = 2):
+                 fast_cost: float = FAST_COST, bulk_depth: int = 2,
+                 bulk_env_tile_cap: int = BULK_ENV_TILE_CAP, pinned: PinnedPool | None = None):
         import torch
         self.torch = torch
+        self.lib = load_library()
         self.sensors = list(sensors)
         self.device = torch.device("cuda") if device is None else torch.device(device)
         self.budget = int(budget_bytes)
+        self.max_batch = int(max_batch)
+        self.streams = int(streams)
+        self.bulk_depth = int(bulk_depth)
         self.copy_back = bool(copy_back)
         self.fast_cost = float(fast_cost)
-        lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream,
-                                                              "priority_range") else (0, -1)
-        n_fast = max(1, streams)
-        n_bulk = max(1, streams if bulk_streams is None else bulk_streams)
-        self.fast = _Lane("fast", [torch.cuda.Stream(device=self.device, priority=hi)
-                                   for _ in range(n_fast)], int(max_batch))
-        self.bulk = _Lane("bulk", [torch.cuda.Stream(device=self.device, priority=lo)
-                                   for _ in range(n_bulk)], max(1, int(bulk_batch)), bulk_depth)
-        self._cv = threading.Condition()
-        self._reserved = 0
-        self._inflight_q: collections.deque = collections.deque()
-        self._events: list = []      # completion events free for reuse
-        self._ws_bytes: dict = {}    # batch workspace bytes by sensor tuple
-        self._running = False
-        self._threads = []
-        self.batches = 0
-        self.completed: list[Request] = []
         self.pinned = pinned if pinned is not None else (PinnedPool() if copy_back else None)
         if copy_back:
             # page-locking takes milliseconds per gigabyte: hold enough host
-            # images now for the frames that can be in flight at once (the
-            # bulk lane's depth of big frames, small ones in the fast lane's
-            # batches), counted per sensor and pooled per shape
+            # images now for the frames that can be queued or in flight at
+            # once (a small frame's few, the bulk lane's depth plus the ones
+            # waiting for it), counted per sensor and pooled per shape
             want = collections.Counter()
             for sn in self.sensors:
                 small = sn.cost <= self.fast_cost
-                want[tuple(sn.image_shape)] += 4 if small else self.bulk.depth + 1
+                want[tuple(sn.image_shape)] += 4 if small else self.bulk_depth + 2
             for shape, n in want.items():
                 self.pinned.reserve(shape, n)
         # big frames' envelopes retire their CTAs every few tiles, so the fast
@@ -225,24 +235,44 @@ class Server:
         for sn in self.sensors:
             if sn.cost > self.fast_cost and hasattr(sn.plan, "set_envelope_tile_cap"):
                 sn.plan.set_envelope_tile_cap(bulk_env_tile_cap)
+        self._handle = ctypes.c_void_p()
+        self._cv = threading.Condition()
+        self._reqs: dict = {}          # ticket -> Request, until its completion is taken
+        self._running = False
+        self._waiter = None
+        self._batches = 0.0
+        self.completed: list[Request] = []
 
-    def _lane_of(self, sensor: int) -> _Lane:
-        return self.fast if self.sensors[sensor].cost <= self.fast_cost else self.bulk
+    @property
+    def batches(self) -> int:
+        """Batches completed (each frame counts 1 / its batch's size)."""
+        return int(round(self._batches))
 
     # -- lifecycle -------------------------------------------------------
     def start(self):
+        torch = self.torch
+        plans = (ctypes.c_void_p * len(self.sensors))(*[sn.plan.handle.value for sn in self.sensors])
+        desc = _ServerDesc(len(self.sensors), ctypes.cast(plans, ctypes.c_void_p), self.fast_cost,
+                           self.streams, self.max_batch, self.bulk_depth, self.budget)
+        with torch.cuda.device(self.device):
+            st = self.lib.dmas_server_create(ctypes.byref(desc), ctypes.byref(self._handle))
+        if st != 0:
+            raise DmasError(st, "dmas_server_create")
         self._running = True
-        self._threads = [threading.Thread(target=self._loop, daemon=True)]
-        for t in self._threads:
-            t.start()
+        self._waiter = threading.Thread(target=self._wait_loop, daemon=True)
+        self._waiter.start()
         return self
 
     def stop(self):
+        """Finish the frames submitted so far, then shut the runtime down."""
+        if not self._handle:
+            return
+        self.drain(600.0)
         with self._cv:
             self._running = False
-            self._cv.notify_all()
-        for t in self._threads:
-            t.join(timeout=60)
+        self._waiter.join(timeout=60)
+        self.lib.dmas_server_destroy(self._handle)
+        self._handle = ctypes.c_void_p()
 
     def __enter__(self):
         return self.start()
@@ -252,138 +282,74 @@ class Server:
 
     def submit(self, sensor: int, frame, t_arrival: float | None = None,
                keep_image: bool = False) -> Request:
+        """frame: host tensor [N][T] float32 (page-locked for an asynchronous
+        upload), kept unchanged until the request completes."""
+        torch = self.torch
+        sn = self.sensors[sensor]
+        if frame.device.type != "cpu" or not frame.is_contiguous() or \
+                frame.dtype != torch.float32 or tuple(frame.shape) != tuple(sn.frame_shape):
+            raise ValueError(f"frame must be a contiguous host float32 {tuple(sn.frame_shape)}")
         req = Request(sensor, frame, time.perf_counter() if t_arrival is None else t_arrival,
                       keep_image)
+        req._host = self.pinned.get(sn.image_shape) if self.copy_back else None
+        keep_device = keep_image and not self.copy_back
+        ticket = ctypes.c_uint64()
         with self._cv:
-            self._lane_of(sensor).queue.append(req)
-            self._cv.notify_all()
+            st = self.lib.dmas_server_submit(
+                self._handle, int(sensor), ctypes.c_void_p(frame.data_ptr()),
+                ctypes.c_void_p(req._host.data_ptr() if req._host is not None else 0),
+                int(keep_device), float(req.t_arrival), ctypes.byref(ticket))
+            if st != 0:
+                raise DmasError(st, "dmas_server_submit")
+            self._reqs[ticket.value] = req
         return req
 
     def drain(self, timeout: float = 600.0) -> bool:
+        """Wait until every submitted frame has completed."""
         end = time.perf_counter() + timeout
         with self._cv:
-            while (self.fast.queue or self.bulk.queue or self.fast.in_flight
-                   or self.bulk.in_flight):
+            while self._reqs:
                 left = end - time.perf_counter()
                 if left <= 0:
                     return False
                 self._cv.wait(timeout=min(left, 0.1))
         return True
 
-    # -- the server's thread: completion, admission and batching ------------
-    def _loop(self):
-        """One thread completes finished batches, admits queued frames and
-        launches batches: with no second thread to hand the interpreter lock
-        to, a launch is not kept waiting behind a completion poll."""
+    # -- completions ------------------------------------------------------
+    def _wait_loop(self):
+        """Take the runtime's completions (blocking in the library, outside the
+        interpreter lock) and fill in the requests."""
+        done = _ServerDone()
         while True:
-            self._reap()
+            st = self.lib.dmas_server_wait(self._handle, 0.05, ctypes.byref(done))
+            if st == _ETIMEOUT:
+                with self._cv:
+                    if not self._running and not self._reqs:
+                        return
+                continue
             with self._cv:
-                lane = next((ln for ln in (self.fast, self.bulk) if self._can_launch(ln)), None)
-                if lane is None:
-                    if not self._inflight_q and not self._running:
-                        return                      # stopped, nothing in flight
-                    # poll the batches in flight; otherwise sleep until a submit
-                    self._cv.wait(timeout=self.poll_s if self._inflight_q else 0.05)
-                    continue
-                batch = []
-                while lane.queue and len(batch) < lane.max_batch:
-                    req = lane.queue[0]
-                    need = self.sensors[req.sensor].device_bytes
-                    if need > self.budget:          # can never fit: reject
-                        lane.queue.popleft()
-                        req.rejected = True
-                        req.t_done = time.perf_counter()
-                        req.done.set()
-                        continue
-                    if self._reserved + need > self.budget:
-                        break
-                    lane.queue.popleft()
-                    self._reserved += need
-                    batch.append(req)
-                if not batch:
-                    continue
-                lane.in_flight += 1
-                stream = lane.streams[lane.next_stream]
-                lane.next_stream = (lane.next_stream + 1) % len(lane.streams)
-            now = time.perf_counter()
-            for r in batch:
-                r.t_admitted = now
-            self._launch(batch, stream, lane)
-
-    def _can_launch(self, lane) -> bool:
-        if not lane.queue or lane.in_flight >= lane.depth:
-            return False
-        head = self.sensors[lane.queue[0].sensor].device_bytes
-        return head > self.budget or self._reserved + head <= self.budget
-
-    def _event(self, stream):
-        """A completion event from the free list (created by one record)."""
-        if self._events:
-            return self._events.pop()
-        ev = self.torch.cuda.Event()
-        ev.record(stream)
-        return ev
-
-    def _launch(self, batch, stream, lane):
-        torch = self.torch
-        with torch.cuda.stream(stream):
-            plans = [self.sensors[r.sensor].plan for r in batch]
-            key = tuple(r.sensor for r in batch)
-            ws_bytes = self._ws_bytes.get(key)
-            if ws_bytes is None:
-                ws_bytes = self._ws_bytes[key] = batch_workspace_bytes(plans)
-            frames = [torch.empty((p.n_mics, p.n_samples), device=self.device) for p in plans]
-            images = [torch.empty((p.n_dirs, p.n_samples), device=self.device) for p in plans]
-            ws = torch.empty(ws_bytes, device=self.device, dtype=torch.uint8)
-            hosts = None
-            if self.copy_back:
-                ev = torch.cuda.Event()
-                beamform_batch_upload(plans, [r.frame for r in batch], frames, images, ws,
-                                      stream=stream)
-                hosts = [self.pinned.get(im.shape) for im in images]
-                for h, im in zip(hosts, images):
-                    _copy_in_pieces(h, im)
-                ev.record(stream)
-            else:
-                # uploads, the batch and its completion event in one library call
-                ev = self._event(stream)
-                beamform_batch_upload(plans, [r.frame for r in batch], frames, images, ws,
-                                      stream=stream, done_event=ev)
-        self.batches += 1
-        with self._cv:
-            self._inflight_q.append((ev, batch, frames, images, ws, hosts, lane))
-            self._cv.notify_all()
-
-    # -- completion: latency and memory release ----------------------------
-    def _reap(self):
-        """Every batch whose completion event has fired (fast lanes finish out
-        of order with the bulk lane): record its requests' latency, hand back
-        host buffers and release its share of the memory budget."""
-        with self._cv:
-            done = [x for x in self._inflight_q if x[0].query()]
-            for item in done:
-                self._inflight_q.remove(item)
-        if not done:
-            return
-        t = time.perf_counter()
-        for ev, batch, frames, images, ws, hosts, lane in done:
-            for k, r in enumerate(batch):
-                r.t_done = t
-                r.batch_size = len(batch)
-                if r.keep_image:
-                    r.image = hosts[k] if hosts is not None else images[k]
-                elif hosts is not None:
-                    self.pinned.put(hosts[k])
-        with self._cv:
-            for ev, batch, frames, images, ws, hosts, lane in done:
-                for r in batch:
-                    self._reserved -= self.sensors[r.sensor].device_bytes
-                    self.completed.append(r)
-                    r.done.set()
-                lane.in_flight -= 1
-                if hosts is None:
-                    self._events.append(ev)
-            self._cv.notify_all()
+                req = self._reqs.get(done.ticket)
+            if req is None:
+                continue
+            req.t_admitted = done.t_admitted
+            req.t_done = done.t_done
+            req.batch_size = done.batch_size
+            req.rejected = done.status == _ENOMEM
+            req.status = done.status
+            if done.d_image:
+                req._holder = _DeviceImage(self.lib, done.d_image, self.sensors[req.sensor].image_shape)
+                req.image = self.torch.as_tensor(req._holder, device=self.device)
+            elif req.keep_image and req._host is not None and done.status == 0:
+                req.image = req._host
+            elif req._host is not None:
+                self.pinned.put(req._host)
+            req._host = None
+            with self._cv:
+                del self._reqs[done.ticket]
+                self._batches += 1.0 / max(1, done.batch_size)
+                self.completed.append(req)
+                req.done.set()
+                self._cv.notify_all()
 
 
 def one_frame_per_launch(sensors, requests, device=None, copy_back: bool = False,

@@ -5,6 +5,7 @@ own scratch and the per-pixel arithmetic is the same, so the comparison with
 dmas_beamform of the frame alone is bitwise.
 """
 import functools
+import gc
 import time
 
 import numpy as np
@@ -119,6 +120,46 @@ def test_server_admission_by_memory_and_rejection():
         r = small.submit(0, host[0])
         assert small.drain(30.0)
     assert r.rejected
+    for s in sensors:
+        s.plan.close()
+
+
+def test_handed_over_image_lives_as_long_as_its_tensor():
+    """The server hands device images over through the CUDA array interface;
+    torch keeps the holder (whose finaliser frees the image) alive for as long
+    as a tensor over it exists."""
+    class Holder:
+        freed = False
+
+        def __init__(self, t):
+            self.t = t
+            self.__cuda_array_interface__ = t.__cuda_array_interface__
+
+        def __del__(self):
+            Holder.freed = True
+
+    h = Holder(torch.zeros(4, device="cuda"))
+    x = torch.as_tensor(h, device="cuda")
+    del h
+    gc.collect()
+    assert not Holder.freed
+    del x
+    gc.collect()
+    assert Holder.freed
+
+
+def test_server_images_outlive_the_server():
+    mix = _small_mix()
+    sensors = _sensors(mix)
+    host = [torch.from_numpy(s.frames[0]).pin_memory() for s in mix]
+    with serving.Server(sensors, streams=2) as srv:
+        reqs = [srv.submit(k, host[k], keep_image=True) for k in range(len(mix))]
+        assert srv.drain(60.0)
+    images = [r.image for r in reqs]
+    del reqs, srv
+    gc.collect()
+    for k, im in enumerate(images):
+        assert torch.equal(im, sensors[k].plan(host[k].cuda()))
     for s in sensors:
         s.plan.close()
 
