@@ -49,16 +49,23 @@
 // warp roles: a producer stages each k-block of 64 samples of y by TMA (2-D
 // tensor map, two boxes of 32 samples x 128 rows; cp.async to the same layout
 // when T % 4 != 0) into one of n_stages shared-memory stages (up to
-// kTcStages: as many as fit beside the taps); 4 split warps
-// (one row per thread, the warp's TMEM lane quarter) read |y| rounded to TF32
-// and the remainder and store them (tcgen05.st) into one of two A stages in
-// TMEM (hi, lo: 2 x 64 columns); four MMA warps (one block or phase each)
-// issue the k-block's k-steps x 3 MMAs into one of two accumulators (J columns)
-// and commit them to the A stage's and, after a tile's last k-block, the
-// accumulator's mbarrier; 4 epilogue warps read their row of a finished
-// accumulator (TMEM lane = row) and store 8 consecutive outputs (one 32-byte
-// sector) at a time while the next tile accumulates into the other.  TMEM:
-// accumulators from column 0, A stages after them.  Every wait is bounded.
+// kTcStages: as many as fit beside the tap operand); 4 split warps (one row
+// per thread, the warp's TMEM lane quarter) read |y| rounded to TF32 and the
+// remainder and store them (tcgen05.st) into an A stage in TMEM (hi, lo:
+// 2 x 64 columns); four MMA warps (one block or phase each) issue the
+// k-block's k-steps x 3 MMAs and commit them to the A stage's mbarrier.
+//  * Toeplitz form: one accumulator (J columns from column 0) with a full and
+//    an empty barrier per block, three A stages after it.  A block's warp
+//    commits its block's full barrier after the block's last k-step; the
+//    epilogue reads the block's 32 columns, hands them back (empty barrier),
+//    writes the row's 32 outputs into a 128-byte swizzled shared-memory buffer
+//    and one thread stores the 32 x 128 box with a tensor store (two buffers
+//    alternate; a buffer is rewritten only after its store has read it).
+//  * Phase form: two accumulators (2 x J columns), two A stages after them;
+//    the epilogue reads a finished accumulator while the next tile
+//    accumulates into the other and stores 8 consecutive outputs (one 32-byte
+//    sector) at a time.
+// Every wait is bounded.
 #pragma once
 
 #include <cuda.h>
