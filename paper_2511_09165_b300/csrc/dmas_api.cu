@@ -96,7 +96,7 @@ struct dmas_plan {
     HostPlan hp;
     int device = 0;
     int *d_gdir = nullptr, *d_gws = nullptr, *d_rel = nullptr, *d_sel = nullptr;
-    float *d_frac = nullptr, *d_w4 = nullptr;
+    float *d_frac = nullptr, *d_wf2 = nullptr;
     unsigned *d_err = nullptr;
     void *d_scratch = nullptr;        // root channels (+ y buffer with the envelope)
     size_t chan_bytes = 0, ybuf_bytes = 0, table_bytes = 0;
@@ -164,7 +164,7 @@ void free_plan_memory(dmas_plan *p) {
     cudaFree(p->d_rel);
     cudaFree(p->d_frac);
     cudaFree(p->d_sel);
-    cudaFree(p->d_w4);
+    cudaFree(p->d_wf2);
     cudaFree(p->d_err);
     cudaFree(p->d_scratch);
     cudaFree(p->d_io_frame);
@@ -189,7 +189,7 @@ void free_plan_memory(dmas_plan *p) {
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
     p->copy_stream = nullptr;
     p->d_gdir = p->d_gws = p->d_rel = p->d_sel = nullptr;
-    p->d_frac = p->d_w4 = nullptr;
+    p->d_frac = p->d_wf2 = nullptr;
     p->d_err = nullptr;
     p->d_scratch = nullptr;
     p->d_io_frame = p->d_io_image = nullptr;
@@ -511,7 +511,7 @@ BeamParams beam_params(const dmas_plan *p, void *scratch, float *ybuf, float *d_
     bp.rel = p->d_rel;
     bp.frac = p->d_frac;
     bp.sel = p->d_sel;
-    bp.w4 = p->d_w4;
+    bp.wf2 = p->d_wf2;
     bp.y = ybuf;
     bp.cf = d_cf;
     bp.err = p->d_err;
@@ -982,7 +982,7 @@ dmas_status enqueue_orders(dmas_plan *p, const float *d_frame, unsigned mask, in
     op.gdir = p->d_gdir;
     op.gws = p->d_gws;
     op.rel = p->d_rel;
-    op.w4 = p->d_w4;
+    op.wf2 = p->d_wf2;
     op.y = ybuf;
     op.img = img;
     op.cf = d_cf;
@@ -1088,7 +1088,7 @@ dmas_status dmas_plan_create(const dmas_plan_desc *desc, dmas_plan **out) {
         (e = upload(&p->d_rel, hp.rel)) != cudaSuccess ||
         (e = upload(&p->d_frac, hp.gfrac)) != cudaSuccess ||
         (e = upload(&p->d_sel, hp.gsel)) != cudaSuccess ||
-        (e = upload(&p->d_w4, hp.gw4)) != cudaSuccess) {
+        (e = upload(&p->d_wf2, hp.gwf2)) != cudaSuccess) {
         free_plan_memory(p);
         delete p;
         cudaGetLastError();
@@ -1112,7 +1112,7 @@ dmas_status dmas_plan_create(const dmas_plan_desc *desc, dmas_plan **out) {
         }
     }
     p->table_bytes = (hp.gdir.size() + hp.gws.size() + hp.rel.size() + hp.gfrac.size() +
-                      hp.gsel.size() + hp.gw4.size()) * 4;
+                      hp.gsel.size() + hp.gwf2.size()) * 4;
     // the interpolated-delay pair kernel also reads every root row shifted by
     // one sample
     p->chan_bytes = (size_t)hp.N * hp.row * chan_elem_bytes(hp.chan_prec) *

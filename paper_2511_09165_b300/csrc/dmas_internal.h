@@ -48,9 +48,9 @@ struct HostPlan {
     std::vector<float> gfrac;   // [n_groups][N][kGroup] interpolation weight f
     // interpolated-delay pair kernel: byte offset, from the staged windows'
     // base, of lane 0's first pixel pair (window as is for an even shift, the
-    // shifted window for an odd one), and the weights {1 - f, 1 - f, f, f}
+    // shifted window for an odd one), and the weight f twice (one packed operand)
     std::vector<int32_t> gsel;  // [n_groups][N][kGroup]
-    std::vector<float> gw4;     // [n_groups][N][kGroup][4]
+    std::vector<float> gwf2;    // [n_groups][N][kGroup][2] {f, f}
 
     int window = 0;      // staged samples per microphone row (multiple of kAlign)
     int mic_chunk = 0;   // microphones staged per pass
@@ -100,7 +100,7 @@ inline size_t pair_stage_bytes(int mic_chunk, int window) {
 // by one sample; its CTA stages, per microphone, one 128-byte aligned block
 // holding the window as is and then shifted (lin_mic_bytes), and per
 // microphone and direction the shift (int), the pair offset (int) and the
-// weights (4 floats).
+// weight f twice (2 floats).
 inline bool uses_shifted_rows(int chan_prec, int order, int delay_mode) {
     return uses_pair_kernel(chan_prec, order) && delay_mode == DMAS_DELAY_LINEAR;
 }
@@ -108,7 +108,7 @@ inline size_t lin_mic_bytes(int window) { return ((size_t)2 * window * 4 + 127) 
 // The CTA also keeps per-lane partial sums of the sample past its tile
 // (8 warps x up to 6 sums x 32 lanes).
 inline size_t lin_pair_smem_bytes(int mic_chunk, int window) {
-    return 128 + (size_t)mic_chunk * lin_mic_bytes(window) + (size_t)mic_chunk * kGroup * 24 +
+    return 128 + (size_t)mic_chunk * lin_mic_bytes(window) + (size_t)mic_chunk * kGroup * 16 +
            8 * 6 * 32 * 4;
 }
 // Largest window one tensor copy (box dimension <= 256) stages.
@@ -116,7 +116,7 @@ constexpr int kTmaMaxBox = 256;
 
 // Every-order pass (dmas_beamform_orders): one microphone's staged block
 // (its plane rows), padded to 128 bytes; one staging buffer (mic_chunk blocks,
-// the chunk's shift table and, interpolated, its {1-f, 1-f, f, f} table); the
+// the chunk's shift table and, interpolated, its {f, f} weight table); the
 // CTA's dynamic shared memory: barrier slot, two staging buffers and, for
 // interpolated delays, the per-lane sums of the sample past the tile.
 constexpr int kOrdersMaxOrder = 5;  // highest order of the every-order pass
@@ -130,7 +130,7 @@ inline size_t orders_mic_bytes(int nmax, int window) {
 }
 inline size_t orders_stage_bytes(int nmax, bool lin, int mic_chunk, int window) {
     return ((size_t)mic_chunk * orders_mic_bytes(nmax, window) + (size_t)mic_chunk * kGroup * 4 +
-            (lin ? (size_t)mic_chunk * kGroup * 16 : 0) + 127) & ~(size_t)127;
+            (lin ? (size_t)mic_chunk * kGroup * 8 : 0) + 127) & ~(size_t)127;
 }
 inline size_t orders_smem_bytes(int nmax, bool lin, int mic_chunk, int window) {
     return 128 + 2 * orders_stage_bytes(nmax, lin, mic_chunk, window) +

@@ -535,7 +535,7 @@ struct BeamParams {
     const int *rel;      // [n_groups][N][8] shift relative to window start
     const float *frac;   // [n_groups][N][8] interpolation weight (LINEAR)
     const int *sel;      // LINEAR pair kernel: [n_groups][N][8] byte offset of lane 0's pair
-    const float *w4;     // LINEAR pair kernel: [n_groups][N][8][4] {1-f, 1-f, f, f}
+    const float *wf2;    // LINEAR pair kernel: [n_groups][N][8][2] {f, f}, the later sample's weight
     float *y;            // [M][T] E_n (x CF)
     float *cf;           // [M][T] or nullptr
     unsigned *err;       // error word
@@ -881,9 +881,9 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
     float *win = reinterpret_cast<float *>(smem + 128);
     int *s_rel = reinterpret_cast<int *>(smem + 128 + NC * MBf * 4);
     int *s_sel = s_rel + NC * 8;
-    float *s_w4 = reinterpret_cast<float *>(s_sel + NC * 8);
+    float *s_wf = reinterpret_cast<float *>(s_sel + NC * 8);
     // per-lane partial sums of the sample past the tile: [warp][q][lane]
-    float *s_vext = s_w4 + NC * 32 + ((threadIdx.x >> 5) * NA * 32 + (threadIdx.x & 31));
+    float *s_vext = s_wf + NC * 16 + ((threadIdx.x >> 5) * NA * 32 + (threadIdx.x & 31));
 
     const unsigned item = block + p.item0;
     const int tile = (int)(item / (unsigned)p.n_groups);
@@ -930,17 +930,17 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
             if (warp + 8 * lane < nc) x_first = gws[c0 + warp + 8 * lane];
         }
         if (threadIdx.x == 0) {
-            mbar_arrive_expect_tx(bar, 2 * nc * row_bytes + 6 * tab_bytes);
+            mbar_arrive_expect_tx(bar, 2 * nc * row_bytes + 4 * tab_bytes);
             const size_t to = ((size_t)g * p.N + c0) * 8;
             if (checked_ok(((size_t)g * p.N + c0 + nc) <= (size_t)p.n_groups * p.N &&
                                smem_in(s_rel, tab_bytes) && smem_in(s_sel, tab_bytes) &&
-                               smem_in(s_w4, 4 * tab_bytes),
+                               smem_in(s_wf, 2 * tab_bytes),
                            p.err)) {
                 bulk_g2s(s_rel, p.rel + to, tab_bytes, bar);
                 bulk_g2s(s_sel, p.sel + to, tab_bytes, bar);
-                bulk_g2s(s_w4, p.w4 + to * 4, 4 * tab_bytes, bar);
+                bulk_g2s(s_wf, p.wf2 + to * 2, 2 * tab_bytes, bar);
             } else {
-                mbar_complete_tx_local(bar, 6 * tab_bytes);
+                mbar_complete_tx_local(bar, 4 * tab_bytes);
             }
         }
         __syncthreads();  // the byte count is set before any copy can land
@@ -972,21 +972,20 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
         // (x, x+1), x = off + 2l + 64k: at x in copy 0 (even off) or at x - 1
         // in copy 1 (odd off); s_sel holds that byte offset for lane 0, k = 0
         // 32-bit shared addresses (0.9 % faster than generic pointers, measured):
-        // lane l's pairs, and the weight {f, f} (the upper half of the entry
-        // {1-f, 1-f, f, f})
+        // lane l's pairs, and the weight {f, f} of the direction's entry
         const uint32_t base = smem_addr(win) + 8 * lane;
-        const uint32_t wq = smem_addr(s_w4) + 16 * warp + 8;
+        const uint32_t wq = smem_addr(s_wf) + 8 * warp;
 #pragma unroll 4
         for (int il = 0; il < nc; ++il) {
             const uint32_t a = base + (uint32_t)s_sel[il * 8 + warp];
             if constexpr (kChecked) {  // the lane's pairs inside microphone il's block
                 const uint32_t blk = smem_addr(win) + (uint32_t)(il * MBf * 4);
                 if (!checked_ok(a >= blk && a + 256 * (kPairs - 1) + 8 <= blk + MBf * 4 &&
-                                    smem_in(wq + 128 * il, 8),
+                                    smem_in(wq + 64 * il, 8),
                                 p.err))
                     continue;
             }
-            const f32x2_t wf = lds_f32x2(wq + 128 * il);
+            const f32x2_t wf = lds_f32x2(wq + 64 * il);
 #pragma unroll
             for (int k = 0; k < kPairs; ++k)
                 accumulate2_sv<ORDER>(acc[k], vac[k], lds_f32x2(a + 256 * k), wf);
@@ -1000,7 +999,7 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
             for (int il = lane; il < nc; il += 32) {
                 const int o = s_rel[il * 8 + warp] + kTile;
                 if (checked_ok(o >= 0 && o < WS, p.err))
-                    accumulate_v<ORDER>(ve, win[il * MBf + o], s_w4[(il * 8 + warp) * 4 + 2]);
+                    accumulate_v<ORDER>(ve, win[il * MBf + o], s_wf[(il * 8 + warp) * 2]);
             }
 #pragma unroll
             for (int q = 0; q < NA; ++q) s_vext[q * 32] = ve[q];

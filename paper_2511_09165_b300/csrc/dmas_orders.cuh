@@ -85,7 +85,7 @@ struct OrdersParams {
     const int *gdir;    // [n_groups * 8] direction index or -1
     const int *gws;     // [n_groups][N] window start relative to t0
     const int *rel;     // [n_groups][N][8] shift relative to the window start
-    const float *w4;    // [n_groups][N][8][4] {1 - f, 1 - f, f, f} (interpolated delays)
+    const float *wf2;   // [n_groups][N][8][2] {f, f} (interpolated delays)
     float *y;           // images [n_images][M][T]
     size_t img;         // elements from one image to the next (M * T)
     float *cf;          // [M][T] or nullptr
@@ -107,7 +107,7 @@ __device__ __forceinline__ int orders_mic_bytes_dev(int planes, int window) {
 __device__ __forceinline__ int orders_stage_bytes_dev(int planes, bool lin, int mic_chunk,
                                                       int window) {
     return (mic_chunk * orders_mic_bytes_dev(planes, window) + mic_chunk * 32 +
-            (lin ? mic_chunk * 128 : 0) + 127) & ~127;
+            (lin ? mic_chunk * 64 : 0) + 127) & ~127;
 }
 
 constexpr unsigned long long kAbsMask2 = 0x7fffffff7fffffffull;
@@ -290,21 +290,21 @@ __global__ void __launch_bounds__(kThreads, 2)
     auto stage_head = [&](int ci) {
         unsigned char *bb = smem + 128 + (ci & 1) * SB;
         int *rel = reinterpret_cast<int *>(reinterpret_cast<float *>(bb) + NC * MB);
-        float *w4 = reinterpret_cast<float *>(rel + NC * 8);
+        float *wf = reinterpret_cast<float *>(rel + NC * 8);
         const int c0 = ci * NC;
         const int nc = min(NC, p.N - c0);
         const uint32_t row_bytes = (uint32_t)(WS * 4);
         const uint32_t tab_bytes = (uint32_t)(nc * 8 * 4);
         mbar_arrive_expect_tx(&bar[ci & 1], (uint32_t)NP * nc * row_bytes + tab_bytes +
-                                                (LINEAR ? 4u * tab_bytes : 0u));
+                                                (LINEAR ? 2u * tab_bytes : 0u));
         const size_t to = ((size_t)g * p.N + c0) * 8;
         if (checked_ok(((size_t)g * p.N + c0 + nc) <= (size_t)p.n_groups * p.N &&
-                           smem_in(rel, tab_bytes) && (!LINEAR || smem_in(w4, 4 * tab_bytes)),
+                           smem_in(rel, tab_bytes) && (!LINEAR || smem_in(wf, 2 * tab_bytes)),
                        p.err)) {
             bulk_g2s(rel, p.rel + to, tab_bytes, &bar[ci & 1]);
-            if (LINEAR) bulk_g2s(w4, p.w4 + to * 4, 4 * tab_bytes, &bar[ci & 1]);
+            if (LINEAR) bulk_g2s(wf, p.wf2 + to * 2, 2 * tab_bytes, &bar[ci & 1]);
         } else {
-            mbar_complete_tx_local(&bar[ci & 1], tab_bytes * (LINEAR ? 5u : 1u));
+            mbar_complete_tx_local(&bar[ci & 1], tab_bytes * (LINEAR ? 3u : 1u));
         }
     };
     auto window_start = [&](int ci) -> int {
@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const unsigned char *bb = smem + 128 + b * SB;
         const float *win = reinterpret_cast<const float *>(bb);
         const int *s_rel = reinterpret_cast<const int *>(win + NC * MB);
-        const float *s_w4 = reinterpret_cast<const float *>(s_rel + NC * 8);
+        const float *s_wf = reinterpret_cast<const float *>(s_rel + NC * 8);
         const int nc = min(NC, p.N - ci * NC);
 
 #pragma unroll 4
@@ -387,9 +387,9 @@ __global__ void __launch_bounds__(kThreads, 2)
             const float *r = win + il * MB + off + lane;
             if (!checked_ok(off >= 0 && off + 31 + 64 * (kPairs - 1) + 32 < WS, p.err)) continue;
             if constexpr (LINEAR) {
-                // {f, f}: the upper half of the entry {1-f, 1-f, f, f}
+                // the weight {f, f} of the direction's entry
                 const f32x2_t wf =
-                    reinterpret_cast<const f32x2_t *>(s_w4)[(il * 8 + warp) * 2 + 1];
+                    reinterpret_cast<const f32x2_t *>(s_wf)[il * 8 + warp];
                 f32x2_t st[NP], s[NMAX];
 #pragma unroll
                 for (int q = 0; q < NP; ++q) st[q] = f2_pack(r[q * WS], r[q * WS + 32]);
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
                     for (int q = 0; q < NP; ++q) st[q] = r[q * WS];
                     expand_roots<NMAX>(st, sv);
-                    accumulate_orders_v<NMAX>(ve, sv, s_w4[(il * 8 + warp) * 4 + 2]);
+                    accumulate_orders_v<NMAX>(ve, sv, s_wf[(il * 8 + warp) * 2]);
                 }
 #pragma unroll
                 for (int q = 0; q < NA; ++q) s_vext[q * 32] = ve[q];

@@ -300,7 +300,7 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
                                      : kWindowSmemBudget - (pair ? 8 * 6 * 32 * 4 : 0);
     const size_t tab = (size_t)kGroup * 4 * (lin ? 2 : 1);
     const size_t per_mic = persistent ? 2 * ((size_t)window * eb + tab)
-                                      : (pair ? lin_mic_bytes((int)window) + (size_t)kGroup * 24
+                                      : (pair ? lin_mic_bytes((int)window) + (size_t)kGroup * 16
                                               : (size_t)window * eb + tab);
     if (per_mic > budget)
         return fail("a direction group's delay spread does not fit in shared memory");
@@ -313,7 +313,7 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
     if (pair && lin) {
         const size_t mb = lin_mic_bytes(hp.window);
         hp.gsel.assign(hp.rel.size(), 0);
-        hp.gw4.assign(hp.rel.size() * 4, 0.0f);
+        hp.gwf2.assign(hp.rel.size() * 2, 0.0f);
         for (int g = 0; g < G; ++g)
             for (int i = 0; i < N; ++i)
                 for (int s = 0; s < kGroup; ++s) {
@@ -324,10 +324,8 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
                                                                   (size_t)(off - 1) * 4
                                                             : (size_t)off * 4));
                     const float f = hp.gfrac[o];
-                    hp.gw4[o * 4 + 0] = 1.0f - f;
-                    hp.gw4[o * 4 + 1] = 1.0f - f;
-                    hp.gw4[o * 4 + 2] = f;
-                    hp.gw4[o * 4 + 3] = f;
+                    hp.gwf2[o * 2 + 0] = f;
+                    hp.gwf2[o * 2 + 1] = f;
                 }
     }
     hp.spread = (int)spread;
