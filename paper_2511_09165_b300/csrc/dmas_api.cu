@@ -209,7 +209,7 @@ size_t beam_smem_bytes(const HostPlan &hp) {
     const size_t eb = chan_elem_bytes(hp.chan_prec);
     const size_t win = ((size_t)hp.mic_chunk * hp.window * eb + 127) & ~(size_t)127;
     const size_t tabs = (size_t)hp.mic_chunk * kGroup * 4 * (hp.delay_mode ? 2 : 1);
-    if (uses_shifted_rows(hp.chan_prec, hp.order, hp.delay_mode))  // window and shifted window
+    if (uses_raw_rows(hp.chan_prec, hp.order, hp.delay_mode))  // root and raw-sample windows
         return lin_pair_smem_bytes(hp.mic_chunk, hp.window);
     if (uses_pair_kernel(hp.chan_prec, hp.order))  // persistent: two staging buffers
         return 128 + 2 * pair_stage_bytes(hp.mic_chunk, hp.window);
@@ -455,7 +455,7 @@ RootsParams roots_params(const dmas_plan *p, const float *d_frame, void *scratch
     rp.frame = d_frame;
     rp.chan = scratch;
     rp.work = work_counter(p, scratch);
-    rp.shifted = uses_shifted_rows(hp.chan_prec, hp.order, hp.delay_mode) ? 1 : 0;
+    rp.raw = uses_raw_rows(hp.chan_prec, hp.order, hp.delay_mode) ? 1 : 0;
     rp.N = hp.N;
     rp.T = hp.T;
     rp.row = hp.row;
@@ -482,13 +482,13 @@ BeamParams beam_params(const dmas_plan *p, void *scratch, float *ybuf, float *d_
     BeamParams bp;
     std::memset(&bp, 0, sizeof(bp));
     bp.use_tma = 0;
-    if (uses_shifted_rows(hp.chan_prec, hp.order, hp.delay_mode) && hp.window <= kTmaMaxBox) {
+    if (uses_raw_rows(hp.chan_prec, hp.order, hp.delay_mode) && hp.window <= kTmaMaxBox) {
         std::lock_guard<std::mutex> lock(p->map_mu);
         if (p->beam_map_ptr == scratch) {
             bp.tmap = p->beam_map;
             bp.use_tma = 1;
         } else if (EncodeTiledFn enc = encode_tiled()) {
-            // root rows [N][row], then their shifted copies: one box per
+            // root rows [N][row], then the raw sample rows: one box per
             // microphone, its window in both
             cuuint64_t dims[3] = {(cuuint64_t)hp.row, (cuuint64_t)hp.N, 2};
             cuuint64_t strides[2] = {(cuuint64_t)hp.row * 4, (cuuint64_t)hp.N * hp.row * 4};
@@ -1113,10 +1113,10 @@ dmas_status dmas_plan_create(const dmas_plan_desc *desc, dmas_plan **out) {
     }
     p->table_bytes = (hp.gdir.size() + hp.gws.size() + hp.rel.size() + hp.gfrac.size() +
                       hp.gsel.size() + hp.gwf2.size()) * 4;
-    // the interpolated-delay pair kernel also reads every root row shifted by
-    // one sample
+    // the interpolated-delay pair kernel also reads the raw samples as a
+    // second zero-padded plane
     p->chan_bytes = (size_t)hp.N * hp.row * chan_elem_bytes(hp.chan_prec) *
-                    (uses_shifted_rows(hp.chan_prec, hp.order, hp.delay_mode) ? 2 : 1);
+                    (uses_raw_rows(hp.chan_prec, hp.order, hp.delay_mode) ? 2 : 1);
     p->ybuf_bytes = hp.L > 0 ? sizeof(float) * (size_t)hp.M * hp.T : 0;
     p->mf_bytes = hp.mf.empty() ? 0 : sizeof(float) * (size_t)hp.N * hp.T;
     if (!hp.mf.empty() && (e = upload(&p->d_mf, hp.mf)) != cudaSuccess) {

@@ -47,8 +47,8 @@ struct HostPlan {
     std::vector<int32_t> rel;   // [n_groups][N][kGroup] shift - window start
     std::vector<float> gfrac;   // [n_groups][N][kGroup] interpolation weight f
     // interpolated-delay pair kernel: byte offset, from the staged windows'
-    // base, of lane 0's first pixel pair (window as is for an even shift, the
-    // shifted window for an odd one), and the weight f twice (one packed operand)
+    // base, of the direction's staged sample for pixel t0 (its microphone's
+    // block + 4 x rel), and the weight f twice (one packed operand)
     std::vector<int32_t> gsel;  // [n_groups][N][kGroup]
     std::vector<float> gwf2;    // [n_groups][N][kGroup][2] {f, f}
 
@@ -96,19 +96,19 @@ inline size_t pair_stage_bytes(int mic_chunk, int window) {
     return (pair_window_bytes(mic_chunk, window) + (size_t)mic_chunk * kGroup * 4 + 127) &
            ~(size_t)127;
 }
-// Pair kernel with interpolated delays: its root rows are also stored shifted
-// by one sample; its CTA stages, per microphone, one 128-byte aligned block
-// holding the window as is and then shifted (lin_mic_bytes), and per
-// microphone and direction the shift (int), the pair offset (int) and the
-// weight f twice (2 floats).
-inline bool uses_shifted_rows(int chan_prec, int order, int delay_mode) {
+// Pair kernel with interpolated delays: beside the root rows the roots kernel
+// writes the raw samples as a second plane; its CTA stages, per microphone,
+// one 128-byte aligned block holding the root window and then the raw-sample
+// window (lin_mic_bytes), and per microphone and direction the byte offset of
+// its first staged sample (int) and the weight f twice (2 floats).
+inline bool uses_raw_rows(int chan_prec, int order, int delay_mode) {
     return uses_pair_kernel(chan_prec, order) && delay_mode == DMAS_DELAY_LINEAR;
 }
 inline size_t lin_mic_bytes(int window) { return ((size_t)2 * window * 4 + 127) & ~(size_t)127; }
 // The CTA also keeps per-lane partial sums of the sample past its tile
 // (8 warps x up to 6 sums x 32 lanes).
 inline size_t lin_pair_smem_bytes(int mic_chunk, int window) {
-    return 128 + (size_t)mic_chunk * lin_mic_bytes(window) + (size_t)mic_chunk * kGroup * 16 +
+    return 128 + (size_t)mic_chunk * lin_mic_bytes(window) + (size_t)mic_chunk * kGroup * 12 +
            8 * 6 * 32 * 4;
 }
 // Largest window one tensor copy (box dimension <= 256) stages.

@@ -215,10 +215,10 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_ch<__nv_bfloat16>(float 
 // ---------------------------------------------------------------------------
 struct RootsParams {
     const float *frame;  // [N][T]
-    void *chan;          // [N][row] CH, then (shifted != 0) [N][row] shifted by one sample
+    void *chan;          // [N][row] CH, then (raw != 0) [N][row] the raw samples
     unsigned *work;      // the frame's beamform work counters [kWorkSlots]: set to zero
     int N, T, row, padl, order;
-    int shifted;         // also write chan1[i][c] = chan0[i][c + 1] after the first block
+    int raw;             // also write chan1[i][c] = m, the sample the root is taken of
     float inv_order;
 };
 
@@ -240,13 +240,9 @@ __device__ __forceinline__ void roots_body(const RootsParams &p, size_t first, s
         const int i = (int)(idx / (size_t)p.row);
         const int c = (int)(idx - (size_t)i * p.row);
         const int t = c - p.padl;
-        float r = 0.0f;
-        if (t >= 0 && t < p.T) r = signed_root(p.frame[(size_t)i * p.T + t], p.order, p.inv_order);
-        chan[idx] = to_ch<CH>(r);
-        if (p.shifted) {  // chan1[i][c - 1] = chan0[i][c]; the row's last sample is 0
-            if (c > 0) chan[total + idx - 1] = to_ch<CH>(r);
-            if (c == p.row - 1) chan[total + idx] = to_ch<CH>(0.0f);
-        }
+        const float m = (t >= 0 && t < p.T) ? p.frame[(size_t)i * p.T + t] : 0.0f;
+        chan[idx] = to_ch<CH>(signed_root(m, p.order, p.inv_order));
+        if (p.raw) chan[total + idx] = to_ch<CH>(m);
     }
 }
 
@@ -525,8 +521,8 @@ __device__ __forceinline__ float cf_ratio(float A, float B, float n_mics, float 
 }
 
 struct BeamParams {
-    // interpolated-delay pair kernel: 3-D view of the root rows and their
-    // shifted copies, dims (row, N, 2), box (window, 1, 2): one tensor copy
+    // interpolated-delay pair kernel: 3-D view of the root rows and the raw
+    // sample rows, dims (row, N, 2), box (window, 1, 2): one tensor copy
     // stages both windows of a microphone; valid when use_tma != 0
     CUtensorMap tmap;
     const void *chan;    // [N][row] roots, zero padded
@@ -534,7 +530,8 @@ struct BeamParams {
     const int *gws;      // [n_groups][N] window start relative to t0
     const int *rel;      // [n_groups][N][8] shift relative to window start
     const float *frac;   // [n_groups][N][8] interpolation weight (LINEAR)
-    const int *sel;      // LINEAR pair kernel: [n_groups][N][8] byte offset of lane 0's pair
+    const int *sel;      // LINEAR pair kernel: [n_groups][N][8] byte offset of the staged
+                         // sample of pixel t0 (the microphone's block + 4 x rel)
     const float *wf2;    // LINEAR pair kernel: [n_groups][N][8][2] {f, f}, the later sample's weight
     float *y;            // [M][T] E_n (x CF)
     float *cf;           // [M][T] or nullptr
@@ -712,13 +709,11 @@ __device__ __forceinline__ void beamform_body(const BeamParams &p, unsigned bloc
 //  * nearest-sample delays (beamform_x2_run): persistent, lane l and pair k
 //    take samples t0 + l + 64k and t0 + l + 32 + 64k, each half loaded by a
 //    conflict-free 32-lane shared load;
-//  * interpolated delays (beamform_x2_lin_body): one work item per CTA, lane l
-//    and pair k take the neighbours t = t0 + 2l + 64k and t + 1, fetched by
-//    one 8-byte shared load straight into the 64-bit register the packed
-//    instructions read.  That load must be 8-byte aligned but t + shift may be
-//    odd, so the roots kernel also writes every channel row shifted by one
-//    sample (chan1[x] = chan0[x + 1]); both windows are staged, and each pair
-//    is read from the copy in which it starts at an even index.
+//  * interpolated delays (beamform_x2_lin_body): one work item per CTA, the
+//    same lane layout; the roots kernel also writes the raw samples m as a
+//    second zero-padded plane (chan1), and both windows of a microphone are
+//    staged, so the loop takes x = m and x^2 from m instead of forming them
+//    from the root.
 // ---------------------------------------------------------------------------
 typedef unsigned long long f32x2_t;
 
@@ -816,55 +811,91 @@ __device__ __forceinline__ void accumulate2_plain(f32x2_t (&a)[SumLayout<ORDER>:
 //   S[t] = sum_i p(x_i(t)),   V[t] = sum_i f_i p(x_i(t)),
 // both summed over the SAME samples, the interpolated sum is
 // S[t] - V[t] + V[t + 1]: each staged sample's powers are formed once, added
-// plain (FADD2) and f-weighted (FFMA2), and the loop needs only the weight
-// {f, f}.  (Keeping U[t] = sum (1 - f) p instead of S takes the same number of
-// instructions but twice the weight registers per microphone in flight:
-// measured on B300 at 80 registers, the 32-microphone, 2048 x 16384 frame
-// beamforms in 0.78 against 0.73 ms.)
+// plain and f-weighted, and the loop needs only the weight {f, f}.  (Keeping
+// U[t] = sum (1 - f) p instead of S takes the same number of instructions but
+// twice the weight registers per microphone in flight: measured on B300 at 80
+// registers, the 32-microphone, 2048 x 16384 frame beamforms in 0.78 against
+// 0.73 ms.)
+//
+// The kernel stages two planes per microphone, the root s and the raw sample
+// m, so x = m (for odd n, s^n; for even n, |m| = s^n) and x^2 need no powers
+// of s: per pixel pair and microphone, n = 5 forms s^2, f s^2 and f m
+// (FMUL2) and takes
+//   P_1 += s, P_2 += s^2, P_3 += s^2 s, P_4 += s^2 s^2, A += m, B += m m,
+//   V_1 += f s, V_2 += f s^2, V_3 += (f s^2) s, V_4 += (f s^2) s^2,
+//   V_A += f m, V_B += (f m) m,
+// 15 packed instructions against 17 when x and every power of s are formed by
+// multiplies.  Each product that the FMA folds rounds once where a multiply
+// and an add rounded twice.
 template <int ORDER>
-__device__ __forceinline__ void accumulate2_sv(f32x2_t (&sa)[SumLayout<ORDER>::kNum],
-                                               f32x2_t (&v)[SumLayout<ORDER>::kNum],
-                                               f32x2_t s, f32x2_t wf) {
+__device__ __forceinline__ void accumulate2_svm(f32x2_t (&sa)[SumLayout<ORDER>::kNum],
+                                                f32x2_t (&v)[SumLayout<ORDER>::kNum],
+                                                f32x2_t s, f32x2_t m, f32x2_t wf) {
     constexpr int NP = SumLayout<ORDER>::kNumP;
-    f32x2_t pw = s;
-    if constexpr (NP >= 1) {
+    if constexpr (ORDER == 2) {
+        const f32x2_t am = m & 0x7fffffff7fffffffull;  // s^2 = |m|
         sa[0] = f2_add(sa[0], s);
         v[0] = f2_fma(wf, s, v[0]);
+        sa[1] = f2_add(sa[1], am);
+        v[1] = f2_fma(wf, am, v[1]);
+    } else if constexpr (ORDER == 3) {
+        const f32x2_t u = f2_mul(wf, s);
+        sa[0] = f2_add(sa[0], s);
+        v[0] = f2_add(v[0], u);
+        sa[1] = f2_fma(s, s, sa[1]);
+        v[1] = f2_fma(u, s, v[1]);
+    } else if constexpr (ORDER == 4) {
+        const f32x2_t s2 = f2_mul(s, s);
+        const f32x2_t u = f2_mul(wf, s);
+        const f32x2_t am = m & 0x7fffffff7fffffffull;  // s^4 = |m|
+        sa[0] = f2_add(sa[0], s);
+        v[0] = f2_add(v[0], u);
+        sa[1] = f2_add(sa[1], s2);
+        v[1] = f2_fma(u, s, v[1]);
+        sa[2] = f2_fma(s2, s, sa[2]);
+        v[2] = f2_fma(u, s2, v[2]);
+        sa[3] = f2_add(sa[3], am);
+        v[3] = f2_fma(wf, am, v[3]);
+    } else if constexpr (ORDER == 5) {
+        const f32x2_t s2 = f2_mul(s, s);
+        const f32x2_t w2 = f2_mul(wf, s2);
+        sa[0] = f2_add(sa[0], s);
+        v[0] = f2_fma(wf, s, v[0]);
+        sa[1] = f2_add(sa[1], s2);
+        v[1] = f2_add(v[1], w2);
+        sa[2] = f2_fma(s2, s, sa[2]);
+        v[2] = f2_fma(w2, s, v[2]);
+        sa[3] = f2_fma(s2, s2, sa[3]);
+        v[3] = f2_fma(w2, s2, v[3]);
     }
-#pragma unroll
-    for (int q = 2; q <= ORDER; ++q) {
-        pw = f2_mul(pw, s);
-        if (q <= NP) {
-            sa[q - 1] = f2_add(sa[q - 1], pw);
-            v[q - 1] = f2_fma(wf, pw, v[q - 1]);
-        }
-    }
-    const f32x2_t x = (ORDER & 1) ? pw : f2_copysign(pw, s);
-    sa[NP] = f2_add(sa[NP], x);
-    v[NP] = f2_fma(wf, x, v[NP]);
-    const f32x2_t xx = f2_mul(x, x);
-    sa[NP + 1] = f2_add(sa[NP + 1], xx);
-    v[NP + 1] = f2_fma(wf, xx, v[NP + 1]);
+    const f32x2_t wm = f2_mul(wf, m);
+    sa[NP] = f2_add(sa[NP], m);
+    v[NP] = f2_add(v[NP], wm);
+    sa[NP + 1] = f2_fma(m, m, sa[NP + 1]);
+    v[NP + 1] = f2_fma(wm, m, v[NP + 1]);
 }
 
-// The same for one sample in scalar arithmetic, f-weighted part only.
+// The f-weighted part for one sample (root s, raw sample m) in scalar
+// arithmetic.
 template <int ORDER>
-__device__ __forceinline__ void accumulate_v(float (&v)[SumLayout<ORDER>::kNum], float s,
-                                             float w1) {
+__device__ __forceinline__ void accumulate_vm(float (&v)[SumLayout<ORDER>::kNum], float s,
+                                              float m, float w1) {
     constexpr int NP = SumLayout<ORDER>::kNumP;
     float pw = s;
-    if constexpr (NP >= 1) v[0] = fmaf(w1, s, v[0]);
 #pragma unroll
-    for (int q = 2; q <= ORDER; ++q) {
-        pw *= s;
-        if (q <= NP) v[q - 1] = fmaf(w1, pw, v[q - 1]);
+    for (int q = 1; q <= NP; ++q) {
+        if (q > 1) pw *= s;
+        v[q - 1] = fmaf(w1, (q == ORDER) ? fabsf(m) : pw, v[q - 1]);
     }
-    const float x = (ORDER & 1) ? pw : copysignf(pw, s);
-    v[NP] = fmaf(w1, x, v[NP]);
-    v[NP + 1] = fmaf(w1, x * x, v[NP + 1]);
+    const float wm = w1 * m;
+    v[NP] += wm;
+    v[NP + 1] = fmaf(wm, m, v[NP + 1]);
 }
 
 // Interpolated delays, one work item (time tile, direction group) per CTA.
+// Lane l and pair k hold the pixels t0 + l + 64k (low half) and t0 + l + 32 +
+// 64k (high half), each half one conflict-free 32-lane 4-byte shared load
+// from the root window and one from the raw-sample window.
 template <int ORDER, int NGP, int PAIRS>
 __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsigned block) {
     constexpr int kPairs = PAIRS;
@@ -875,12 +906,11 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     const int WS = p.window;
     const int NC = p.mic_chunk;
-    // per microphone one 128-byte aligned block: its window, then the window
-    // shifted by one sample
+    // per microphone one 128-byte aligned block: its root window, then its
+    // raw-sample window
     const int MBf = ((2 * WS * 4 + 127) & ~127) >> 2;
     float *win = reinterpret_cast<float *>(smem + 128);
-    int *s_rel = reinterpret_cast<int *>(smem + 128 + NC * MBf * 4);
-    int *s_sel = s_rel + NC * 8;
+    int *s_sel = reinterpret_cast<int *>(smem + 128 + NC * MBf * 4);
     float *s_wf = reinterpret_cast<float *>(s_sel + NC * 8);
     // per-lane partial sums of the sample past the tile: [warp][q][lane]
     float *s_vext = s_wf + NC * 16 + ((threadIdx.x >> 5) * NA * 32 + (threadIdx.x & 31));
@@ -930,17 +960,15 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
             if (warp + 8 * lane < nc) x_first = gws[c0 + warp + 8 * lane];
         }
         if (threadIdx.x == 0) {
-            mbar_arrive_expect_tx(bar, 2 * nc * row_bytes + 4 * tab_bytes);
+            mbar_arrive_expect_tx(bar, 2 * nc * row_bytes + 3 * tab_bytes);
             const size_t to = ((size_t)g * p.N + c0) * 8;
             if (checked_ok(((size_t)g * p.N + c0 + nc) <= (size_t)p.n_groups * p.N &&
-                               smem_in(s_rel, tab_bytes) && smem_in(s_sel, tab_bytes) &&
-                               smem_in(s_wf, 2 * tab_bytes),
+                               smem_in(s_sel, tab_bytes) && smem_in(s_wf, 2 * tab_bytes),
                            p.err)) {
-                bulk_g2s(s_rel, p.rel + to, tab_bytes, bar);
                 bulk_g2s(s_sel, p.sel + to, tab_bytes, bar);
                 bulk_g2s(s_wf, p.wf2 + to * 2, 2 * tab_bytes, bar);
             } else {
-                mbar_complete_tx_local(bar, 4 * tab_bytes);
+                mbar_complete_tx_local(bar, 3 * tab_bytes);
             }
         }
         __syncthreads();  // the byte count is set before any copy can land
@@ -969,26 +997,30 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
         }
         parity ^= 1u;
 
-        // (x, x+1), x = off + 2l + 64k: at x in copy 0 (even off) or at x - 1
-        // in copy 1 (odd off); s_sel holds that byte offset for lane 0, k = 0
-        // 32-bit shared addresses (0.9 % faster than generic pointers, measured):
-        // lane l's pairs, and the weight {f, f} of the direction's entry
-        const uint32_t base = smem_addr(win) + 8 * lane;
-        const uint32_t wq = smem_addr(s_wf) + 8 * warp;
+        // s_sel: byte offset, from the staged windows' base, of the
+        // direction's sample for pixel t0 (its microphone's block + 4 x the
+        // shift relative to the window start).  Plain loads, so the compiler
+        // can move them ahead of the arithmetic of the microphone before.
+        const unsigned char *wb = reinterpret_cast<const unsigned char *>(win) + 4 * lane;
+        const f32x2_t *wfp = reinterpret_cast<const f32x2_t *>(s_wf) + warp;
 #pragma unroll 4
         for (int il = 0; il < nc; ++il) {
-            const uint32_t a = base + (uint32_t)s_sel[il * 8 + warp];
-            if constexpr (kChecked) {  // the lane's pairs inside microphone il's block
-                const uint32_t blk = smem_addr(win) + (uint32_t)(il * MBf * 4);
-                if (!checked_ok(a >= blk && a + 256 * (kPairs - 1) + 8 <= blk + MBf * 4 &&
-                                    smem_in(wq + 64 * il, 8),
+            const float *r = reinterpret_cast<const float *>(wb + s_sel[il * 8 + warp]);
+            if constexpr (kChecked) {  // the lane's samples inside microphone il's root window
+                const unsigned char *blk =
+                    reinterpret_cast<const unsigned char *>(win) + il * MBf * 4;
+                if (!checked_ok(reinterpret_cast<const unsigned char *>(r) >= blk &&
+                                    reinterpret_cast<const unsigned char *>(r + 64 * (kPairs - 1) +
+                                                                            33) <= blk + WS * 4 &&
+                                    smem_in(wfp + 8 * il, 8),
                                 p.err))
                     continue;
             }
-            const f32x2_t wf = lds_f32x2(wq + 64 * il);
+            const f32x2_t wf = wfp[8 * il];
 #pragma unroll
             for (int k = 0; k < kPairs; ++k)
-                accumulate2_sv<ORDER>(acc[k], vac[k], lds_f32x2(a + 256 * k), wf);
+                accumulate2_svm<ORDER>(acc[k], vac[k], f2_pack(r[64 * k], r[64 * k + 32]),
+                                       f2_pack(r[WS + 64 * k], r[WS + 64 * k + 32]), wf);
         }
         // the sample past the tile lies inside the window (its span covers the
         // last pixel's x + 1)
@@ -997,9 +1029,12 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
 #pragma unroll
             for (int q = 0; q < NA; ++q) ve[q] = s_vext[q * 32];
             for (int il = lane; il < nc; il += 32) {
-                const int o = s_rel[il * 8 + warp] + kTile;
-                if (checked_ok(o >= 0 && o < WS, p.err))
-                    accumulate_v<ORDER>(ve, win[il * MBf + o], s_wf[(il * 8 + warp) * 2]);
+                const int o = s_sel[il * 8 + warp] + 4 * kTile;  // bytes from win
+                if (checked_ok(o >= il * MBf * 4 && o + 4 <= il * MBf * 4 + WS * 4, p.err)) {
+                    const float *e = reinterpret_cast<const float *>(
+                        reinterpret_cast<const unsigned char *>(win) + o);
+                    accumulate_vm<ORDER>(ve, e[0], e[WS], s_wf[(il * 8 + warp) * 2]);
+                }
             }
 #pragma unroll
             for (int q = 0; q < NA; ++q) s_vext[q * 32] = ve[q];
@@ -1008,9 +1043,11 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
 
     const int dir = p.gdir[(size_t)g * 8 + warp];
     if (dir < 0 || !checked_ok(dir < p.M, p.err)) return;
-    // sum[t] = S[t] - V[t] + V[t + 1].  For the pair (t, t+1): V[t+1] is the pair's
-    // own second half; V[t+2] the next lane's first half (lane 31: lane 0's of
-    // the next pair, or vext after the last).
+    // sum[t] = S[t] - V[t] + V[t + 1].  Pixel t0 + l + 64k (low half): V[t + 1] is
+    // lane l + 1's low half (lane 31: lane 0's high half); t0 + l + 32 + 64k (high
+    // half): lane l + 1's high half (lane 31: lane 0's low half of the next pair,
+    // or, after the last pair, the sample past the tile summed over the lanes'
+    // microphones).
     float vext[NA];
 #pragma unroll
     for (int q = 0; q < NA; ++q) {
@@ -1018,14 +1055,15 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) vext[q] += __shfl_xor_sync(0xffffffffu, vext[q], o);
     }
-    float nxt[kPairs][NA];
+    float nlo[kPairs][NA], nhi[kPairs][NA];
 #pragma unroll
     for (int k = 0; k < kPairs; ++k)
 #pragma unroll
         for (int q = 0; q < NA; ++q) {
             float lo, hi;
             f2_unpack(vac[k][q], lo, hi);
-            nxt[k][q] = __shfl_sync(0xffffffffu, lo, (lane + 1) & 31);
+            nlo[k][q] = __shfl_sync(0xffffffffu, lo, (lane + 1) & 31);
+            nhi[k][q] = __shfl_sync(0xffffffffu, hi, (lane + 1) & 31);
         }
 #pragma unroll
     for (int k = 0; k < kPairs; ++k)
@@ -1034,9 +1072,10 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
             float slo, shi, vlo, vhi;
             f2_unpack(acc[k][q], slo, shi);
             f2_unpack(vac[k][q], vlo, vhi);
-            const float vn =
-                lane < 31 ? nxt[k][q] : (k + 1 < kPairs ? nxt[(k + 1) % kPairs][q] : vext[q]);
-            acc[k][q] = f2_pack((slo - vlo) + vhi, (shi - vhi) + vn);
+            const float vn_lo = lane < 31 ? nlo[k][q] : nhi[k][q];
+            const float vn_hi =
+                lane < 31 ? nhi[k][q] : (k + 1 < kPairs ? nlo[(k + 1) % kPairs][q] : vext[q]);
+            acc[k][q] = f2_pack((slo - vlo) + vn_lo, (shi - vhi) + vn_hi);
         }
     float *yrow = p.y + (size_t)dir * p.T;
     float *cfrow = p.cf ? p.cf + (size_t)dir * p.T : nullptr;
@@ -1050,7 +1089,7 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
         f2_unpack(acc[k][NP + 1], B[0], B[1]);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int t = t0 + 2 * lane + 64 * k + h;
+            const int t = t0 + lane + 32 * h + 64 * k;
             if (t >= p.T) continue;
             if constexpr (SumLayout<ORDER>::kPnIsA) P[h][ORDER] = A[h];
             const float E = esym_from_power_sums<ORDER, NGP>(P[h]);

@@ -292,15 +292,15 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
     }
     long long window = round_up(hp.tile + spread, kAlign);
     // The persistent pair kernel (nearest-sample delays) double-buffers its
-    // staged windows; the interpolated-delay pair kernel stages each window
-    // as is and shifted by one sample.
+    // staged windows; the interpolated-delay pair kernel stages a root and a
+    // raw-sample window per microphone.
     const bool pair = uses_pair_kernel(d.chan_prec, d.order);
     const bool persistent = pair && !lin;
     const size_t budget = persistent ? kPairSmemBudget - 2 * 256
                                      : kWindowSmemBudget - (pair ? 8 * 6 * 32 * 4 : 0);
     const size_t tab = (size_t)kGroup * 4 * (lin ? 2 : 1);
     const size_t per_mic = persistent ? 2 * ((size_t)window * eb + tab)
-                                      : (pair ? lin_mic_bytes((int)window) + (size_t)kGroup * 16
+                                      : (pair ? lin_mic_bytes((int)window) + (size_t)kGroup * 12
                                               : (size_t)window * eb + tab);
     if (per_mic > budget)
         return fail("a direction group's delay spread does not fit in shared memory");
@@ -320,9 +320,7 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
                     const size_t o = ((size_t)g * N + i) * kGroup + s;
                     const int off = hp.rel[o];
                     const size_t blk = (size_t)(i % hp.mic_chunk) * mb;
-                    hp.gsel[o] = (int32_t)(blk + ((off & 1) ? (size_t)hp.window * 4 +
-                                                                  (size_t)(off - 1) * 4
-                                                            : (size_t)off * 4));
+                    hp.gsel[o] = (int32_t)(blk + (size_t)off * 4);
                     const float f = hp.gfrac[o];
                     hp.gwf2[o * 2 + 0] = f;
                     hp.gwf2[o * 2 + 1] = f;
