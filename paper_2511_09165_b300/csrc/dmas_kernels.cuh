@@ -932,11 +932,29 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
     const int *gws = p.gws + (size_t)g * p.N;
     int x_first = 0;
     if (warp + 8 * lane < min(NC, p.N)) x_first = gws[warp + 8 * lane];
+    const uint32_t row_bytes = (uint32_t)(WS * 4);
+    // Thread 0 sets a chunk's byte count and copies its tables (the first
+    // chunk's right after the barrier's initialisation, so one CTA barrier
+    // precedes the first window copies).
+    auto stage_head = [&](int c0, int nc) {
+        const uint32_t tab_bytes = (uint32_t)(nc * 8 * 4);
+        mbar_arrive_expect_tx(bar, 2 * nc * row_bytes + 3 * tab_bytes);
+        const size_t to = ((size_t)g * p.N + c0) * 8;
+        if (checked_ok(((size_t)g * p.N + c0 + nc) <= (size_t)p.n_groups * p.N &&
+                           smem_in(s_sel, tab_bytes) && smem_in(s_wf, 2 * tab_bytes),
+                       p.err)) {
+            bulk_g2s(s_sel, p.sel + to, tab_bytes, bar);
+            bulk_g2s(s_wf, p.wf2 + to * 2, 2 * tab_bytes, bar);
+        } else {
+            mbar_complete_tx_local(bar, 3 * tab_bytes);
+        }
+    };
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
+        stage_head(0, min(NC, p.N));
     }
-    __syncthreads();
+    __syncthreads();  // the barrier and the first byte count are set before any copy lands
 
     // S (acc) and V (vac) of the lane's pairs (U = S - V); s_vext: V at
     // t0 + 64 PAIRS, the sample past the tile, one microphone per lane
@@ -953,25 +971,12 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
     uint32_t parity = 0;
     for (int c0 = 0; c0 < p.N; c0 += NC) {
         const int nc = min(NC, p.N - c0);
-        const uint32_t row_bytes = (uint32_t)(WS * 4);
-        const uint32_t tab_bytes = (uint32_t)(nc * 8 * 4);
         if (c0 > 0) {
             __syncthreads();  // every warp is done with the previous chunk
             if (warp + 8 * lane < nc) x_first = gws[c0 + warp + 8 * lane];
+            if (threadIdx.x == 0) stage_head(c0, nc);
+            __syncthreads();  // the byte count is set before any copy can land
         }
-        if (threadIdx.x == 0) {
-            mbar_arrive_expect_tx(bar, 2 * nc * row_bytes + 3 * tab_bytes);
-            const size_t to = ((size_t)g * p.N + c0) * 8;
-            if (checked_ok(((size_t)g * p.N + c0 + nc) <= (size_t)p.n_groups * p.N &&
-                               smem_in(s_sel, tab_bytes) && smem_in(s_wf, 2 * tab_bytes),
-                           p.err)) {
-                bulk_g2s(s_sel, p.sel + to, tab_bytes, bar);
-                bulk_g2s(s_wf, p.wf2 + to * 2, 2 * tab_bytes, bar);
-            } else {
-                mbar_complete_tx_local(bar, 3 * tab_bytes);
-            }
-        }
-        __syncthreads();  // the byte count is set before any copy can land
         for (int il = warp + 8 * lane; il < nc; il += kThreads) {
             const int i = c0 + il;
             // a multiple of 8 samples (32 bytes)
