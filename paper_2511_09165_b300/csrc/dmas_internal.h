@@ -78,6 +78,9 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
 // (too many running sums for its registers) and FP16/BF16 channels run the
 // scalar beamform kernel.
 constexpr int kPairMaxOrder = 5;
+// Nearest-sample delays up to this order take four pixel pairs per lane (a
+// 256-sample tile) instead of two.
+constexpr int kWidePairMaxOrder = 3;
 
 inline bool uses_pair_kernel(int chan_prec, int order) {
     return chan_prec == DMAS_CH_F32 && order <= kPairMaxOrder;

@@ -80,12 +80,21 @@ cudaError_t launch_beam_variant(const BeamParams &p, unsigned grid, size_t smem,
     if constexpr (std::is_same<CH, float>::value && ORDER <= kPairMaxOrder) {
         static std::once_flag once;
         static cudaError_t err = cudaSuccess;
-        if constexpr (LINEAR)
+        if constexpr (LINEAR) {
             return launch_kernel(beamform_x2_kernel<ORDER, LINEAR, NGP, 2>, once, err, p, grid,
                                  smem, s);
-        else
+        } else {
+            if constexpr (ORDER <= kWidePairMaxOrder) {
+                if (p.pairs == 4) {
+                    static std::once_flag once4;
+                    static cudaError_t err4 = cudaSuccess;
+                    return launch_persistent(beamform_x2_kernel<ORDER, LINEAR, NGP, 4>, once4,
+                                             err4, p, grid, smem, s);
+                }
+            }
             return launch_persistent(beamform_x2_kernel<ORDER, LINEAR, NGP, 2>, once, err, p,
                                      grid, smem, s);
+        }
     } else {
         static std::once_flag once;
         static cudaError_t err = cudaSuccess;
@@ -131,12 +140,21 @@ cudaError_t launch_beam_batch_variant(const BeamBatch &b, unsigned grid, size_t 
     if constexpr (std::is_same<CH, float>::value && ORDER <= kPairMaxOrder) {
         static std::once_flag once;
         static cudaError_t err = cudaSuccess;
-        if constexpr (LINEAR)
+        if constexpr (LINEAR) {
             return launch_kernel(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, 2>, once, err, b,
                                  grid, smem, s);
-        else
+        } else {
+            if constexpr (ORDER <= kWidePairMaxOrder) {
+                if (b.e[0].pairs == 4) {  // a batch's entries share their kernel variant
+                    static std::once_flag once4;
+                    static cudaError_t err4 = cudaSuccess;
+                    return launch_persistent(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, 4>,
+                                             once4, err4, b, grid, smem, s);
+                }
+            }
             return launch_persistent(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, 2>, once, err,
                                      b, grid, smem, s);
+        }
     } else {
         static std::once_flag once;
         static cudaError_t err = cudaSuccess;

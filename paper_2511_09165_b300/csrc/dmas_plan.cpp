@@ -284,7 +284,8 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
     }
     const size_t eb = chan_elem_bytes(d.chan_prec);
     if (uses_pair_kernel(d.chan_prec, d.order)) {
-        hp.pairs = 2;  // pixel pairs per lane (time tile 64 x pairs)
+        // pixel pairs per lane (time tile 64 x pairs)
+        hp.pairs = (!lin && d.order <= kWidePairMaxOrder) ? 4 : 2;
         hp.tile = 64 * hp.pairs;
     } else {
         hp.pairs = 0;
