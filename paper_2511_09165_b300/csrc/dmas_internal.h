@@ -79,8 +79,9 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
 // scalar beamform kernel.
 constexpr int kPairMaxOrder = 5;
 // Nearest-sample delays up to this order take four pixel pairs per lane (a
-// 256-sample tile) instead of two.
-constexpr int kWidePairMaxOrder = 3;
+// 256-sample tile) instead of two: fewer staged bytes and table loads per
+// output (orders 4 and 5 then run at three CTAs per SM, 80 registers).
+constexpr int kWidePairMaxOrder = 5;
 
 inline bool uses_pair_kernel(int chan_prec, int order) {
     return chan_prec == DMAS_CH_F32 && order <= kPairMaxOrder;

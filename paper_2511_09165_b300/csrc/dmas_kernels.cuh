@@ -1382,17 +1382,18 @@ struct ManyFrames {
     __device__ unsigned first(int e) const { return b.start[e]; }
 };
 
-// Four CTAs per SM for nearest-sample delays, three for interpolated ones
-// (twice the accumulators).
+// Four CTAs per SM for nearest-sample delays (three with four pixel pairs
+// per lane above order 3), three for interpolated ones (twice the
+// accumulators).
 template <int ORDER, bool LINEAR, int NGP, int PAIRS>
-__global__ void __launch_bounds__(kThreads, LINEAR ? 3 : 4)
+__global__ void __launch_bounds__(kThreads, (LINEAR || (PAIRS > 2 && ORDER > 3)) ? 3 : 4)
     beamform_x2_kernel(const __grid_constant__ BeamParams p) {
     if constexpr (LINEAR) beamform_x2_lin_body<ORDER, NGP, PAIRS>(p, blockIdx.x);
     else beamform_x2_run<ORDER, NGP, PAIRS>(OneFrame{p});
 }
 
 template <int ORDER, bool LINEAR, int NGP, int PAIRS>
-__global__ void __launch_bounds__(kThreads, LINEAR ? 3 : 4)
+__global__ void __launch_bounds__(kThreads, (LINEAR || (PAIRS > 2 && ORDER > 3)) ? 3 : 4)
     beamform_x2_batch_kernel(const __grid_constant__ BeamBatch b) {
     if constexpr (LINEAR) {
         const int k = batch_entry(b.start, b.count, blockIdx.x);
