@@ -78,10 +78,16 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
 // (too many running sums for its registers) and FP16/BF16 channels run the
 // scalar beamform kernel.
 constexpr int kPairMaxOrder = 5;
-// Nearest-sample delays up to this order take four pixel pairs per lane (a
-// 256-sample tile) instead of two: fewer staged bytes and table loads per
-// output (orders 4 and 5 then run at three CTAs per SM, 80 registers).
-constexpr int kWidePairMaxOrder = 5;
+// Pixel pairs per lane of the nearest-sample pair kernel: four (a 256-sample
+// tile; interpolated delays take two), for fewer staged bytes and table loads
+// per output than two (orders 4 and 5 run at three CTAs per SM, 80 registers).
+// Measured on B300 against two pairs: passive 256-microphone frame, n = 3
+// 19.99 -> 16.12 ms, n = 5 23.35 -> 21.98 ms; hemisphere frame, n = 5
+// 460 -> 454 us.  A frame with fewer than kWideMinItems wide work items (two
+// per CTA at four CTAs on each of the 148 SMs: the device not filled twice)
+// keeps two pairs, twice the items, so its CTAs end sooner.
+constexpr int kRoundPairs = 4;
+constexpr size_t kWideMinItems = 148 * 4 * 2;
 
 inline bool uses_pair_kernel(int chan_prec, int order) {
     return chan_prec == DMAS_CH_F32 && order <= kPairMaxOrder;

@@ -284,8 +284,10 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
     }
     const size_t eb = chan_elem_bytes(d.chan_prec);
     if (uses_pair_kernel(d.chan_prec, d.order)) {
-        // pixel pairs per lane (time tile 64 x pairs)
-        hp.pairs = (!lin && d.order <= kWidePairMaxOrder) ? 4 : 2;
+        // pixel pairs per lane (time tile 64 x pairs): nearest-sample frames
+        // with enough work items take the wide tile
+        const size_t wide_items = (size_t)G * (size_t)((T + 64 * kRoundPairs - 1) / (64 * kRoundPairs));
+        hp.pairs = (!lin && wide_items >= kWideMinItems) ? kRoundPairs : 2;
         hp.tile = 64 * hp.pairs;
     } else {
         hp.pairs = 0;

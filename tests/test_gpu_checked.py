@@ -25,7 +25,8 @@ CHECKED = os.path.join(ROOT, "paper_2511_09165_b300", "_lib", "libdmas_checked.s
 SELECTION = [
     ("test_gpu_parity.py", "short_frames or several_staging_passes or ragged_tiles or "
                            "microphone_chunks or weights_near_the_ends or every_order or "
-                           "single_mic or order_above or zero_frame or newton_girard"),
+                           "single_mic or order_above or zero_frame or newton_girard or "
+                           "wide_tile"),
     ("test_gpu_orders.py", ""),
     ("test_gpu_serving.py", "bitwise or tile_cap"),
     ("test_zz_no_alloc.py", ""),
