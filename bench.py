@@ -967,6 +967,22 @@ def run_orders(args) -> None:
         for i, pl in enumerate(singles):
             name = ("das" if i % 5 == 0 else "dmas%d" % (i % 5 + 1)) + ("_cf" if i >= 5 else "")
             per_order[name] = timed(lambda: pl(frame, out=images[i // 5, i % 5], stream=stream))
+        # the beamform stage of each single-order call with CF (configuration 2 asks
+        # for n = 1..5 each) against the FP32 roofline, by the stage events
+        single_roof = {}
+        for i, pl in enumerate(singles[5:]):
+            k = i + 1
+            pl.set_profiling(True)
+            bst = []
+            for _ in range(max(5, steps // 2)):
+                flush.zero_()
+                pl(frame, out=images[1, i], stream=stream)
+                bst.append(pl.stage_ms()[1])
+            t_ms = float(np.median(bst))
+            ops_k = algorithmic_ops_per_pixel(N, k, mode == "linear")["beam_total"]
+            single_roof["das_cf" if k == 1 else "dmas%d_cf" % k] = {
+                "beamform_ms": t_ms, "ops_per_pixel": ops_k,
+                "frac": ops_k * px / (t_ms * 1e-3) / 1e12 / peak}
         for pl in singles:
             pl.check()
             pl.close()
@@ -975,6 +991,7 @@ def run_orders(args) -> None:
         modes.append({
             "delays": mode, "pass_ms": pass_ms, "separate_ms": sep_ms,
             "single_call_ms": per_order,
+            "single_order_beamform_cf": single_roof,
             "speedup": sep_ms / pass_ms,
             "stage_ms": {"root planes": float(st[0]), "beamform (every order)": float(st[1]),
                          "envelope (10 images)": float(st[2])},
