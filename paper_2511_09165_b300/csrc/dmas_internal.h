@@ -87,6 +87,11 @@ constexpr int kPairMaxOrder = 5;
 // per CTA at four CTAs on each of the 148 SMs: the device not filled twice)
 // keeps two pairs, twice the items, so its CTAs end sooner.
 constexpr int kRoundPairs = 4;
+// Interpolated delays up to order kLinWideMaxOrder (four running sums, split
+// plain and f-weighted) take three pairs per lane, a 192-sample tile, in the
+// registers that orders 4 and 5 (six sums) need for two.
+constexpr int kLinWidePairs = 3;
+constexpr int kLinWideMaxOrder = 3;
 constexpr size_t kWideMinItems = 148 * 4 * 2;
 
 inline bool uses_pair_kernel(int chan_prec, int order) {

@@ -82,6 +82,14 @@ cudaError_t launch_beam_variant(const BeamParams &p, unsigned grid, size_t smem,
         static std::once_flag once;
         static cudaError_t err = cudaSuccess;
         if constexpr (LINEAR) {
+            if constexpr (ORDER <= kLinWideMaxOrder) {
+                if (p.pairs == kLinWidePairs) {
+                    static std::once_flag once_w;
+                    static cudaError_t err_w = cudaSuccess;
+                    return launch_kernel(beamform_x2_kernel<ORDER, LINEAR, NGP, kLinWidePairs>,
+                                         once_w, err_w, p, grid, smem, s);
+                }
+            }
             return launch_kernel(beamform_x2_kernel<ORDER, LINEAR, NGP, 2>, once, err, p, grid,
                                  smem, s);
         } else if (p.pairs == kRoundPairs) {
@@ -139,6 +147,15 @@ cudaError_t launch_beam_batch_variant(const BeamBatch &b, unsigned grid, size_t 
         static std::once_flag once;
         static cudaError_t err = cudaSuccess;
         if constexpr (LINEAR) {
+            if constexpr (ORDER <= kLinWideMaxOrder) {
+                if (b.e[0].pairs == kLinWidePairs) {  // a batch's entries share their variant
+                    static std::once_flag once_w;
+                    static cudaError_t err_w = cudaSuccess;
+                    return launch_kernel(
+                        beamform_x2_batch_kernel<ORDER, LINEAR, NGP, kLinWidePairs>, once_w,
+                        err_w, b, grid, smem, s);
+                }
+            }
             return launch_kernel(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, 2>, once, err, b,
                                  grid, smem, s);
         } else if (b.e[0].pairs == kRoundPairs) {  // a batch's entries share their variant
