@@ -87,11 +87,14 @@ constexpr int kPairMaxOrder = 5;
 // per CTA at four CTAs on each of the 148 SMs: the device not filled twice)
 // keeps two pairs, twice the items, so its CTAs end sooner.
 constexpr int kRoundPairs = 4;
-// Interpolated delays up to order kLinWideMaxOrder (four running sums, split
-// plain and f-weighted) take three pairs per lane, a 192-sample tile, in the
-// registers that orders 4 and 5 (six sums) need for two.
-constexpr int kLinWidePairs = 3;
-constexpr int kLinWideMaxOrder = 3;
+// Pixel pairs per lane of the interpolated-delay pair kernel: three, a
+// 192-sample tile (orders up to 3 at three CTAs per SM, 72-80 registers;
+// orders 4 and 5, six running sums split plain and f-weighted, at two CTAs per
+// SM, 118 registers).  Measured on B300 against two pairs (128 samples, three
+// CTAs per SM at n = 5) and four (two CTAs per SM): hemisphere frame, n = 5
+// 749 / 745 against 728 us; n = 1, 2, 3 0.305 / 0.535 / 0.520 against
+// 0.274 / 0.496 / 0.493 ms with three.
+constexpr int kLinPairs = 3;
 constexpr size_t kWideMinItems = 148 * 4 * 2;
 
 inline bool uses_pair_kernel(int chan_prec, int order) {

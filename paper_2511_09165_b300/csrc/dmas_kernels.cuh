@@ -1382,18 +1382,22 @@ struct ManyFrames {
     __device__ unsigned first(int e) const { return b.start[e]; }
 };
 
-// Four CTAs per SM for nearest-sample delays (three with four pixel pairs
-// per lane above order 3), three for interpolated ones (twice the
-// accumulators).
+// CTAs per SM of the pair kernels (the register budget): nearest-sample
+// delays four (three with four pixel pairs per lane above order 3);
+// interpolated delays (twice the accumulators, three pairs per lane) three up
+// to order 3, two above.
+constexpr int pair_ctas_per_sm(bool linear, int order, int pairs) {
+    return linear ? (order > 3 ? 2 : 3) : ((pairs > 2 && order > 3) ? 3 : 4);
+}
 template <int ORDER, bool LINEAR, int NGP, int PAIRS>
-__global__ void __launch_bounds__(kThreads, (LINEAR || (PAIRS > 2 && ORDER > 3)) ? 3 : 4)
+__global__ void __launch_bounds__(kThreads, pair_ctas_per_sm(LINEAR, ORDER, PAIRS))
     beamform_x2_kernel(const __grid_constant__ BeamParams p) {
     if constexpr (LINEAR) beamform_x2_lin_body<ORDER, NGP, PAIRS>(p, blockIdx.x);
     else beamform_x2_run<ORDER, NGP, PAIRS>(OneFrame{p});
 }
 
 template <int ORDER, bool LINEAR, int NGP, int PAIRS>
-__global__ void __launch_bounds__(kThreads, (LINEAR || (PAIRS > 2 && ORDER > 3)) ? 3 : 4)
+__global__ void __launch_bounds__(kThreads, pair_ctas_per_sm(LINEAR, ORDER, PAIRS))
     beamform_x2_batch_kernel(const __grid_constant__ BeamBatch b) {
     if constexpr (LINEAR) {
         const int k = batch_entry(b.start, b.count, blockIdx.x);

@@ -71,9 +71,9 @@ cudaError_t launch_persistent(K kern, std::once_flag &once, cudaError_t &attr_er
     return cudaGetLastError();
 }
 
-// FP32 channels up to kPairMaxOrder: the pair kernel (2 pairs per lane for
-// interpolated delays; kRoundPairs, or 2 for small frames, and persistent for
-// nearest-sample delays, `grid` then counting its work items);
+// FP32 channels up to kPairMaxOrder: the pair kernel (kLinPairs pairs per lane
+// for interpolated delays; kRoundPairs, or 2 for small frames, and persistent
+// for nearest-sample delays, `grid` then counting its work items);
 // otherwise the scalar one (the same choice as uses_pair_kernel on the host).
 template <int ORDER, bool LINEAR, typename CH, int NGP>
 cudaError_t launch_beam_variant(const BeamParams &p, unsigned grid, size_t smem,
@@ -82,16 +82,8 @@ cudaError_t launch_beam_variant(const BeamParams &p, unsigned grid, size_t smem,
         static std::once_flag once;
         static cudaError_t err = cudaSuccess;
         if constexpr (LINEAR) {
-            if constexpr (ORDER <= kLinWideMaxOrder) {
-                if (p.pairs == kLinWidePairs) {
-                    static std::once_flag once_w;
-                    static cudaError_t err_w = cudaSuccess;
-                    return launch_kernel(beamform_x2_kernel<ORDER, LINEAR, NGP, kLinWidePairs>,
-                                         once_w, err_w, p, grid, smem, s);
-                }
-            }
-            return launch_kernel(beamform_x2_kernel<ORDER, LINEAR, NGP, 2>, once, err, p, grid,
-                                 smem, s);
+            return launch_kernel(beamform_x2_kernel<ORDER, LINEAR, NGP, kLinPairs>, once, err, p,
+                                 grid, smem, s);
         } else if (p.pairs == kRoundPairs) {
             static std::once_flag once_w;
             static cudaError_t err_w = cudaSuccess;
@@ -147,17 +139,8 @@ cudaError_t launch_beam_batch_variant(const BeamBatch &b, unsigned grid, size_t 
         static std::once_flag once;
         static cudaError_t err = cudaSuccess;
         if constexpr (LINEAR) {
-            if constexpr (ORDER <= kLinWideMaxOrder) {
-                if (b.e[0].pairs == kLinWidePairs) {  // a batch's entries share their variant
-                    static std::once_flag once_w;
-                    static cudaError_t err_w = cudaSuccess;
-                    return launch_kernel(
-                        beamform_x2_batch_kernel<ORDER, LINEAR, NGP, kLinWidePairs>, once_w,
-                        err_w, b, grid, smem, s);
-                }
-            }
-            return launch_kernel(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, 2>, once, err, b,
-                                 grid, smem, s);
+            return launch_kernel(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, kLinPairs>, once,
+                                 err, b, grid, smem, s);
         } else if (b.e[0].pairs == kRoundPairs) {  // a batch's entries share their variant
             static std::once_flag once_w;
             static cudaError_t err_w = cudaSuccess;

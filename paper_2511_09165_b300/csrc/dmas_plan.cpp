@@ -287,8 +287,7 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
         // pixel pairs per lane (time tile 64 x pairs): nearest-sample frames
         // with enough work items take the wide tile
         const size_t wide_items = (size_t)G * (size_t)((T + 64 * kRoundPairs - 1) / (64 * kRoundPairs));
-        hp.pairs = lin ? (d.order <= kLinWideMaxOrder ? kLinWidePairs : 2)
-                       : (wide_items >= kWideMinItems ? kRoundPairs : 2);
+        hp.pairs = lin ? kLinPairs : (wide_items >= kWideMinItems ? kRoundPairs : 2);
         hp.tile = 64 * hp.pairs;
     } else {
         hp.pairs = 0;
