@@ -116,9 +116,9 @@ WORKLOADS = {
 # interpolated-delay pair kernel on the hemisphere frame), valid only while
 # the kernel source is the one that was measured; otherwise the line's
 # "traffic" is null and "traffic_note" says why.
-TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "ng": "cf32", "kernel_src_sha256_16": "fe40f56e1fd61a9c",
+TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "ng": "cf32", "kernel_src_sha256_16": "aeca89db20bf57e4",
                   # ncu dram__bytes_read.sum + dram__bytes_write.sum (bytes)
-                  "bytes": 5_095_168 + 76_134_912}
+                  "bytes": 5_131_520 + 76_112_128}
 
 
 def beam_traffic(workload: str, ng: str = "cf32"):
