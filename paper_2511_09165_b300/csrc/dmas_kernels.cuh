@@ -1008,7 +1008,7 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
         // can move them ahead of the arithmetic of the microphone before.
         const unsigned char *wb = reinterpret_cast<const unsigned char *>(win) + 4 * lane;
         const f32x2_t *wfp = reinterpret_cast<const f32x2_t *>(s_wf) + warp;
-#pragma unroll 4
+#pragma unroll 8
         for (int il = 0; il < nc; ++il) {
             const float *r = reinterpret_cast<const float *>(wb + s_sel[il * 8 + warp]);
             if constexpr (kChecked) {  // the lane's samples inside microphone il's root window
