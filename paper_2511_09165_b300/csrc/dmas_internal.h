@@ -78,15 +78,17 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
 // (too many running sums for its registers) and FP16/BF16 channels run the
 // scalar beamform kernel.
 constexpr int kPairMaxOrder = 5;
-// Pixel pairs per lane of the nearest-sample pair kernel: four (a 256-sample
-// tile; interpolated delays take two), for fewer staged bytes and table loads
-// per output than two (orders 4 and 5 run at three CTAs per SM, 80 registers).
-// Measured on B300 against two pairs: passive 256-microphone frame, n = 3
-// 19.99 -> 16.12 ms, n = 5 23.35 -> 21.98 ms; hemisphere frame, n = 5
-// 460 -> 454 us.  A frame with fewer than kWideMinItems wide work items (two
-// per CTA at four CTAs on each of the 148 SMs: the device not filled twice)
-// keeps two pairs, twice the items, so its CTAs end sooner.
-constexpr int kRoundPairs = 4;
+// Pixel pairs per lane of the nearest-sample pair kernel: six up to order 3
+// (a 384-sample tile, 80 registers, three CTAs per SM) and four above (a
+// 256-sample tile, 80 registers, three CTAs per SM), for fewer staged bytes
+// and table loads per output than two (128 samples, four CTAs per SM).
+// Measured on B300, passive 256-microphone frame: n = 3 19.99 / 16.12 /
+// 14.79 ms with two / four / six pairs; n = 5 23.35 / 21.98 / 22.15 ms;
+// hemisphere frame, n = 5 460 / 454 / 458 us.  A frame with fewer than
+// kWideMinItems wide work items (two per CTA at four CTAs on each of the 148
+// SMs: the device not filled twice) keeps two pairs, more items, so its CTAs
+// end sooner.
+constexpr int round_pairs(int order) { return order <= 3 ? 6 : 4; }
 // Pixel pairs per lane of the interpolated-delay pair kernel: three, a
 // 192-sample tile (orders up to 3 at three CTAs per SM, 72-80 registers;
 // orders 4 and 5, six running sums split plain and f-weighted, at two CTAs per

@@ -1383,11 +1383,11 @@ struct ManyFrames {
 };
 
 // CTAs per SM of the pair kernels (the register budget): nearest-sample
-// delays four (three with four pixel pairs per lane above order 3);
-// interpolated delays (twice the accumulators, three pairs per lane) three up
-// to order 3, two above.
+// delays four with two pixel pairs per lane, three with more (four pairs above
+// order 3, six up to it); interpolated delays (twice the accumulators, three
+// pairs per lane) three up to order 3, two above.
 constexpr int pair_ctas_per_sm(bool linear, int order, int pairs) {
-    return linear ? (order > 3 ? 2 : 3) : ((pairs > 2 && order > 3) ? 3 : 4);
+    return linear ? (order > 3 ? 2 : 3) : (pairs > 2 ? 3 : 4);
 }
 template <int ORDER, bool LINEAR, int NGP, int PAIRS>
 __global__ void __launch_bounds__(kThreads, pair_ctas_per_sm(LINEAR, ORDER, PAIRS))

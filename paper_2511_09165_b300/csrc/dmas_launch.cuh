@@ -72,8 +72,8 @@ cudaError_t launch_persistent(K kern, std::once_flag &once, cudaError_t &attr_er
 }
 
 // FP32 channels up to kPairMaxOrder: the pair kernel (kLinPairs pairs per lane
-// for interpolated delays; kRoundPairs, or 2 for small frames, and persistent
-// for nearest-sample delays, `grid` then counting its work items);
+// for interpolated delays; round_pairs(ORDER), or 2 for small frames, and
+// persistent for nearest-sample delays, `grid` then counting its work items);
 // otherwise the scalar one (the same choice as uses_pair_kernel on the host).
 template <int ORDER, bool LINEAR, typename CH, int NGP>
 cudaError_t launch_beam_variant(const BeamParams &p, unsigned grid, size_t smem,
@@ -84,11 +84,11 @@ cudaError_t launch_beam_variant(const BeamParams &p, unsigned grid, size_t smem,
         if constexpr (LINEAR) {
             return launch_kernel(beamform_x2_kernel<ORDER, LINEAR, NGP, kLinPairs>, once, err, p,
                                  grid, smem, s);
-        } else if (p.pairs == kRoundPairs) {
+        } else if (p.pairs == round_pairs(ORDER)) {
             static std::once_flag once_w;
             static cudaError_t err_w = cudaSuccess;
-            return launch_persistent(beamform_x2_kernel<ORDER, LINEAR, NGP, kRoundPairs>, once_w,
-                                     err_w, p, grid, smem, s);
+            return launch_persistent(beamform_x2_kernel<ORDER, LINEAR, NGP, round_pairs(ORDER)>,
+                                     once_w, err_w, p, grid, smem, s);
         } else {
             return launch_persistent(beamform_x2_kernel<ORDER, LINEAR, NGP, 2>, once, err, p,
                                      grid, smem, s);
@@ -141,11 +141,12 @@ cudaError_t launch_beam_batch_variant(const BeamBatch &b, unsigned grid, size_t 
         if constexpr (LINEAR) {
             return launch_kernel(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, kLinPairs>, once,
                                  err, b, grid, smem, s);
-        } else if (b.e[0].pairs == kRoundPairs) {  // a batch's entries share their variant
+        } else if (b.e[0].pairs == round_pairs(ORDER)) {  // a batch's entries share their variant
             static std::once_flag once_w;
             static cudaError_t err_w = cudaSuccess;
-            return launch_persistent(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, kRoundPairs>,
-                                     once_w, err_w, b, grid, smem, s);
+            return launch_persistent(
+                beamform_x2_batch_kernel<ORDER, LINEAR, NGP, round_pairs(ORDER)>, once_w, err_w,
+                b, grid, smem, s);
         } else {
             return launch_persistent(beamform_x2_batch_kernel<ORDER, LINEAR, NGP, 2>, once, err,
                                      b, grid, smem, s);

@@ -286,8 +286,9 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
     if (uses_pair_kernel(d.chan_prec, d.order)) {
         // pixel pairs per lane (time tile 64 x pairs): nearest-sample frames
         // with enough work items take the wide tile
-        const size_t wide_items = (size_t)G * (size_t)((T + 64 * kRoundPairs - 1) / (64 * kRoundPairs));
-        hp.pairs = lin ? kLinPairs : (wide_items >= kWideMinItems ? kRoundPairs : 2);
+        const int rp = round_pairs(d.order);
+        const size_t wide_items = (size_t)G * (size_t)((T + 64 * rp - 1) / (64 * rp));
+        hp.pairs = lin ? kLinPairs : (wide_items >= kWideMinItems ? rp : 2);
         hp.tile = 64 * hp.pairs;
     } else {
         hp.pairs = 0;
