@@ -1289,9 +1289,13 @@ __device__ __forceinline__ void beamform_x2_run(const Src &src) {
         const unsigned char *buf = smem + 128 + (size_t)bf * stage_bytes;
         const float *w = reinterpret_cast<const float *>(buf);
         const int *s_rel = reinterpret_cast<const int *>(buf + stage_window_bytes(p));
-        // unrolled by 4 (measured on B300, 2048 x 16384 frame: unroll 2 480 us,
-        // 4 455 us, 8 472 us)
-#pragma unroll 4
+        // unrolled by 4 up to order 3 and by 8 above (measured on B300: two
+        // pixel pairs per lane, 2048 x 16384 frame, n = 5: unroll 2 480 us, 4 455
+        // us, 8 472 us; four pairs, n = 5: 4 455 us, 8 441 us, and the passive
+        // 256-microphone frame 21.99 against 21.22 ms; six pairs, n = 3, passive:
+        // 4 14.80 ms, 8 15.11 ms, 2 15.49 ms)
+        constexpr int kUnroll = ORDER > 3 ? 8 : 4;
+#pragma unroll kUnroll
         for (int il = 0; il < nc; ++il) {
             const int off = s_rel[il * 8 + warp];
             const float *r = w + il * WS + off + lane;
