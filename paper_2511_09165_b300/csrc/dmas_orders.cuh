@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         const float *s_wf = reinterpret_cast<const float *>(s_rel + NC * 8);
         const int nc = min(NC, p.N - ci * NC);
 
-#pragma unroll 4
+#pragma unroll 8
         for (int il = 0; il < nc; ++il) {
             const int off = s_rel[il * 8 + warp];
             const float *r = win + il * MB + off + lane;
