@@ -156,7 +156,9 @@ inline size_t orders_smem_bytes(int nmax, bool lin, int mic_chunk, int window) {
     return 128 + 2 * orders_stage_bytes(nmax, lin, mic_chunk, window) +
            (lin ? (size_t)8 * orders_num_sums(nmax) * 32 * 4 : 0);
 }
-// Shared memory of one every-order CTA (two per SM: the register limit).
+// Shared memory of one every-order CTA: two per SM with interpolated delays,
+// three with nearest-sample ones (the register limits).
 constexpr size_t kOrdersSmemBudget = 110 * 1024;
+constexpr size_t kOrdersRoundSmemBudget = 72 * 1024;
 
 }  // namespace dmas

@@ -253,8 +253,11 @@ __device__ __forceinline__ void emit_orders(const float (&a)[OrdersLayout<NMAX>:
     }
 }
 
+// Two CTAs per SM with interpolated delays (twice the running sums), three
+// with nearest-sample ones (80 registers; measured on B300, hemisphere frame,
+// n = 5: 1.227 ms at two CTAs per SM, 1.145 ms at three).
 template <int NMAX, bool LINEAR, int NGP>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, LINEAR ? 2 : 3)
     beamform_orders_kernel(const __grid_constant__ OrdersParams p) {
     constexpr int kPairs = LINEAR ? 1 : 2;
     constexpr int kTile = 64 * kPairs;

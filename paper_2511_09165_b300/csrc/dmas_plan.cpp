@@ -339,7 +339,8 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
         const int mt = orders_tile(lin);
         const int mw = (int)round_up(mt + spread, kAlign);
         int chunk = 0;
-        while (chunk < N && orders_smem_bytes(d.order, lin, chunk + 1, mw) <= kOrdersSmemBudget)
+        while (chunk < N && orders_smem_bytes(d.order, lin, chunk + 1, mw) <=
+                                   (lin ? kOrdersSmemBudget : kOrdersRoundSmemBudget))
             ++chunk;
         if (chunk > 0) {
             const int n_chunks = (N + chunk - 1) / chunk;
