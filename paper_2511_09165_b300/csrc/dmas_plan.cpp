@@ -285,10 +285,11 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
     const size_t eb = chan_elem_bytes(d.chan_prec);
     if (uses_pair_kernel(d.chan_prec, d.order)) {
         // pixel pairs per lane (time tile 64 x pairs): nearest-sample frames
-        // with enough work items take the wide tile
+        // with enough work items, and at least one wide tile long, take the
+        // wide tile
         const int rp = round_pairs(d.order);
         const size_t wide_items = (size_t)G * (size_t)((T + 64 * rp - 1) / (64 * rp));
-        hp.pairs = lin ? kLinPairs : (wide_items >= kWideMinItems ? rp : 2);
+        hp.pairs = lin ? kLinPairs : (wide_items >= kWideMinItems && T >= 64 * rp ? rp : 2);
         hp.tile = 64 * hp.pairs;
     } else {
         hp.pairs = 0;
