@@ -304,9 +304,18 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
     const size_t budget = persistent ? kPairSmemBudget - 2 * 256
                                      : kWindowSmemBudget - (pair ? 8 * 6 * 32 * 4 : 0);
     const size_t tab = (size_t)kGroup * 4 * (lin ? 2 : 1);
-    const size_t per_mic = persistent ? 2 * ((size_t)window * eb + tab)
-                                      : (pair ? lin_mic_bytes((int)window) + (size_t)kGroup * 12
-                                              : (size_t)window * eb + tab);
+    auto bytes_per_mic = [&](long long w) {
+        return persistent ? 2 * ((size_t)w * eb + tab)
+                          : (pair ? lin_mic_bytes((int)w) + (size_t)kGroup * 12
+                                  : (size_t)w * eb + tab);
+    };
+    if (persistent && hp.pairs > 2 && bytes_per_mic(window) > budget) {
+        // a delay spread too wide for the wide tile: back to two pairs
+        hp.pairs = 2;
+        hp.tile = 64 * hp.pairs;
+        window = round_up(hp.tile + spread, kAlign);
+    }
+    const size_t per_mic = bytes_per_mic(window);
     if (per_mic > budget)
         return fail("a direction group's delay spread does not fit in shared memory");
     hp.window = (int)window;
