@@ -153,6 +153,25 @@ def test_wide_tile_round(order):
     assert_parity(g, r)
 
 
+def test_wide_delay_spread_keeps_the_narrow_tile():
+    """A nearest-sample frame with enough work for the wide tile but delay
+    spreads too long for its staging budget (8 microphones, 2048 directions,
+    delays of 0..8900 samples) falls back to two pixel pairs per lane and still
+    matches the oracle."""
+    rng = np.random.default_rng(11)
+    N, T, M, fs = 8, 4096, 2048, 1000.0
+    frame = rng.standard_normal((N, T)).astype(np.float32)
+    tau = rng.integers(0, 8901, size=(M, N)) / fs
+    plan = dm.Plan(delays_s=tau, n_samples=T, fs=fs, order=3, delay_mode=dm.ROUND,
+                   env_cutoff_hz=100.0, env_taps=15)
+    assert plan.info().time_tile == 128
+    plan.close()
+    g = _explicit(frame, tau, fs, 3, dm.ROUND, env_cutoff_hz=100.0, env_taps=15)
+    r = oracle.dmas(frame.astype(np.float64), tau, fs, 3, oracle.ROUND, use_cf=True,
+                    taps=oracle.fir_taps(fs, 100.0, 15))
+    assert_parity(g, r)
+
+
 @pytest.mark.parametrize("ng", ["cf32", "f64", "f32"])
 @pytest.mark.parametrize("order", [1, 2, 3, 4, 5])
 def test_every_order_linear(order, ng):
