@@ -992,6 +992,7 @@ dmas_status enqueue_orders(dmas_plan *p, const float *d_frame, unsigned mask, in
     op.row = hp.row;
     op.padl = hp.padl;
     op.window = hp.mo_window;
+    op.halves = hp.mo_halves;
     op.mic_chunk = hp.mo_chunk;
     op.n_groups = hp.n_groups;
     op.n_mics_f = (float)hp.N;
@@ -999,7 +1000,9 @@ dmas_status enqueue_orders(dmas_plan *p, const float *d_frame, unsigned mask, in
     const bool lin = hp.delay_mode == DMAS_DELAY_LINEAR;
     e = kOrdersLaunchers[hp.order](op, lin ? 1 : 0, hp.ng_prec,
                                    (unsigned)((size_t)hp.n_groups * hp.mo_tiles),
-                                   orders_smem_bytes(hp.order, lin, hp.mo_chunk, hp.mo_window), s);
+                                   orders_smem_bytes(hp.order, lin, hp.mo_chunk, hp.mo_window,
+                                                     hp.mo_halves),
+                                   s);
     if (e != cudaSuccess) return cuda_fail(p, e, "beamform_orders_kernel launch");
     mark(p, 2, s);
     p->env_ran = hp.L > 0;

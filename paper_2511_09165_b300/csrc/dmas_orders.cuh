@@ -94,6 +94,8 @@ struct OrdersParams {
     // coherence factor; -1: not wanted
     int slot[2][kOrdersMaxOrder + 1];
     int N, T, row, padl, window, mic_chunk, n_groups, use_tma;
+    int halves;         // interpolated delays: 64-sample halves per CTA tile (2 only with
+                        // one microphone chunk, which then takes one staging buffer)
     float n_mics_f, cf_eps;
 };
 
@@ -276,11 +278,16 @@ __global__ void __launch_bounds__(kThreads, LINEAR ? 2 : 3)
     const int SB = orders_stage_bytes_dev(NP, LINEAR, NC, WS);
     const int n_chunks = (p.N + NC - 1) / NC;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *s_vext = reinterpret_cast<float *>(smem + 128 + 2 * SB) + (warp * NA * 32 + lane);
+    // interpolated delays with every microphone in one stage: the CTA's tile is
+    // H halves of kTile samples, summed one after the other from one staged
+    // window (fewer CTA starts and less window overhang per output)
+    const int H = (LINEAR && p.halves > 1 && n_chunks == 1) ? p.halves : 1;
+    float *s_vext = reinterpret_cast<float *>(smem + 128 + (H > 1 ? 1 : 2) * SB) +
+                    (warp * NA * 32 + lane);
 
     const int tile = (int)(blockIdx.x / (unsigned)p.n_groups);
     const int g = (int)(blockIdx.x - (unsigned)tile * (unsigned)p.n_groups);
-    const int t0 = tile * kTile;
+    const int t0 = tile * kTile * H;
 
     // Staging microphone chunk ci into buffer ci & 1: thread 0 sets the
     // byte count and copies the tables (stage_head); after a barrier every
@@ -354,6 +361,8 @@ __global__ void __launch_bounds__(kThreads, LINEAR ? 2 : 3)
 
     f32x2_t acc[kPairs][NA];
     f32x2_t vac[LINEAR ? NA : 1];
+    for (int h = 0; h < H; ++h) {
+    const int th = kTile * h;  // this half's first sample within the CTA tile
 #pragma unroll
     for (int q = 0; q < NA; ++q) {
 #pragma unroll
@@ -367,8 +376,8 @@ __global__ void __launch_bounds__(kThreads, LINEAR ? 2 : 3)
     for (int ci = 0; ci < n_chunks; ++ci) {
         const int b = ci & 1;
         const uint32_t parity = (uint32_t)(ci >> 1) & 1u;
-        const bool ok = mbar_wait_sleep_bounded(&bar[b], parity);
-        if (__syncthreads_or(!ok)) {
+        const bool ok = h > 0 || mbar_wait_sleep_bounded(&bar[b], parity);
+        if (h == 0 && __syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
                 atomicOr(p.err, kErrTimeout);
                 // let the copies in flight land: this chunk's and the next one's
@@ -386,7 +395,7 @@ __global__ void __launch_bounds__(kThreads, LINEAR ? 2 : 3)
 
 #pragma unroll 8
         for (int il = 0; il < nc; ++il) {
-            const int off = s_rel[il * 8 + warp];
+            const int off = s_rel[il * 8 + warp] + th;
             const float *r = win + il * MB + off + lane;
             if (!checked_ok(off >= 0 && off + 31 + 64 * (kPairs - 1) + 32 < WS, p.err)) continue;
             if constexpr (LINEAR) {
@@ -417,10 +426,11 @@ __global__ void __launch_bounds__(kThreads, LINEAR ? 2 : 3)
 #pragma unroll
                 for (int q = 0; q < NA; ++q) ve[q] = s_vext[q * 32];
                 for (int il = lane; il < nc; il += 32) {
-                    if (!checked_ok(s_rel[il * 8 + warp] >= 0 && s_rel[il * 8 + warp] + kTile < WS,
+                    if (!checked_ok(s_rel[il * 8 + warp] >= 0 &&
+                                        s_rel[il * 8 + warp] + th + kTile < WS,
                                     p.err))
                         continue;
-                    const float *r = win + il * MB + s_rel[il * 8 + warp] + kTile;
+                    const float *r = win + il * MB + s_rel[il * 8 + warp] + th + kTile;
                     float st[NP], sv[NMAX];
 #pragma unroll
                     for (int q = 0; q < NP; ++q) st[q] = r[q * WS];
@@ -471,15 +481,16 @@ __global__ void __launch_bounds__(kThreads, LINEAR ? 2 : 3)
 #pragma unroll
         for (int q = 0; q < NA; ++q) f2_unpack(acc[k][q], a[0][q], a[1][q]);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int t = t0 + lane + 32 * h + 64 * k;
+        for (int hh = 0; hh < 2; ++hh) {
+            const int t = t0 + th + lane + 32 * hh + 64 * k;
             if (t >= p.T) continue;
             const size_t pix = (size_t)dir * p.T + t;
-            const float cf = cf_ratio(a[h][0], a[h][1], p.n_mics_f, p.cf_eps);
-            emit_orders<1, NMAX, NGP>(a[h], cf, p, pix);
+            const float cf = cf_ratio(a[hh][0], a[hh][1], p.n_mics_f, p.cf_eps);
+            emit_orders<1, NMAX, NGP>(a[hh], cf, p, pix);
             if (p.cf) p.cf[pix] = cf;
         }
     }
+    }  // halves
 }
 
 // Launch of one (NMAX, delay mode, Newton-Girard precision) variant; each

@@ -345,7 +345,19 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
     // interpolated ones; as many microphones per stage as fit two stages in
     // the budget, in balanced chunks.
     hp.mo_tile = hp.mo_window = hp.mo_chunk = hp.mo_tiles = 0;
-    if (pair) {
+    hp.mo_halves = 1;
+    const size_t mo_budget = lin ? kOrdersSmemBudget : kOrdersRoundSmemBudget;
+    if (pair && lin &&
+        orders_smem_bytes(d.order, lin, N, (int)round_up(2 * orders_tile(lin) + spread, kAlign),
+                          2) <= mo_budget) {
+        // interpolated delays, every microphone in one stage: a tile of two
+        // 64-sample halves summed one after the other from one staged window
+        hp.mo_halves = 2;
+        hp.mo_tile = 2 * orders_tile(lin);
+        hp.mo_window = (int)round_up(hp.mo_tile + spread, kAlign);
+        hp.mo_chunk = N;
+        hp.mo_tiles = (T + hp.mo_tile - 1) / hp.mo_tile;
+    } else if (pair) {
         const int mt = orders_tile(lin);
         const int mw = (int)round_up(mt + spread, kAlign);
         int chunk = 0;
@@ -364,6 +376,10 @@ dmas_status build_host_plan(const dmas_plan_desc &d, HostPlan &hp, std::string *
     hp.padl = (int)round_up(std::max(0, -ws_min), kAlign);
     long long read_end = (long long)hp.padl + (long long)(hp.n_tiles - 1) * hp.tile +
                          ws_max + window;
+    if (hp.mo_chunk > 0)  // the every-order pass's last window as well
+        read_end = std::max<long long>(read_end, (long long)hp.padl +
+                                                     (long long)(hp.mo_tiles - 1) * hp.mo_tile +
+                                                     ws_max + hp.mo_window);
     hp.row = (int)round_up(std::max<long long>(read_end, (long long)hp.padl + T), kAlign);
 
     // ---- envelope taps (windowed sinc, Hamming, unit DC gain) -----------
