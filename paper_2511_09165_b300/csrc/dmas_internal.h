@@ -65,8 +65,9 @@ struct HostPlan {
     // its time tile, staged window, microphones per stage and time tiles;
     // mo_chunk == 0 when the pass is not available for this plan
     int mo_tile = 0, mo_window = 0, mo_chunk = 0, mo_tiles = 0;
-    // interpolated delays: the CTA's tile is summed in mo_halves halves of 64
-    // samples from one staged window (2 when every microphone fits one stage)
+    // interpolated delays: the CTA's tile is summed in mo_halves pieces of 64
+    // samples from one staged window (2 or 3 when every microphone fits one
+    // stage)
     int mo_halves = 1;
 
     std::vector<float> taps;  // [L]
@@ -155,7 +156,8 @@ inline size_t orders_stage_bytes(int nmax, bool lin, int mic_chunk, int window) 
     return ((size_t)mic_chunk * orders_mic_bytes(nmax, window) + (size_t)mic_chunk * kGroup * 4 +
             (lin ? (size_t)mic_chunk * kGroup * 8 : 0) + 127) & ~(size_t)127;
 }
-// (halves > 1: one microphone chunk, one staging buffer)
+// (halves > 1: pieces of the tile from one microphone chunk, one staging
+// buffer)
 inline size_t orders_smem_bytes(int nmax, bool lin, int mic_chunk, int window, int halves = 1) {
     return 128 + (halves > 1 ? 1 : 2) * orders_stage_bytes(nmax, lin, mic_chunk, window) +
            (lin ? (size_t)8 * orders_num_sums(nmax) * 32 * 4 : 0);

@@ -94,8 +94,9 @@ struct OrdersParams {
     // coherence factor; -1: not wanted
     int slot[2][kOrdersMaxOrder + 1];
     int N, T, row, padl, window, mic_chunk, n_groups, use_tma;
-    int halves;         // interpolated delays: 64-sample halves per CTA tile (2 only with
-                        // one microphone chunk, which then takes one staging buffer)
+    int halves;         // interpolated delays: 64-sample pieces per CTA tile (more than 1
+                        // only with one microphone chunk, which then takes one staging
+                        // buffer)
     float n_mics_f, cf_eps;
 };
 
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, LINEAR ? 2 : 3)
     const int n_chunks = (p.N + NC - 1) / NC;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // interpolated delays with every microphone in one stage: the CTA's tile is
-    // H halves of kTile samples, summed one after the other from one staged
+    // H pieces of kTile samples, summed one after the other from one staged
     // window (fewer CTA starts and less window overhang per output)
     const int H = (LINEAR && p.halves > 1 && n_chunks == 1) ? p.halves : 1;
     float *s_vext = reinterpret_cast<float *>(smem + 128 + (H > 1 ? 1 : 2) * SB) +
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, LINEAR ? 2 : 3)
     f32x2_t acc[kPairs][NA];
     f32x2_t vac[LINEAR ? NA : 1];
     for (int h = 0; h < H; ++h) {
-    const int th = kTile * h;  // this half's first sample within the CTA tile
+    const int th = kTile * h;  // this piece's first sample within the CTA tile
 #pragma unroll
     for (int q = 0; q < NA; ++q) {
 #pragma unroll
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(kThreads, LINEAR ? 2 : 3)
             if (p.cf) p.cf[pix] = cf;
         }
     }
-    }  // halves
+    }  // pieces
 }
 
 // Launch of one (NMAX, delay mode, Newton-Girard precision) variant; each
