@@ -9,8 +9,10 @@ different frames, and compare each result with dmas_beamform on the same plan
 and frame: once with nearest-sample delays, once with interpolated delays
 (whose kernel reads the root rows through a tensor map built over whichever
 scratch the call uses, so alternating the two entry points on one plan must
-rebuild it each time).  They live in their own file, collected last, and pass
-both alone in a fresh process and after the rest of the suite.
+rebuild it each time).  One more captures the call in a CUDA graph in global
+capture mode, which fails if anything in the captured call allocates.  They
+live in their own file, collected last, and pass both alone in a fresh process
+and after the rest of the suite.
 """
 import ctypes
 
@@ -87,4 +89,38 @@ def test_noalloc_rejects_plans_larger_than_its_scratch():
     msg = lib.dmas_plan_last_error(plan.handle).decode()
     assert "static" in msg and str(16 << 20) in msg
     assert torch.count_nonzero(image).item() == 0             # nothing was launched
+    plan.close()
+
+
+def test_noalloc_call_captures_in_a_global_mode_cuda_graph():
+    """A CUDA graph captured in global mode fails if anything in the captured
+    region allocates device memory, so a capture that succeeds shows that the
+    call allocates nothing; the replayed graph must give the image of an
+    ordinary call."""
+    lib = dm.load_library()
+    sc = scenes.hemi_3d(seed=4, n_samples=2048, n_dirs=256)   # linear delays
+    plan = dm.Plan(mic_xyz=sc.mic_xyz, dir_unit=sc.dir_unit, n_samples=sc.n_samples,
+                   fs=sc.fs, c=sc.c, order=5, delay_mode=dm.LINEAR)
+    frame = torch.from_numpy(sc.frame).cuda()
+    want = plan(frame).clone()
+    got = torch.full_like(want, float("nan"))
+    # one warm call: the static array's address and the tensor map over it are
+    # looked up before the capture
+    assert _call_noalloc(lib, plan, frame, got) == 0
+    torch.cuda.synchronize()
+    got.fill_(float("nan"))
+    graph = torch.cuda.CUDAGraph()
+    statuses = []
+    with torch.cuda.graph(graph, capture_error_mode="global"):
+        statuses.append(_call_noalloc(lib, plan, frame, got))
+    assert statuses == [0]
+    torch.cuda.synchronize()
+    assert torch.isnan(got).all()           # capturing ran nothing
+    graph.replay()
+    torch.cuda.synchronize()
+    plan.check()
+    g, w = got.cpu().numpy(), want.cpu().numpy()
+    assert np.all(np.isfinite(g))
+    assert eps_peak(g, w) <= TOL_F32
+    del graph
     plan.close()
