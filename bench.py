@@ -1043,7 +1043,7 @@ def main() -> None:
     ap.add_argument("--serve-bulk-depth", type=int, default=2,
                     help="big-frame batches in flight at once")
     ap.add_argument("--serve-to-host-rates", type=float, nargs="*", default=[100.0])
-    ap.add_argument("--serve-env-cap", type=int, default=16,
+    ap.add_argument("--serve-env-cap", type=int, default=0,
                     help="tensor-core envelope tiles per CTA for the bulk lane (0: no cap)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--split", action="store_true",

@@ -229,7 +229,8 @@ dmas_status dmas_beamform_host(dmas_plan *plan, const float *h_frame, float *h_i
  * that run the same kernel variant (order, delay mode, channel and
  * Newton-Girard precision, tile; for the envelope, the same taps) share one
  * launch per stage, up to 64 entries per launch, so a mixed batch costs a few
- * launches instead of three per frame.  plans/d_frames/d_images are HOST
+ * launches instead of three per frame; a batch of one entry is enqueued
+ * exactly as dmas_beamform enqueues it.  plans/d_frames/d_images are HOST
  * arrays of `count` entries; each frame and image is a device buffer shaped as
  * for dmas_beamform.  The same plan may appear more than once (each entry gets
  * its own scratch from the workspace).  d_workspace is device memory of at

@@ -1246,6 +1246,15 @@ dmas_status dmas_beamform_batch(int count, dmas_plan *const *plans, const float 
     if (((uintptr_t)d_workspace & 255) != 0) return DMAS_EINVAL;
     if (workspace_bytes < dmas_batch_workspace_bytes(count, plans)) return DMAS_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
+    // A batch of one runs exactly as dmas_beamform runs it, on the workspace:
+    // the batch kernels find each CTA's entry and normalise the staging size
+    // across entries, which a lone frame does not need (measured on B300, one
+    // 128 x 8192 x 32768 frame: 8.49 ms as a batch, 8.23 ms alone).
+    if (count == 1) {
+        plans[0]->last_stream = s;
+        return enqueue_frame(plans[0], d_frames[0], d_images[0], nullptr, nullptr, d_workspace,
+                             s);
+    }
     char *ws = (char *)d_workspace;
     std::vector<BatchEntry> v;
     try {

@@ -68,8 +68,13 @@ class Sensor:
 # Frames of at most this cost (microphones x directions x samples) take the
 # fast lane.
 FAST_COST = 1.3e9
-# Tensor-core envelope tiles per CTA for the bulk lane's plans
-BULK_ENV_TILE_CAP = 16
+# Tensor-core envelope tiles per CTA for the bulk lane's plans; 0: no cap
+# (one persistent CTA per SM).  Measured on B300, 16-sensor mix at 200
+# frames/s over four arrival seeds: without a cap the overall p99 is 0.04-0.4
+# ms lower than with 16 tiles per CTA and the small frames' p99 is the same
+# (1.1 ms): a capped envelope costs a big frame 0.03-0.06 ms of relaunched
+# CTAs, more than the small frames gain from the earlier SM slots.
+BULK_ENV_TILE_CAP = 0
 
 
 # Device-to-host copies of big images go out in pieces of this many bytes, so
@@ -230,8 +235,9 @@ class Server:
                 want[tuple(sn.image_shape)] += 4 if small else self.bulk_depth + 2
             for shape, n in want.items():
                 self.pinned.reserve(shape, n)
-        # big frames' envelopes retire their CTAs every few tiles, so the fast
-        # lane's kernels reach the SMs without waiting for a whole envelope
+        # with a cap, big frames' envelopes retire their CTAs every few tiles,
+        # so the fast lane's kernels reach the SMs without waiting for a whole
+        # envelope
         for sn in self.sensors:
             if sn.cost > self.fast_cost and hasattr(sn.plan, "set_envelope_tile_cap"):
                 sn.plan.set_envelope_tile_cap(bulk_env_tile_cap)
