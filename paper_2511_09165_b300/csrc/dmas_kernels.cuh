@@ -875,6 +875,46 @@ __device__ __forceinline__ void accumulate2_svm(f32x2_t (&sa)[SumLayout<ORDER>::
     v[NP + 1] = f2_fma(wm, m, v[NP + 1]);
 }
 
+// Order 5, K pixel pairs at once: every product formed before the sums that
+// use it, across the pairs, so each product is several instructions ahead
+// of its first use.  (Measured on B300, 2048 x 16384 interpolated frame:
+// 713.0 -> 710.8 us against one pair after the other, 126 registers.)
+template <int K>
+__device__ __forceinline__ void accumulate2_svm5_multi(f32x2_t (&sa)[K][SumLayout<5>::kNum],
+                                                       f32x2_t (&v)[K][SumLayout<5>::kNum],
+                                                       const f32x2_t (&s)[K],
+                                                       const f32x2_t (&m)[K], f32x2_t wf) {
+    constexpr int NP = SumLayout<5>::kNumP;
+    f32x2_t s2[K], w2[K], wm[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) s2[k] = f2_mul(s[k], s[k]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) wm[k] = f2_mul(wf, m[k]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        sa[k][0] = f2_add(sa[k][0], s[k]);
+        v[k][0] = f2_fma(wf, s[k], v[k][0]);
+        sa[k][NP] = f2_add(sa[k][NP], m[k]);
+        sa[k][NP + 1] = f2_fma(m[k], m[k], sa[k][NP + 1]);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) w2[k] = f2_mul(wf, s2[k]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        sa[k][1] = f2_add(sa[k][1], s2[k]);
+        sa[k][2] = f2_fma(s2[k], s[k], sa[k][2]);
+        sa[k][3] = f2_fma(s2[k], s2[k], sa[k][3]);
+        v[k][NP] = f2_add(v[k][NP], wm[k]);
+        v[k][NP + 1] = f2_fma(wm[k], m[k], v[k][NP + 1]);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        v[k][1] = f2_add(v[k][1], w2[k]);
+        v[k][2] = f2_fma(w2[k], s[k], v[k][2]);
+        v[k][3] = f2_fma(w2[k], s2[k], v[k][3]);
+    }
+}
+
 // The f-weighted part for one sample (root s, raw sample m) in scalar
 // arithmetic.
 template <int ORDER>
@@ -1022,10 +1062,20 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
                     continue;
             }
             const f32x2_t wf = wfp[8 * il];
+            if constexpr (ORDER == 5) {
+                f32x2_t sv[kPairs], mv[kPairs];
 #pragma unroll
-            for (int k = 0; k < kPairs; ++k)
-                accumulate2_svm<ORDER>(acc[k], vac[k], f2_pack(r[64 * k], r[64 * k + 32]),
-                                       f2_pack(r[WS + 64 * k], r[WS + 64 * k + 32]), wf);
+                for (int k = 0; k < kPairs; ++k) {
+                    sv[k] = f2_pack(r[64 * k], r[64 * k + 32]);
+                    mv[k] = f2_pack(r[WS + 64 * k], r[WS + 64 * k + 32]);
+                }
+                accumulate2_svm5_multi<kPairs>(acc, vac, sv, mv, wf);
+            } else {
+#pragma unroll
+                for (int k = 0; k < kPairs; ++k)
+                    accumulate2_svm<ORDER>(acc[k], vac[k], f2_pack(r[64 * k], r[64 * k + 32]),
+                                           f2_pack(r[WS + 64 * k], r[WS + 64 * k + 32]), wf);
+            }
         }
         // the sample past the tile lies inside the window (its span covers the
         // last pixel's x + 1)
