@@ -915,6 +915,37 @@ __device__ __forceinline__ void accumulate2_svm5_multi(f32x2_t (&sa)[K][SumLayou
     }
 }
 
+// Order 3, K pixel pairs at once, ordered as for order 5 above.  (Measured on
+// B300, 2048 x 16384 interpolated frame: 0.598 -> 0.594 ms per frame; the same
+// ordering at order 4 took 0.811 -> 0.822 ms at 128 registers, so order 4
+// keeps the pair-by-pair form.)
+template <int K>
+__device__ __forceinline__ void accumulate2_svm3_multi(f32x2_t (&sa)[K][SumLayout<3>::kNum],
+                                                       f32x2_t (&v)[K][SumLayout<3>::kNum],
+                                                       const f32x2_t (&s)[K],
+                                                       const f32x2_t (&m)[K], f32x2_t wf) {
+    constexpr int NP = SumLayout<3>::kNumP;
+    f32x2_t u[K], wm[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) u[k] = f2_mul(wf, s[k]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) wm[k] = f2_mul(wf, m[k]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        sa[k][0] = f2_add(sa[k][0], s[k]);
+        sa[k][1] = f2_fma(s[k], s[k], sa[k][1]);
+        sa[k][NP] = f2_add(sa[k][NP], m[k]);
+        sa[k][NP + 1] = f2_fma(m[k], m[k], sa[k][NP + 1]);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        v[k][0] = f2_add(v[k][0], u[k]);
+        v[k][1] = f2_fma(u[k], s[k], v[k][1]);
+        v[k][NP] = f2_add(v[k][NP], wm[k]);
+        v[k][NP + 1] = f2_fma(wm[k], m[k], v[k][NP + 1]);
+    }
+}
+
 // The f-weighted part for one sample (root s, raw sample m) in scalar
 // arithmetic.
 template <int ORDER>
@@ -1062,14 +1093,15 @@ __device__ __forceinline__ void beamform_x2_lin_body(const BeamParams &p, unsign
                     continue;
             }
             const f32x2_t wf = wfp[8 * il];
-            if constexpr (ORDER == 5) {
+            if constexpr (ORDER == 5 || ORDER == 3) {
                 f32x2_t sv[kPairs], mv[kPairs];
 #pragma unroll
                 for (int k = 0; k < kPairs; ++k) {
                     sv[k] = f2_pack(r[64 * k], r[64 * k + 32]);
                     mv[k] = f2_pack(r[WS + 64 * k], r[WS + 64 * k + 32]);
                 }
-                accumulate2_svm5_multi<kPairs>(acc, vac, sv, mv, wf);
+                if constexpr (ORDER == 5) accumulate2_svm5_multi<kPairs>(acc, vac, sv, mv, wf);
+                else accumulate2_svm3_multi<kPairs>(acc, vac, sv, mv, wf);
             } else {
 #pragma unroll
                 for (int k = 0; k < kPairs; ++k)
