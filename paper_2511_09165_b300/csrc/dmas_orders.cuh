@@ -175,6 +175,40 @@ __device__ __forceinline__ void accumulate_orders(f32x2_t (&a)[OrdersLayout<NMAX
     }
 }
 
+// Nearest-sample delays, K pixel pairs at once: the same sums as
+// accumulate_orders, each step taken for every pair before the next.
+template <int NMAX, int K>
+__device__ __forceinline__ void accumulate_orders_multi(f32x2_t (&a)[K][OrdersLayout<NMAX>::kNum],
+                                                        const f32x2_t (&s)[K][NMAX]) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const f32x2_t x = s[k][0];
+        a[k][0] = f2_add(a[k][0], x);
+        a[k][1] = f2_fma(x, x, a[k][1]);
+        if constexpr (NMAX >= 2) a[k][2] = f2_add(a[k][2], x & kAbsMask2);
+    }
+#pragma unroll
+    for (int q = 2; q <= NMAX; ++q) {
+        const int b = OrdersLayout<NMAX>::base(q);
+        f32x2_t pw[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            pw[k] = s[k][q - 1];
+            a[k][b] = f2_add(a[k][b], pw[k]);
+        }
+#pragma unroll
+        for (int j = 2; j < q - 1; ++j)
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                pw[k] = f2_mul(pw[k], s[k][q - 1]);
+                a[k][b + j - 1] = f2_add(a[k][b + j - 1], pw[k]);
+            }
+        if (q >= 3)
+#pragma unroll
+            for (int k = 0; k < K; ++k) a[k][b + q - 2] = f2_fma(pw[k], s[k][q - 1], a[k][b + q - 2]);
+    }
+}
+
 // Interpolated delays: every power of the sample goes plain into S and
 // f-weighted into V (the (1 - f)-weighted sum is S - V; only the weight {f, f}
 // is held per microphone).
@@ -409,15 +443,16 @@ __global__ void __launch_bounds__(kThreads, LINEAR ? 2 : 3)
                 expand_roots<NMAX>(st, s);
                 accumulate_orders_sv<NMAX>(acc[0], vac, s, wf);
             } else {
+                f32x2_t sk[kPairs][NMAX];
 #pragma unroll
                 for (int k = 0; k < kPairs; ++k) {
-                    f32x2_t st[NP], s[NMAX];
+                    f32x2_t st[NP];
 #pragma unroll
                     for (int q = 0; q < NP; ++q)
                         st[q] = f2_pack(r[q * WS + 64 * k], r[q * WS + 64 * k + 32]);
-                    expand_roots<NMAX>(st, s);
-                    accumulate_orders<NMAX>(acc[k], s);
+                    expand_roots<NMAX>(st, sk[k]);
                 }
+                accumulate_orders_multi<NMAX, kPairs>(acc, sk);
             }
         }
         if constexpr (LINEAR) {
