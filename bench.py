@@ -116,9 +116,9 @@ WORKLOADS = {
 # interpolated-delay pair kernel on the hemisphere frame), valid only while
 # the kernel source is the one that was measured; otherwise the line's
 # "traffic" is null and "traffic_note" says why.
-TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "ng": "cf32", "kernel_src_sha256_16": "ba1378ea2feeeec1",
+TRAFFIC_RECORD = {"workload": "hemi_3d_n5", "ng": "cf32", "kernel_src_sha256_16": "9eaadf1d3864f53f",
                   # ncu dram__bytes_read.sum + dram__bytes_write.sum (bytes)
-                  "bytes": 5_145_856 + 76_070_912}
+                  "bytes": 5_145_600 + 76_103_680}
 
 
 def beam_traffic(workload: str, ng: str = "cf32"):

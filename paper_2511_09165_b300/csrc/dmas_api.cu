@@ -469,6 +469,12 @@ unsigned roots_blocks(const dmas_plan *p) {
     const size_t total = (size_t)p->hp.N * p->hp.row;
     return (unsigned)std::min<size_t>((total + 255) / 256, 148 * 32);
 }
+// The roots kernels take four samples per thread (rows are multiples of 8).
+static_assert(kAlign % 4 == 0, "a roots group of four samples must not straddle a row");
+unsigned roots4_blocks(const dmas_plan *p) {
+    const size_t groups = (size_t)p->hp.N * p->hp.row / 4;
+    return (unsigned)std::min<size_t>((groups + 255) / 256, 148 * 32);
+}
 
 // Where y (E_n x CF before the envelope) goes: the image itself without the
 // envelope, else d_y or the scratch after the root channels.
@@ -583,7 +589,7 @@ dmas_status enqueue_roots(dmas_plan *p, const float *d_frame, void *scratch, cud
         d_frame = mf_buffer(p, scratch);
     }
     const RootsParams rp = roots_params(p, d_frame, scratch);
-    const unsigned rgrid = roots_blocks(p);
+    const unsigned rgrid = roots4_blocks(p);
     switch (p->hp.chan_prec) {
         case DMAS_CH_F16: roots_kernel<__half><<<rgrid, 256, 0, s>>>(rp); break;
         case DMAS_CH_BF16: roots_kernel<__nv_bfloat16><<<rgrid, 256, 0, s>>>(rp); break;
@@ -791,7 +797,7 @@ dmas_status enqueue_batch(const std::vector<BatchEntry> &v, cudaStream_t s) {
                 rb.e[k] = roots_params(x.plan,
                                        x.plan->hp.mf.empty() ? x.frame : mf_buffer(x.plan, x.scratch),
                                        x.scratch);
-                blocks += roots_blocks(x.plan);
+                blocks += roots4_blocks(x.plan);
             }
             rb.start[rb.count] = blocks;
             if (chan == DMAS_CH_F16) roots_batch_kernel<__half><<<blocks, 256, 0, s>>>(rb);

@@ -231,18 +231,47 @@ __device__ __forceinline__ float signed_root(float m, int order, float inv_order
     }
 }
 
+// Four consecutive channel samples of one row with one vector store (rows
+// and the left pad are multiples of 8 samples, so a group never straddles a
+// row and starts on a 16-byte boundary for FP32, 8 for 16-bit channels).
+template <typename CH> __device__ __forceinline__ void store4(CH *dst, const float (&v)[4]);
+template <> __device__ __forceinline__ void store4<float>(float *dst, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <> __device__ __forceinline__ void store4<__half>(__half *dst, const float (&v)[4]) {
+    const __half2 a = __floats2half2_rn(v[0], v[1]), b = __floats2half2_rn(v[2], v[3]);
+    *reinterpret_cast<uint2 *>(dst) = make_uint2(*reinterpret_cast<const unsigned *>(&a),
+                                                 *reinterpret_cast<const unsigned *>(&b));
+}
+template <> __device__ __forceinline__ void store4<__nv_bfloat16>(__nv_bfloat16 *dst,
+                                                                  const float (&v)[4]) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]);
+    const __nv_bfloat162 b = __floats2bfloat162_rn(v[2], v[3]);
+    *reinterpret_cast<uint2 *>(dst) = make_uint2(*reinterpret_cast<const unsigned *>(&a),
+                                                 *reinterpret_cast<const unsigned *>(&b));
+}
+
+// `first` and `stride` count groups of four samples.
 template <typename CH>
 __device__ __forceinline__ void roots_body(const RootsParams &p, size_t first, size_t stride) {
     const size_t total = (size_t)p.N * (size_t)p.row;
+    const size_t groups = total / 4;
+    const unsigned row4 = (unsigned)p.row / 4u;
     CH *chan = reinterpret_cast<CH *>(p.chan);
     if (first < kWorkSlots && p.work) p.work[first] = 0u;
-    for (size_t idx = first; idx < total; idx += stride) {
-        const int i = (int)(idx / (size_t)p.row);
-        const int c = (int)(idx - (size_t)i * p.row);
-        const int t = c - p.padl;
-        const float m = (t >= 0 && t < p.T) ? p.frame[(size_t)i * p.T + t] : 0.0f;
-        chan[idx] = to_ch<CH>(signed_root(m, p.order, p.inv_order));
-        if (p.raw) chan[total + idx] = to_ch<CH>(m);
+    for (size_t gi = first; gi < groups; gi += stride) {
+        const size_t i = gi / row4;
+        const int c = (int)(gi - i * row4) * 4;
+        const float *src = p.frame + i * (size_t)p.T;
+        float m[4], r[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int t = c + j - p.padl;
+            m[j] = (t >= 0 && t < p.T) ? src[t] : 0.0f;
+            r[j] = signed_root(m[j], p.order, p.inv_order);
+        }
+        store4<CH>(chan + gi * 4, r);
+        if (p.raw) store4<CH>(chan + total + gi * 4, m);
     }
 }
 
